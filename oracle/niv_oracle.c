@@ -1,0 +1,416 @@
+/*
+ * CPU FP64 oracle of the Neural Irradiance Volume query, its loss and its gradient.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the benchmark's
+ * CPU-baseline / reference leg may load this code.  It shares no source with
+ * the CUDA library; the two meet only through the seeded inputs of niv_inputs.
+ *
+ * Every function follows the paper's description step by step, in plain loops:
+ *  - Sec. 4.1 (multi-level hash-grid encoding of Mueller et al. 2022, which the
+ *    paper adopts): per level a resolution N_l = floor(base * growth^l); dense
+ *    storage of the (N_l+1)^d vertices when that fits in T entries, otherwise the
+ *    spatial hash  (XOR_k v_k * pi_k) mod T  with pi = (1, 2654435761, 805459861);
+ *    multilinear interpolation of the F features stored at the 2^d cell corners.
+ *  - Sec. 4.1: a fully connected network with ReLU on all but the final layer,
+ *    mapping (encoded position, direction) to irradiance; the final activation is
+ *    softplus (keeps E >= 0).
+ *  - Eq. 3 (Sec. 4.5): relative L2 loss (E_theta - E)^2 / (sg(E_theta^2) + eps).
+ *  - Sec. 4.5: Adam.
+ *
+ * Readings where the paper is silent (also listed in the design notes):
+ *  - position normalisation u = (p - aabb_min) * inv_extent, clamped to [0,1],
+ *    each step an FP32 operation (so that grid indices are well defined); here
+ *    emulated exactly by rounding FP64 results of FP32 operands to float;
+ *  - s = u * N_l (FP32 product), i = min(floor(s), N_l - 1), w = s - i, vertices
+ *    at integer coordinates 0..N_l (no half-cell offset);
+ *  - 4th (time) grid dimension hashed with a caller-chosen odd constant;
+ *  - network input = [level 0 features, ..., level L-1 features, n.xyz, (t)].
+ *
+ * Parity status: every function here is pinned by tests (closed forms, brute
+ * force, library special cases, finite differences).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_LEVELS 32
+#define ORC_MAX_DIMS 4
+#define ORC_MAX_LAYERS 8
+#define ORC_MAX_WIDTH 256
+
+typedef struct {
+    int32_t dims;      /* 3 (x,y,z) or 4 (x,y,z,t) */
+    int32_t levels;    /* L */
+    int32_t feat;      /* F features per table entry */
+    int32_t log2_T;    /* hashed table size T = 2^log2_T */
+    double base;       /* N_0 */
+    double growth;     /* per-level scale */
+    int32_t n_hidden;  /* hidden layers */
+    int32_t width;     /* hidden width */
+    int32_t in_extra;  /* raw inputs after the encoding: 3 (normal) or 4 (normal, t) */
+    int32_t out_dim;   /* 3 */
+    int32_t out_act;   /* 0 identity, 1 softplus */
+    uint32_t prime_t;  /* hash constant of the 4th dimension */
+} orc_desc;
+
+typedef struct {
+    int32_t res[ORC_MAX_LEVELS];
+    int32_t dense[ORC_MAX_LEVELS];
+    int64_t offset[ORC_MAX_LEVELS]; /* first entry of the level */
+    int64_t entries[ORC_MAX_LEVELS];
+    int64_t total;                  /* entries over all levels */
+} orc_layout_t;
+
+static const uint32_t ORC_PI[3] = {1u, 2654435761u, 805459861u};
+
+/* ---- FP32 operations emulated in FP64 (exact: operands are floats) ---- */
+static float f32_sub(float a, float b) { return (float)((double)a - (double)b); }
+static float f32_mul(float a, float b) { return (float)((double)a * (double)b); }
+
+/* ---- level layout (Sec. 4.1) ---- */
+int64_t orc_layout(const orc_desc* d, int32_t* res, int32_t* dense, int64_t* offset, int64_t* entries)
+{
+    if (d->levels < 1 || d->levels > ORC_MAX_LEVELS || d->dims < 3 || d->dims > ORC_MAX_DIMS) return -1;
+    const int64_t T = (int64_t)1 << d->log2_T;
+    int64_t off = 0;
+    for (int l = 0; l < d->levels; ++l) {
+        int32_t N = (int32_t)floor(d->base * pow(d->growth, (double)l));
+        int64_t verts = 1;
+        for (int k = 0; k < d->dims; ++k) verts *= (int64_t)(N + 1);
+        int is_dense = verts <= T;
+        if (res) res[l] = N;
+        if (dense) dense[l] = is_dense;
+        if (offset) offset[l] = off;
+        if (entries) entries[l] = is_dense ? verts : T;
+        off += is_dense ? verts : T;
+    }
+    return off;
+}
+
+static int fill_layout(const orc_desc* d, orc_layout_t* L)
+{
+    L->total = orc_layout(d, L->res, L->dense, L->offset, L->entries);
+    return L->total < 0 ? -1 : 0;
+}
+
+/* index of vertex v in level l (dense row-major with x fastest, or spatial hash) */
+static int64_t vertex_index(const orc_desc* d, const orc_layout_t* L, int l, const int64_t* v)
+{
+    if (L->dense[l]) {
+        int64_t stride = 1, idx = 0;
+        for (int k = 0; k < d->dims; ++k) { idx += v[k] * stride; stride *= (int64_t)(L->res[l] + 1); }
+        return idx;
+    }
+    uint32_t h = 0;
+    for (int k = 0; k < d->dims; ++k) {
+        uint32_t p = k < 3 ? ORC_PI[k] : d->prime_t;
+        h ^= (uint32_t)v[k] * p; /* product mod 2^32 */
+    }
+    return (int64_t)(h & (uint32_t)(((uint64_t)1 << d->log2_T) - 1));
+}
+
+/* normalised grid coordinate of one query (FP32 operations, emulated exactly) */
+static void normalise(const orc_desc* d, const float* p, const float* aabb_min, const float* aabb_max,
+                      float t, float* u)
+{
+    for (int k = 0; k < 3; ++k) {
+        float inv = (float)(1.0 / ((double)aabb_max[k] - (double)aabb_min[k]));
+        float x = f32_mul(f32_sub(p[k], aabb_min[k]), inv);
+        u[k] = x < 0.0f ? 0.0f : (x > 1.0f ? 1.0f : x);
+    }
+    if (d->dims == 4) u[3] = t < 0.0f ? 0.0f : (t > 1.0f ? 1.0f : t);
+}
+
+/* per-level cell and weights: s = u*N (FP32), i = min(floor(s), N-1), w = s - i */
+static void cell_of(const orc_desc* d, int32_t N, const float* u, int64_t* i, double* w)
+{
+    for (int k = 0; k < d->dims; ++k) {
+        float s = f32_mul(u[k], (float)N);
+        int64_t ik = (int64_t)floor((double)s);
+        if (ik > N - 1) ik = N - 1;
+        i[k] = ik;
+        w[k] = (double)s - (double)ik;
+    }
+}
+
+/*
+ * Encoding of one query.  enc[l*F + j] = sum over the 2^d corners c of
+ * prod_k (c_k ? w_k : 1 - w_k) * table_l[index(i + c)][j].
+ * Optionally records the corner indices (level-major, corner-minor) and weights.
+ */
+static void encode_point(const orc_desc* d, const orc_layout_t* L, const double* grid, const float* u,
+                         double* enc, int64_t* idx_out, double* w_out)
+{
+    const int F = d->feat, nc = 1 << d->dims;
+    for (int l = 0; l < d->levels; ++l) {
+        int64_t i[ORC_MAX_DIMS];
+        double w[ORC_MAX_DIMS];
+        cell_of(d, L->res[l], u, i, w);
+        for (int j = 0; j < F; ++j) enc[l * F + j] = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            int64_t v[ORC_MAX_DIMS];
+            double wc = 1.0;
+            for (int k = 0; k < d->dims; ++k) {
+                int bit = (c >> k) & 1;
+                v[k] = i[k] + bit;
+                wc *= bit ? w[k] : 1.0 - w[k];
+            }
+            int64_t e = vertex_index(d, L, l, v);
+            for (int j = 0; j < F; ++j) enc[l * F + j] += wc * grid[(L->offset[l] + e) * F + j];
+            if (idx_out) idx_out[l * nc + c] = e;
+            if (w_out) w_out[l * nc + c] = wc;
+        }
+    }
+}
+
+int orc_net_inputs(const orc_desc* d) { return d->levels * d->feat + d->in_extra; }
+
+/* number of network parameters (all layers, weights and biases) */
+int64_t orc_mlp_param_count(const orc_desc* d)
+{
+    int64_t n = 0, k = orc_net_inputs(d);
+    for (int h = 0; h < d->n_hidden; ++h) { n += (int64_t)d->width * k + d->width; k = d->width; }
+    n += (int64_t)d->out_dim * k + d->out_dim;
+    return n;
+}
+
+static double softplus(double z) { return (z > 0.0 ? z : 0.0) + log1p(exp(-fabs(z))); }
+static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+/*
+ * Network forward for one input vector x (length n_in).  Stores every layer's
+ * pre-activation z_k (layer-major) and post-activation a_k when requested.
+ * Returns E (out_dim values).
+ */
+static void mlp_forward(const orc_desc* d, const double* mlp, const double* x, double* z_all, double* a_all,
+                        double* E)
+{
+    double buf_a[ORC_MAX_WIDTH], buf_b[ORC_MAX_WIDTH];
+    const double* in = x;
+    int k_in = orc_net_inputs(d);
+    const double* p = mlp;
+    int layers = d->n_hidden + 1;
+    for (int layer = 0; layer < layers; ++layer) {
+        int last = layer == layers - 1;
+        int n_out = last ? d->out_dim : d->width;
+        const double* W = p;
+        const double* b = p + (int64_t)n_out * k_in;
+        double* out = (layer & 1) ? buf_b : buf_a;
+        for (int o = 0; o < n_out; ++o) {
+            double z = b[o];
+            for (int i = 0; i < k_in; ++i) z += W[(int64_t)o * k_in + i] * in[i];
+            if (z_all) z_all[layer * ORC_MAX_WIDTH + o] = z;
+            double a;
+            if (!last) a = z > 0.0 ? z : 0.0;                   /* ReLU */
+            else a = d->out_act == 1 ? softplus(z) : z;         /* final layer */
+            out[o] = a;
+            if (a_all) a_all[layer * ORC_MAX_WIDTH + o] = a;
+            if (last) E[o] = a;
+        }
+        p = b + n_out;
+        in = out;
+        k_in = n_out;
+    }
+}
+
+/* assemble the network input of one query: [encoding, n.xyz, (t)] */
+static void net_input(const orc_desc* d, const double* enc, const float* nrm, float t, double* x)
+{
+    int ne = d->levels * d->feat;
+    for (int i = 0; i < ne; ++i) x[i] = enc[i];
+    x[ne + 0] = nrm[0];
+    x[ne + 1] = nrm[1];
+    x[ne + 2] = nrm[2];
+    if (d->in_extra == 4) x[ne + 3] = t;
+}
+
+/*
+ * Encoding only: enc[n][L*F].  Optionally the corner indices idx[n][L][2^d]
+ * (uint32) and corner weights w[n][L][2^d].
+ */
+int orc_encode(const orc_desc* d, const double* grid, const float* pos4, int64_t n, const float* aabb_min,
+               const float* aabb_max, float t, double* enc, uint32_t* idx, double* wts)
+{
+    orc_layout_t L;
+    if (fill_layout(d, &L)) return -1;
+    const int nc = 1 << d->dims, LF = d->levels * d->feat;
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) {
+        float u[ORC_MAX_DIMS];
+        int64_t ix[ORC_MAX_LEVELS * 16];
+        double wc[ORC_MAX_LEVELS * 16];
+        normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
+        encode_point(d, &L, grid, u, enc + q * LF, ix, wc);
+        for (int e = 0; e < d->levels * nc; ++e) {
+            if (idx) idx[q * d->levels * nc + e] = (uint32_t)ix[e];
+            if (wts) wts[q * d->levels * nc + e] = wc[e];
+        }
+    }
+    return 0;
+}
+
+/* network only: x[n][n_in] -> E[n][out_dim] */
+int orc_mlp(const orc_desc* d, const double* mlp, const double* x, int64_t n, double* E)
+{
+    const int n_in = orc_net_inputs(d);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) mlp_forward(d, mlp, x + q * n_in, NULL, NULL, E + q * d->out_dim);
+    return 0;
+}
+
+/*
+ * Full query (Sec. 4.4): G-buffer position and normal -> E(x, n).
+ * params = [grid values | network parameters] in FP64; pos4/nrm4 are [n][4] FP32
+ * records (FP16 G-buffers are widened exactly by the caller); t is the scene
+ * parameter of a 4-D model (ignored otherwise); out E[n][out_dim].
+ */
+int orc_query(const orc_desc* d, const double* params, const float* pos4, const float* nrm4, int64_t n,
+              const float* aabb_min, const float* aabb_max, float t, double* E)
+{
+    orc_layout_t L;
+    if (fill_layout(d, &L)) return -1;
+    const double* mlp = params + L.total * d->feat;
+    const int n_in = orc_net_inputs(d);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) {
+        float u[ORC_MAX_DIMS];
+        double enc[ORC_MAX_LEVELS * 8], x[ORC_MAX_LEVELS * 8 + 8];
+        normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
+        encode_point(d, &L, params, u, enc, NULL, NULL);
+        net_input(d, enc, nrm4 + 4 * q, t, x);
+        (void)n_in;
+        mlp_forward(d, mlp, x, NULL, NULL, E + q * d->out_dim);
+    }
+    return 0;
+}
+
+/*
+ * Loss (Eq. 3, mean over samples and channels, eps = 0.01 unless given) and its
+ * gradient with respect to every parameter, by reverse-mode differentiation of
+ * the steps above.  The denominator is a constant (stop-gradient).  ReLU'(0) = 0.
+ * Grid gradients sum over corners and samples (hash collisions add).
+ * t4 (nullable) gives a per-sample time input for 4-D models.
+ * grad must hold as many values as params and is overwritten.
+ */
+int orc_loss_grad(const orc_desc* d, const double* params, const float* pos4, const float* nrm4,
+                  const float* t_per_sample, const double* target, int64_t n, const float* aabb_min,
+                  const float* aabb_max, double eps, double* loss_out, double* grad)
+{
+    orc_layout_t L;
+    if (fill_layout(d, &L)) return -1;
+    const int F = d->feat, nc = 1 << d->dims, C = d->out_dim, layers = d->n_hidden + 1;
+    const int n_in = orc_net_inputs(d);
+    const int64_t n_grid = L.total * F;
+    const int64_t n_mlp = orc_mlp_param_count(d);
+    const double* mlp = params + n_grid;
+    memset(grad, 0, sizeof(double) * (size_t)(n_grid + n_mlp));
+    double loss = 0.0;
+    double* z_all = (double*)malloc(sizeof(double) * ORC_MAX_LAYERS * ORC_MAX_WIDTH);
+    double* a_all = (double*)malloc(sizeof(double) * ORC_MAX_LAYERS * ORC_MAX_WIDTH);
+    for (int64_t q = 0; q < n; ++q) {
+        float u[ORC_MAX_DIMS];
+        double enc[ORC_MAX_LEVELS * 8], x[ORC_MAX_LEVELS * 8 + 8], E[8];
+        int64_t ix[ORC_MAX_LEVELS * 16];
+        double wc[ORC_MAX_LEVELS * 16];
+        float tq = t_per_sample ? t_per_sample[q] : 0.0f;
+        normalise(d, pos4 + 4 * q, aabb_min, aabb_max, tq, u);
+        encode_point(d, &L, params, u, enc, ix, wc);
+        net_input(d, enc, nrm4 + 4 * q, tq, x);
+        mlp_forward(d, mlp, x, z_all, a_all, E);
+        /* dLoss/dE with the denominator held constant */
+        double g_out[ORC_MAX_WIDTH], g_in[ORC_MAX_WIDTH + ORC_MAX_LEVELS * 8];
+        for (int c = 0; c < C; ++c) {
+            double y = target[q * C + c];
+            double den = E[c] * E[c] + eps;
+            loss += (E[c] - y) * (E[c] - y) / den;
+            double dE = 2.0 * (E[c] - y) / den / ((double)n * C);
+            double z = z_all[(layers - 1) * ORC_MAX_WIDTH + c];
+            g_out[c] = d->out_act == 1 ? dE * sigmoid(z) : dE;
+        }
+        /* walk the layers backwards; parameter offsets recomputed per layer */
+        for (int layer = layers - 1; layer >= 0; --layer) {
+            int k_in = layer == 0 ? n_in : d->width;
+            int n_out = layer == layers - 1 ? C : d->width;
+            int64_t off = 0;
+            for (int ll = 0, kk = n_in; ll < layer; ++ll) { off += (int64_t)d->width * kk + d->width; kk = d->width; }
+            const double* W = mlp + off;
+            double* gW = grad + n_grid + off;
+            double* gb = gW + (int64_t)n_out * k_in;
+            const double* in = layer == 0 ? x : a_all + (layer - 1) * ORC_MAX_WIDTH;
+            for (int o = 0; o < n_out; ++o) {
+                gb[o] += g_out[o];
+                for (int i = 0; i < k_in; ++i) gW[(int64_t)o * k_in + i] += g_out[o] * in[i];
+            }
+            for (int i = 0; i < k_in; ++i) {
+                double s = 0.0;
+                for (int o = 0; o < n_out; ++o) s += W[(int64_t)o * k_in + i] * g_out[o];
+                g_in[i] = s;
+            }
+            if (layer > 0) { /* through the ReLU of the layer below */
+                for (int i = 0; i < k_in; ++i)
+                    g_out[i] = z_all[(layer - 1) * ORC_MAX_WIDTH + i] > 0.0 ? g_in[i] : 0.0;
+            }
+        }
+        /* g_in now holds dLoss/dx; scatter the encoding part into the tables */
+        for (int l = 0; l < d->levels; ++l)
+            for (int c = 0; c < nc; ++c)
+                for (int j = 0; j < F; ++j)
+                    grad[(L.offset[l] + ix[l * nc + c]) * F + j] += wc[l * nc + c] * g_in[l * F + j];
+    }
+    free(z_all);
+    free(a_all);
+    *loss_out = loss / ((double)n * C);
+    return 0;
+}
+
+/*
+ * One Adam step (Kingma & Ba 2014; Sec. 4.5 uses Adam) on every parameter:
+ * m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ * theta -= lr * (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ * step counts from 1.
+ */
+void orc_adam(double* theta, double* m, double* v, const double* g, int64_t n, double lr, double b1,
+              double b2, double eps, int64_t step)
+{
+    double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        theta[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}
+
+/* Diffuse shading (Eq. 2 plus direct light): rgb = albedo * E / pi + direct. */
+void orc_shade(const double* albedo3, const double* E3, const double* direct3, int64_t n, double* out3)
+{
+    for (int64_t i = 0; i < 3 * n; ++i) out3[i] = albedo3[i] * E3[i] / M_PI + direct3[i];
+}
+
+/*
+ * Round to the nearest FP8 E4M3 value (1 sign, 4 exponent bits with bias 7,
+ * 3 mantissa bits, subnormal step 2^-9, largest finite 448, no infinities),
+ * ties to even, saturating to +-448.  Written from the format's definition.
+ */
+double orc_e4m3(double x)
+{
+    if (isnan(x)) return x;
+    double a = fabs(x);
+    if (a >= 448.0) return copysign(448.0, x);
+    double step;
+    if (a < ldexp(1.0, -6)) {
+        step = ldexp(1.0, -9);
+    } else {
+        int e2;
+        frexp(a, &e2);           /* a = m * 2^e2, m in [0.5, 1) */
+        step = ldexp(1.0, e2 - 1 - 3);
+    }
+    double q = nearbyint(a / step) * step; /* default rounding mode: ties to even */
+    if (q > 448.0) q = 448.0;
+    return copysign(q, x);
+}
+
+void orc_e4m3_array(const double* x, int64_t n, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_e4m3(x[i]);
+}
