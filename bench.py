@@ -1,0 +1,312 @@
+"""Benchmark of the Neural Irradiance Volume query on one GB300 (or N independent replicas).
+
+Workload (default): the 1920x1080 FP16 G-buffer of the seeded 10 m room (24 spheres,
+8 boxes, pinhole camera), model with 16 levels x 2 features, base 16, growth 1.38,
+2^17-entry hashed tables, network 35-64-64-3 with softplus output.  One step = one
+niv_query over the whole frame (load G-buffer, normalise, per-level index, gather,
+interpolate, network, store E).  The fused FP16 tensor-core path is the headline;
+the plain FP32 path runs on the same frame beside it, and both are compared with
+the FP64 CPU oracle on sampled pixels.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl niv|reference]
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
+the launching stream, with a 256 MB write between steps to flush L2 (the frame
+and the model are smaller than L2).  Under torchrun every rank renders its own
+frame (weak scaling, no data-path collective) and the max time over ranks counts.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOP_PER_QUERY = {"c1": 2 * (35 * 64 + 64 * 64 + 64 * 3)}  # 13,056: network multiply-adds x 2
+GBUF_BYTES_PER_QUERY = 18  # 12 B of FP16 position/normal in, 6 B of FP16 E out (algorithmic)
+WORKLOAD = ("config1-1080p: seeded 10 m room (24 spheres, 8 boxes, sphere emitter) ray-cast to a "
+            "1920x1080 FP16 G-buffer; model 16 levels x 2 features, base 16, growth 1.38, T=2^17, "
+            "network 35-64-64-3 softplus, He-init weights")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="niv", choices=["niv", "reference"])
+    ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "fp8"])
+    ap.add_argument("--res", default="1080p", choices=["1080p", "4k"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison and error checks")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm": p["hbm_gbs"], "tensor": p["bf16_tflops"], "src": "measured"}
+    except Exception:
+        return {"hbm": 6800.0, "tensor": 1900.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _oracle_threads():
+    try:
+        import oracle
+        return int(oracle.lib().orc_num_threads())
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(a):
+    """The oracle as it stands, on the host cores, K timed steps over a bounded sample of the frame."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from niv_inputs import init_params
+    from niv_inputs.configs import MODEL_C1, ROOM_MIN, ROOM_MAX, RESOLUTIONS, room_gbuffer
+    w, h = RESOLUTIONS[a.res]
+    pos, nrm, _ = room_gbuffer(w, h)
+    om = oracle.Model(**MODEL_C1)
+    params = init_params(oracle.grid_value_count(om), oracle.layer_shapes(om), seed=0)
+    sample = 1 << 16
+    rng = np.random.default_rng(1)
+    times = []
+    for step in range(a.warmup + a.steps):
+        pick = rng.choice(len(pos), sample, replace=False)
+        p, n = pos[pick].astype(np.float32), nrm[pick].astype(np.float32)
+        t0 = time.perf_counter()
+        oracle.query(om, params, p, n, ROOM_MIN, ROOM_MAX)
+        dt = time.perf_counter() - t0
+        if step >= a.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = sample * a.steps / tot / 1e9
+    cores = _oracle_threads()
+    line = {
+        "impl": "reference", "metric": "Gqueries/s (ms/frame @1080p beside it)", "value": value,
+        "unit": "Gqueries/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * tot / a.steps, "ms_per_frame": 1e3 * (w * h) / (value * 1e9),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pixels": w * h, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "Gqueries/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d random pixels of the frame per step, FP64 C oracle with OpenMP" % sample},
+        "e2e": {"value": value, "unit": "Gqueries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2602_12949_gb300 import NIVModel, sync_status
+    from niv_inputs import init_params
+    from niv_inputs.configs import MODEL_C1, ROOM_MIN, ROOM_MAX, RESOLUTIONS, room_gbuffer
+
+    w, h = RESOLUTIONS[a.res]
+    npx = w * h
+    pos, nrm, _ = room_gbuffer(w, h)
+    model = NIVModel(**MODEL_C1)
+    g, _ = model.param_count()
+    params = init_params(g, model.layer_shapes(), seed=0)
+    model.set_params(params)
+    dpos = torch.from_numpy(pos).to(dev)
+    dnrm = torch.from_numpy(nrm).to(dev)
+    out = torch.empty((npx, 4), dtype=torch.float16, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    qkw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, image_width=w)
+
+    def timed(precision, out_t, steps, warmup):
+        for _ in range(warmup):
+            model.query(dpos, dnrm, out=out_t, precision=precision, **qkw)
+        sync_status()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for s, e in evs:
+            flush.zero_()
+            s.record(stream)
+            model.query(dpos, dnrm, out=out_t, precision=precision, **qkw)
+            e.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        sync_status()
+        return [s.elapsed_time(e) for s, e in evs]  # ms
+
+    with ClockSampler(torch.cuda.current_device() if ws == 1 else local) as clk:
+        ms = timed(a.precision, out, a.steps, a.warmup)
+    ms_total = sum(ms)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / a.steps
+    value = npx * ws / (ms_step * 1e-3) / 1e9
+
+    extra = {}
+    if not a.no_compare:
+        out32 = torch.empty((npx, 4), dtype=torch.float32, device=dev)
+        ms32 = timed("fp32", out32, max(5, a.steps // 2), 3)
+        extra["fp32_plain"] = {"ms_per_frame": statistics.mean(ms32),
+                               "gqueries_per_s": npx / (statistics.mean(ms32) * 1e-3) / 1e9}
+
+    # e2e: host buffers through niv_query_host (H2D + kernel + D2H inside the call)
+    hp = torch.from_numpy(pos).pin_memory().numpy()
+    hn = torch.from_numpy(nrm).pin_memory().numpy()
+    ho = torch.empty((npx, 4), dtype=torch.float16).pin_memory().numpy()
+    for _ in range(2):
+        model.query_host(hp, hn, out=ho, precision=a.precision, **qkw)
+    e2e_t = []
+    for _ in range(max(3, min(a.steps, 10))):
+        t0 = time.perf_counter()
+        model.query_host(hp, hn, out=ho, precision=a.precision, **qkw)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = npx / statistics.mean(e2e_t) / 1e9
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    mean_ms = statistics.mean(ms)
+    flop = FLOP_PER_QUERY["c1"] * npx
+    achieved = flop / (mean_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["tensor"], "unit": "TFLOP/s",
+                "frac": achieved / peaks["tensor"], "traffic": None,
+                "peak_source": "%s bf16 burst (fp16 dense rate equal)" % peaks["src"],
+                "hbm_achieved_gbs": GBUF_BYTES_PER_QUERY * npx / (mean_ms * 1e-3) / 1e9}
+
+    cpu = None
+    errs = {}
+    if not a.no_cpu_baseline:
+        import oracle
+        om = oracle.Model(**MODEL_C1)
+        sample = 1 << 17
+        pick = np.random.default_rng(1).choice(npx, sample, replace=False)
+        p32, n32 = pos[pick].astype(np.float32), nrm[pick].astype(np.float32)
+        oracle.query(om, params, p32[:1024], n32[:1024], ROOM_MIN, ROOM_MAX)
+        t0 = time.perf_counter()
+        ref = oracle.query(om, params, p32, n32, ROOM_MIN, ROOM_MAX)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sample / dt / 1e9, "unit": "Gqueries/s", "cores": _oracle_threads(), "kind": "oracle",
+               "sample": "%d random pixels of the frame, FP64 C oracle (OpenMP)" % sample,
+               "ms_per_frame_extrapolated": 1e3 * dt * npx / sample}
+        got = out[pick, :3].double().cpu().numpy()
+        den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+        errs[a.precision] = {"max_rel": float(np.max(np.abs(got - ref) / den)),
+                             "max_abs_normalised": float(np.max(np.abs(got - ref)) / np.abs(ref).max())}
+        if "fp32_plain" in extra:
+            got32 = out32[pick, :3].double().cpu().numpy()
+            errs["fp32"] = {"max_rel": float(np.max(np.abs(got32 - ref) / den)),
+                            "max_abs_normalised": float(np.max(np.abs(got32 - ref)) / np.abs(ref).max())}
+
+    line = {
+        "metric": "Gqueries/s (ms/frame @1080p beside it): %s fused vs FP32 plain, error vs FP64 oracle" %
+                  a.precision.upper(),
+        "value": value, "unit": "Gqueries/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms_step, "ms_per_frame": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "fp8": "e4m3"}[a.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("1920x1080", "%dx%d" % (w, h)), "pixels": npx,
+                   "precision": a.precision, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "Gqueries/s", "h2d_bytes_per_step": int(2 * hp.nbytes),
+                "d2h_bytes_per_step": int(ho.nbytes), "ms_per_frame": 1e3 * statistics.mean(e2e_t)},
+        "clocks": clk.summary(),
+        "gpu_launches": a.steps,
+        "err_vs_fp64": errs,
+        "paper_context": {"ms_per_frame_rtx4090_table1_8lv_f4": 1.35, "note": "different model and GPU"},
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    model.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * niv.h -- C ABI of the Neural Irradiance Volume query library (libniv.so).
+ *
+ * The library evaluates, per G-buffer pixel, the learned indirect irradiance
+ * E(x, n) of "Real-time Rendering with a Neural Irradiance Volume" (Sec. 4.4:
+ * the position and normal buffers are the model's input and the model infers
+ * E for every pixel in one batch), shades it (Eq. 2), and trains the model
+ * (Sec. 4.5) from Monte Carlo targets (Eq. 1).  All compute runs in CUDA
+ * kernels for sm_103a on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: NIV_OK (0) or a negative NIV_ERR_*.
+ *    niv_last_error() returns a message for the calling thread's last failure.
+ *  - "Device pointer" arguments are caller-owned CUDA device memory; the library
+ *    never frees them.  Records are contiguous [n][4] arrays of float32 or
+ *    float16 (xyz + one pad component), so each record is 16 or 8 bytes;
+ *    pointers must be 16-byte aligned (NIV_ERR_ALIGN otherwise).
+ *  - Work is enqueued asynchronously on the given stream (NULL = the legacy
+ *    default stream) unless a function says it synchronises.  Kernel-side
+ *    failures (a bounded wait that ran out) are latched in a device status word
+ *    and reported by niv_sync_status().
+ *  - A handle may be used from one host thread / stream at a time.
+ */
+#ifndef NIV_H
+#define NIV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define NIV_API __attribute__((visibility("default")))
+#else
+#define NIV_API
+#endif
+
+typedef struct CUstream_st* niv_stream; /* a cudaStream_t */
+typedef struct niv_model* niv_handle;
+
+#define NIV_OK 0
+#define NIV_ERR_ARG (-1)         /* invalid argument or shape */
+#define NIV_ERR_ALIGN (-2)       /* pointer not 16-byte aligned */
+#define NIV_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define NIV_ERR_UNSUPPORTED (-4) /* valid description that this build does not support */
+#define NIV_ERR_DEVICE (-5)      /* a kernel reported a failure (see niv_sync_status) */
+#define NIV_ERR_NOMEM (-6)       /* device allocation failed */
+
+/* network precision of a query */
+#define NIV_FP32 0 /* plain path: FP32 features, weights and arithmetic on CUDA cores */
+#define NIV_FP16 1 /* fused path: FP16 features and weights, tensor-core MLP, FP32 accumulate */
+#define NIV_FP8 2  /* fused path: E4M3 weights and activations with per-layer scales, FP32 accumulate */
+
+/* element type of [n][4] record buffers */
+#define NIV_F32 0
+#define NIV_F16 1
+
+/*
+ * Model description (Sec. 4.1).  The encoding is the multi-level hash grid the
+ * paper adopts: level l has resolution N_l = floor(base * growth^l) (FP64 on
+ * the host); it stores its (N_l+1)^dims vertices densely (x fastest) when that
+ * count is <= T = 2^log2_T, else T entries addressed by the spatial hash
+ * (XOR_k v_k * pi_k) mod T with pi = (1, 2654435761, 805459861, prime_t).
+ * Each entry holds `feat` features.  The network is fully connected: n_hidden
+ * ReLU layers of `width`, then `out_dim` outputs with softplus (out_act = 1) or
+ * identity (0).  Its input is [level features (level-major), n.xyz, (t)], so
+ * in_extra is 3, or 4 when a scene parameter t is appended (Sec. 6).
+ */
+typedef struct niv_model_desc {
+    int32_t dims;     /* 3, or 4 for a time-varying field (x, y, z, t) */
+    int32_t levels;   /* 1..32 */
+    int32_t feat;     /* 1, 2 or 4 */
+    int32_t log2_T;   /* 4..24 */
+    double base;      /* coarsest resolution */
+    double growth;    /* resolution scale between levels */
+    int32_t n_hidden; /* 1..4 */
+    int32_t width;    /* 16, 32 or 64 */
+    int32_t in_extra; /* 3 or 4 */
+    int32_t out_dim;  /* 3 */
+    int32_t out_act;  /* 0 identity, 1 softplus */
+    uint32_t prime_t; /* odd hash constant of the 4th dimension */
+} niv_model_desc;
+
+/*
+ * Per-call query parameters.  Positions map to grid coordinates by
+ * u = clamp((p - aabb_min) * inv_extent, 0, 1), inv_extent = fp32(1 / (max - min)),
+ * each step an FP32 operation; t (clamped to [0, 1]) is the 4th coordinate and
+ * the appended network input of 4-D models.  image_width > 0 declares the
+ * records to be a row-major image of that width, which the kernels traverse in
+ * 2-D tiles for cache locality (results are identical either way).
+ */
+typedef struct niv_query_params {
+    float aabb_min[3];
+    float aabb_max[3];
+    float t;
+    int32_t image_width;
+} niv_query_params;
+
+/* Library version string. */
+NIV_API const char* niv_version(void);
+
+/* Message describing the calling thread's most recent failed call ("" if none). */
+NIV_API const char* niv_last_error(void);
+
+/*
+ * Wait for all work queued on `stream`, then read and clear the device status
+ * word of the current device.  Returns NIV_OK, NIV_ERR_DEVICE if a kernel
+ * latched a failure (message in niv_last_error), or NIV_ERR_CUDA.
+ */
+NIV_API int niv_sync_status(niv_stream stream);
+
+/*
+ * Create a model on the current CUDA device (Sec. 4.1).  Allocates the FP32
+ * master parameters (all zero) and derived inference copies; the library owns
+ * them until niv_destroy.  NIV_ERR_ARG for an invalid description,
+ * NIV_ERR_UNSUPPORTED for a valid one outside the kernels' limits, NIV_ERR_NOMEM.
+ */
+NIV_API int niv_create(const niv_model_desc* desc, niv_handle* out);
+
+/* Free everything the handle owns (synchronises the device first).  NULL is accepted. */
+NIV_API int niv_destroy(niv_handle h);
+
+/*
+ * Level layout of the encoding (Sec. 4.1): for level l, its resolution N_l,
+ * whether it is dense (1) or hashed (0), its first entry and its entry count.
+ * Any output pointer may be NULL.  Host pointers.
+ */
+NIV_API int niv_level_info(niv_handle h, int32_t level, int32_t* res, int32_t* dense, int64_t* first_entry,
+                   int64_t* entries);
+
+/*
+ * Parameter counts: grid values (entries x feat) and network values (every
+ * layer's W[out][in] row-major followed by b[out]).  The flat parameter vector
+ * is [grid | network].  Host pointers, either may be NULL.
+ */
+NIV_API int niv_param_count(niv_handle h, int64_t* n_grid_values, int64_t* n_mlp_values);
+
+/*
+ * Replace all parameters with the n float32 values at `params` (host or device
+ * memory, detected), rebuild the FP16 / FP8 inference copies, reset the Adam
+ * state.  n must equal grid + network counts.  Synchronises `stream`.
+ */
+NIV_API int niv_set_params(niv_handle h, const float* params, int64_t n, niv_stream stream);
+
+/* Copy the n FP32 master parameters to `out` (host or device memory).  Synchronises `stream`. */
+NIV_API int niv_get_params(niv_handle h, float* out, int64_t n, niv_stream stream);
+
+/*
+ * The per-pixel query (Sec. 4.4): E = net(encode(u(p)), n, t) for n records.
+ * pos, nrm: device [n][4] records of type dtype_in (NIV_F32 / NIV_F16);
+ * out_E: device [n][4] records of type dtype_out holding E.rgb and 0.
+ * precision: NIV_FP32, NIV_FP16 or NIV_FP8 (NIV_FP8 requires niv_fp8_calibrate
+ * first).  n == 0 is a no-op.  Asynchronous on `stream`.
+ */
+NIV_API int niv_query(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+              const niv_query_params* params, void* out_E, int32_t dtype_out, int32_t precision,
+              niv_stream stream);
+
+/*
+ * niv_query for HOST buffers (pageable or pinned): copies pos/nrm to a
+ * handle-owned device staging area, runs the query, copies E back and
+ * synchronises `stream` before returning.
+ */
+NIV_API int niv_query_host(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+                   const niv_query_params* params, void* out_E, int32_t dtype_out, int32_t precision,
+                   niv_stream stream);
+
+/*
+ * Encoding only (Sec. 4.1), for inspection and parity checks: for each of the n
+ * position records, out_enc (device float32 [n][levels*feat], nullable)
+ * receives the interpolated level features in FP32 from the FP32 master grid,
+ * and out_idx (device uint32 [n][levels][2^dims], nullable) the table entry of
+ * every cell corner, corner c having offset bit k set along dimension k.
+ * Same normalisation and index arithmetic as niv_query.  Asynchronous.
+ */
+NIV_API int niv_encode(niv_handle h, const void* pos, int64_t n, int32_t dtype_in, const niv_query_params* params,
+                       float* out_enc, uint32_t* out_idx, niv_stream stream);
+
+/*
+ * Shading (Eq. 2 plus the runtime direct light of Sec. 3 / Fig. 3):
+ * rgba = (albedo * E / pi + direct, 1), FP32 arithmetic, FP16 output.
+ * albedo, direct, E: device [n][4] FP16 records; out_rgba: device [n][4] FP16.
+ */
+NIV_API int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out_rgba,
+              niv_stream stream);
+
+/*
+ * Diagnostic (no counterpart in the paper): one 128 x 64 x 32 FP16 tensor-core
+ * product of fixed small-integer operands, A[m][k] = (3m + 5k) mod 7 - 3 and
+ * B[n][k] = (5n + 3k) mod 5 - 2, written to out (device float32 [128][64],
+ * D = A B^T, exact).  swap_strides = 1 exchanges the two stride fields of the
+ * operand descriptors (a layout-convention probe that stays inside the operands).
+ * Asynchronous; a timeout of the completion wait is reported by niv_sync_status.
+ */
+NIV_API int niv_selftest_mma(int32_t swap_strides, float* out, niv_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NIV_H */

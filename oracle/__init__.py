@@ -86,6 +86,8 @@ def lib():
         P = ctypes.POINTER
         d, i64, f, u64 = ctypes.c_double, ctypes.c_int64, ctypes.c_float, ctypes.c_uint64
         vp = ctypes.c_void_p
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_num_threads.argtypes = []
         L.orc_layout.restype = i64
         L.orc_layout.argtypes = [P(Desc), vp, vp, vp, vp]
         L.orc_mlp_param_count.restype = i64

@@ -33,6 +33,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAX_LEVELS 32
 #define ORC_MAX_DIMS 4
@@ -61,6 +64,16 @@ typedef struct {
     int64_t entries[ORC_MAX_LEVELS];
     int64_t total;                  /* entries over all levels */
 } orc_layout_t;
+
+/* threads the oracle's parallel loops use (1 without OpenMP) */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 static const uint32_t ORC_PI[3] = {1u, 2654435761u, 805459861u};
 

@@ -1,0 +1,9 @@
+"""Neural Irradiance Volume query path for one GB300 (sm_103a).
+
+``libniv.so`` (hand-written CUDA kernels behind a C ABI, see include/niv.h) does
+all the work; this package marshals torch tensors into it.
+"""
+from ._lib import lib, NivError, LIB_PATH
+from .model import NIVModel, shade, sync_status, PRECISIONS
+
+__all__ = ["lib", "NivError", "LIB_PATH", "NIVModel", "shade", "sync_status", "PRECISIONS"]

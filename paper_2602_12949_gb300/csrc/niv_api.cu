@@ -1,0 +1,357 @@
+// Host side of the C ABI: model objects, parameter management, argument checks
+// and dispatch of the query / shading kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "niv_internal.cuh"
+
+namespace {
+
+thread_local std::string t_err;
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Device status words, one per device ordinal, allocated on first use.
+std::mutex g_status_mu;
+int* g_status[64] = {nullptr};
+
+__global__ void f32_to_f16_kernel(const float* __restrict__ src, __half* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2half_rn(src[i]);
+}
+
+int validate_desc(const niv_model_desc* d) {
+    if (!d) return niv_fail(NIV_ERR_ARG, "desc is NULL");
+    if (d->dims != 3 && d->dims != 4) return niv_fail(NIV_ERR_ARG, "dims must be 3 or 4");
+    if (d->levels < 1 || d->levels > NIV_MAX_LEVELS) return niv_fail(NIV_ERR_ARG, "levels must be in 1..32");
+    if (d->feat != 1 && d->feat != 2 && d->feat != 4) return niv_fail(NIV_ERR_UNSUPPORTED, "feat must be 1, 2 or 4");
+    if (d->log2_T < 4 || d->log2_T > 24) return niv_fail(NIV_ERR_ARG, "log2_T must be in 4..24");
+    if (!(d->base >= 1.0) || !(d->growth >= 1.0)) return niv_fail(NIV_ERR_ARG, "base and growth must be >= 1");
+    if (d->n_hidden < 1 || d->n_hidden > 4) return niv_fail(NIV_ERR_UNSUPPORTED, "n_hidden must be in 1..4");
+    if (d->width != 16 && d->width != 32 && d->width != 64)
+        return niv_fail(NIV_ERR_UNSUPPORTED, "width must be 16, 32 or 64");
+    if (d->in_extra != 3 && d->in_extra != 4) return niv_fail(NIV_ERR_ARG, "in_extra must be 3 or 4");
+    if (d->out_dim != 3) return niv_fail(NIV_ERR_UNSUPPORTED, "out_dim must be 3");
+    if (d->out_act != 0 && d->out_act != 1) return niv_fail(NIV_ERR_ARG, "out_act must be 0 or 1");
+    if (d->levels * d->feat + d->in_extra > NIV_MAX_IN) return niv_fail(NIV_ERR_UNSUPPORTED, "network input too wide");
+    if (d->dims == 4 && (d->prime_t & 1u) == 0) return niv_fail(NIV_ERR_ARG, "prime_t must be odd");
+    return NIV_OK;
+}
+
+int check_device(const niv_model* m) {
+    int dev = -1;
+    NIV_CUDA(cudaGetDevice(&dev));
+    if (dev != m->device) return niv_fail(NIV_ERR_ARG, "current device differs from the model's device");
+    return NIV_OK;
+}
+
+int convert_grid_f16(niv_model* m, cudaStream_t s) {
+    int64_t n = m->n_grid;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    f32_to_f16_kernel<<<(unsigned)blocks, 256, 0, s>>>(m->params, m->grid_f16, n);
+    NIV_CUDA(cudaGetLastError());
+    return NIV_OK;
+}
+
+void free_model(niv_model* m) {
+    if (!m) return;
+    cudaFree(m->params);
+    cudaFree(m->grid_f16);
+    cudaFree(m->mlp_plain);
+    cudaFree(m->mlp_tc);
+    cudaFree(m->stage);
+    delete m;
+}
+
+}  // namespace
+
+int niv_fail(int code, const std::string& msg) {
+    t_err = msg;
+    return code;
+}
+
+int niv_cuda_fail(cudaError_t e, const char* what) {
+    t_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? NIV_ERR_NOMEM : NIV_ERR_CUDA;
+}
+
+int* niv_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+        g_status[dev] = p;
+    }
+    return g_status[dev];
+}
+
+GridArgs niv_grid_args(const niv_model* m, const niv_query_params* p) {
+    GridArgs g;
+    memset(&g, 0, sizeof g);
+    g.dims = m->d.dims;
+    g.levels = m->d.levels;
+    g.feat = m->d.feat;
+    g.n_in = m->n_in;
+    g.hash_mask = (uint32_t)((1ull << m->d.log2_T) - 1ull);
+    g.prime_t = m->d.prime_t;
+    for (int l = 0; l < m->d.levels; ++l) {
+        g.res[l] = m->res[l];
+        g.offset[l] = (uint32_t)m->offset[l];
+        if (m->dense[l]) g.dense_mask |= 1u << l;
+    }
+    for (int k = 0; k < 3; ++k) {
+        g.aabb_min[k] = p->aabb_min[k];
+        g.inv_ext[k] = (float)(1.0 / ((double)p->aabb_max[k] - (double)p->aabb_min[k]));
+    }
+    g.t = p->t;
+    return g;
+}
+
+// Network packed for the plain kernel: [W1^T (n_in x W) | b1 | (W_l row-major | b_l) ... | W_out | b_out].
+int niv_pack_plain(niv_model* m, const float* src, cudaStream_t s) {
+    const int W = m->d.width, n_in = m->n_in;
+    std::vector<float> dst((size_t)m->mlp_plain_len);
+    size_t o = 0, i = 0;
+    for (int r = 0; r < n_in; ++r)
+        for (int c = 0; c < W; ++c) dst[o + (size_t)r * W + c] = src[i + (size_t)c * n_in + r];
+    o += (size_t)n_in * W;
+    i += (size_t)n_in * W;
+    for (int c = 0; c < W; ++c) dst[o++] = src[i++];
+    const size_t rest = (size_t)m->n_mlp - i;
+    memcpy(dst.data() + o, src + i, rest * sizeof(float));
+    NIV_CUDA(cudaMemcpyAsync(m->mlp_plain, dst.data(), sizeof(float) * dst.size(), cudaMemcpyHostToDevice, s));
+    NIV_CUDA(cudaStreamSynchronize(s));
+    return NIV_OK;
+}
+
+extern "C" {
+
+const char* niv_version(void) { return "niv 0.1 (sm_103a)"; }
+
+const char* niv_last_error(void) { return t_err.c_str(); }
+
+int niv_sync_status(niv_stream stream) {
+    NIV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int* w = niv_status_word();
+    if (!w) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
+    int v = 0;
+    NIV_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        NIV_CUDA(cudaMemset(w, 0, sizeof(int)));
+        char buf[96];
+        snprintf(buf, sizeof buf, "a kernel reported failure code %d", v);
+        return niv_fail(NIV_ERR_DEVICE, buf);
+    }
+    return NIV_OK;
+}
+
+int niv_create(const niv_model_desc* desc, niv_handle* out) {
+    if (!out) return niv_fail(NIV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = validate_desc(desc);
+    if (rc) return rc;
+    niv_model* m = new niv_model();
+    memset((void*)m, 0, sizeof(niv_model));
+    m->d = *desc;
+    const int64_t T = 1ll << desc->log2_T;
+    int64_t off = 0;
+    for (int l = 0; l < desc->levels; ++l) {
+        const double Nd = floor(desc->base * pow(desc->growth, (double)l));
+        if (Nd > (double)(1 << 20)) {
+            free_model(m);
+            return niv_fail(NIV_ERR_UNSUPPORTED, "level resolution above 2^20");
+        }
+        const int32_t N = (int32_t)Nd;
+        int64_t verts = 1;
+        for (int k = 0; k < desc->dims && verts <= T; ++k) verts *= (int64_t)(N + 1);
+        m->res[l] = N;
+        m->dense[l] = verts <= T;
+        m->offset[l] = off;
+        m->entries[l] = m->dense[l] ? verts : T;
+        off += m->entries[l];
+    }
+    m->total_entries = off;
+    m->n_in = desc->levels * desc->feat + desc->in_extra;
+    m->n_grid = off * desc->feat;
+    int64_t n = 0, k = m->n_in;
+    for (int h = 0; h < desc->n_hidden; ++h) {
+        n += (int64_t)desc->width * k + desc->width;
+        k = desc->width;
+    }
+    n += (int64_t)desc->out_dim * k + desc->out_dim;
+    m->n_mlp = n;
+    m->mlp_plain_len = n;
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e == cudaSuccess) e = cudaMalloc(&m->params, sizeof(float) * (m->n_grid + m->n_mlp));
+    if (e == cudaSuccess) e = cudaMalloc(&m->grid_f16, sizeof(__half) * m->n_grid);
+    if (e == cudaSuccess) e = cudaMalloc(&m->mlp_plain, sizeof(float) * m->mlp_plain_len);
+    if (e == cudaSuccess) e = cudaMemset(m->params, 0, sizeof(float) * (m->n_grid + m->n_mlp));
+    if (e == cudaSuccess) e = cudaMemset(m->grid_f16, 0, sizeof(__half) * m->n_grid);
+    if (e == cudaSuccess) e = cudaMemset(m->mlp_plain, 0, sizeof(float) * m->mlp_plain_len);
+    if (e != cudaSuccess) {
+        free_model(m);
+        return niv_cuda_fail(e, "niv_create allocation");
+    }
+    *out = m;
+    return NIV_OK;
+}
+
+int niv_destroy(niv_handle h) {
+    if (!h) return NIV_OK;
+    cudaDeviceSynchronize();
+    free_model(h);
+    return NIV_OK;
+}
+
+int niv_level_info(niv_handle h, int32_t level, int32_t* res, int32_t* dense, int64_t* first_entry,
+                   int64_t* entries) {
+    if (!h) return niv_fail(NIV_ERR_ARG, "handle is NULL");
+    if (level < 0 || level >= h->d.levels) return niv_fail(NIV_ERR_ARG, "level out of range");
+    if (res) *res = h->res[level];
+    if (dense) *dense = h->dense[level];
+    if (first_entry) *first_entry = h->offset[level];
+    if (entries) *entries = h->entries[level];
+    return NIV_OK;
+}
+
+int niv_param_count(niv_handle h, int64_t* n_grid_values, int64_t* n_mlp_values) {
+    if (!h) return niv_fail(NIV_ERR_ARG, "handle is NULL");
+    if (n_grid_values) *n_grid_values = h->n_grid;
+    if (n_mlp_values) *n_mlp_values = h->n_mlp;
+    return NIV_OK;
+}
+
+int niv_set_params(niv_handle h, const float* params, int64_t n, niv_stream stream) {
+    if (!h || !params) return niv_fail(NIV_ERR_ARG, "handle or params is NULL");
+    if (n != h->n_grid + h->n_mlp) return niv_fail(NIV_ERR_ARG, "parameter count mismatch");
+    int rc = check_device(h);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    NIV_CUDA(cudaMemcpyAsync(h->params, params, sizeof(float) * n, cudaMemcpyDefault, s));
+    rc = convert_grid_f16(h, s);
+    if (rc) return rc;
+    std::vector<float> mlp_host((size_t)h->n_mlp);
+    NIV_CUDA(cudaMemcpyAsync(mlp_host.data(), h->params + h->n_grid, sizeof(float) * h->n_mlp, cudaMemcpyDeviceToHost, s));
+    NIV_CUDA(cudaStreamSynchronize(s));
+    rc = niv_pack_plain(h, mlp_host.data(), s);
+    if (rc) return rc;
+    rc = niv_pack_tc(h, mlp_host.data(), s);
+    if (rc) return rc;
+    NIV_CUDA(cudaStreamSynchronize(s));
+    return NIV_OK;
+}
+
+int niv_get_params(niv_handle h, float* out, int64_t n, niv_stream stream) {
+    if (!h || !out) return niv_fail(NIV_ERR_ARG, "handle or out is NULL");
+    if (n != h->n_grid + h->n_mlp) return niv_fail(NIV_ERR_ARG, "parameter count mismatch");
+    int rc = check_device(h);
+    if (rc) return rc;
+    NIV_CUDA(cudaMemcpyAsync(out, h->params, sizeof(float) * n, cudaMemcpyDefault, (cudaStream_t)stream));
+    NIV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return NIV_OK;
+}
+
+int niv_query(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+              const niv_query_params* params, void* out_E, int32_t dtype_out, int32_t precision,
+              niv_stream stream) {
+    if (!h || !params) return niv_fail(NIV_ERR_ARG, "handle or params is NULL");
+    if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
+    if (n == 0) return NIV_OK;
+    if (!pos || !nrm || !out_E) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if (!aligned16(pos) || !aligned16(nrm) || !aligned16(out_E))
+        return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    if ((dtype_in != NIV_F32 && dtype_in != NIV_F16) || (dtype_out != NIV_F32 && dtype_out != NIV_F16))
+        return niv_fail(NIV_ERR_ARG, "record dtype must be NIV_F32 or NIV_F16");
+    for (int k = 0; k < 3; ++k)
+        if (!(params->aabb_max[k] > params->aabb_min[k])) return niv_fail(NIV_ERR_ARG, "empty aabb");
+    if (params->image_width < 0) return niv_fail(NIV_ERR_ARG, "image_width < 0");
+    int rc = check_device(h);
+    if (rc) return rc;
+    GridArgs g = niv_grid_args(h, params);
+    IoArgs io;
+    io.pos = pos;
+    io.nrm = nrm;
+    io.out = out_E;
+    io.n = n;
+    io.image_width = params->image_width;
+    io.in_f16 = dtype_in == NIV_F16;
+    io.out_f16 = dtype_out == NIV_F16;
+    switch (precision) {
+        case NIV_FP32: return niv_launch_query_fp32(h, g, io, (cudaStream_t)stream);
+        case NIV_FP16: return niv_launch_query_tc(h, g, io, precision, (cudaStream_t)stream);
+        default: return niv_fail(NIV_ERR_UNSUPPORTED, "precision not supported");
+    }
+}
+
+int niv_query_host(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+                   const niv_query_params* params, void* out_E, int32_t dtype_out, int32_t precision,
+                   niv_stream stream) {
+    if (!h) return niv_fail(NIV_ERR_ARG, "handle is NULL");
+    if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
+    if (n == 0) return NIV_OK;
+    if (!pos || !nrm || !out_E) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    int rc = check_device(h);
+    if (rc) return rc;
+    const size_t in_b = (size_t)n * (dtype_in == NIV_F16 ? 8 : 16);
+    const size_t out_b = (size_t)n * (dtype_out == NIV_F16 ? 8 : 16);
+    const size_t a_in = (in_b + 255) & ~(size_t)255, need = 2 * a_in + out_b;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->stage_bytes < need) {
+        NIV_CUDA(cudaStreamSynchronize(s));
+        cudaFree(h->stage);
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        NIV_CUDA(cudaMalloc(&h->stage, need));
+        h->stage_bytes = need;
+    }
+    char* base = (char*)h->stage;
+    NIV_CUDA(cudaMemcpyAsync(base, pos, in_b, cudaMemcpyHostToDevice, s));
+    NIV_CUDA(cudaMemcpyAsync(base + a_in, nrm, in_b, cudaMemcpyHostToDevice, s));
+    rc = niv_query(h, base, base + a_in, n, dtype_in, params, base + 2 * a_in, dtype_out, precision, stream);
+    if (rc) return rc;
+    NIV_CUDA(cudaMemcpyAsync(out_E, base + 2 * a_in, out_b, cudaMemcpyDeviceToHost, s));
+    NIV_CUDA(cudaStreamSynchronize(s));
+    return NIV_OK;
+}
+
+int niv_encode(niv_handle h, const void* pos, int64_t n, int32_t dtype_in, const niv_query_params* params,
+               float* out_enc, uint32_t* out_idx, niv_stream stream) {
+    if (!h || !params) return niv_fail(NIV_ERR_ARG, "handle or params is NULL");
+    if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
+    if (n == 0) return NIV_OK;
+    if (!pos) return niv_fail(NIV_ERR_ARG, "pos is NULL");
+    if (!aligned16(pos)) return niv_fail(NIV_ERR_ALIGN, "pos must be 16-byte aligned");
+    if (dtype_in != NIV_F32 && dtype_in != NIV_F16) return niv_fail(NIV_ERR_ARG, "bad dtype");
+    for (int k = 0; k < 3; ++k)
+        if (!(params->aabb_max[k] > params->aabb_min[k])) return niv_fail(NIV_ERR_ARG, "empty aabb");
+    int rc = check_device(h);
+    if (rc) return rc;
+    GridArgs g = niv_grid_args(h, params);
+    IoArgs io;
+    memset(&io, 0, sizeof io);
+    io.pos = pos;
+    io.n = n;
+    io.in_f16 = dtype_in == NIV_F16;
+    return niv_launch_encode(h, g, io, out_enc, out_idx, (cudaStream_t)stream);
+}
+
+int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out_rgba,
+              niv_stream stream) {
+    if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
+    if (n == 0) return NIV_OK;
+    if (!albedo || !direct || !E || !out_rgba) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if (!aligned16(albedo) || !aligned16(direct) || !aligned16(E) || !aligned16(out_rgba))
+        return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    return niv_launch_shade(albedo, direct, E, n, out_rgba, (cudaStream_t)stream);
+}
+
+}  // extern "C"

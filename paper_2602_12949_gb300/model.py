@@ -1,0 +1,173 @@
+"""Python face of the library: a model handle plus torch-tensor marshalling.
+
+Tensors are plain containers here (device memory and streams); every step of
+the query, shading, training and Monte Carlo paths runs in libniv's kernels.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib, ModelDesc, QueryParams
+
+PRECISIONS = {"fp32": _lib.NIV_FP32, "fp16": _lib.NIV_FP16, "fp8": _lib.NIV_FP8}
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _rec_dtype(t):
+    if t.dtype == torch.float16:
+        return _lib.NIV_F16
+    if t.dtype == torch.float32:
+        return _lib.NIV_F32
+    raise TypeError("records must be float16 or float32, got %s" % t.dtype)
+
+
+def _check_records(t, name):
+    if not isinstance(t, torch.Tensor) or t.dim() != 2 or t.shape[1] != 4 or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous [n][4] tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must live on the GPU (use query_host for host buffers)" % name)
+
+
+class NIVModel:
+    """One Neural Irradiance Volume on the current CUDA device."""
+
+    def __init__(self, dims=3, levels=16, feat=2, log2_T=17, base=16.0, growth=1.38, n_hidden=2, width=64,
+                 in_extra=None, out_dim=3, out_act=1, prime_t=0x9E3779B1):
+        if in_extra is None:
+            in_extra = 4 if dims == 4 else 3
+        self.desc = ModelDesc(dims, levels, feat, log2_T, float(base), float(growth), n_hidden, width, in_extra,
+                              out_dim, out_act, prime_t)
+        h = ctypes.c_void_p()
+        check(lib().niv_create(ctypes.byref(self.desc), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().niv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n_in(self):
+        return self.desc.levels * self.desc.feat + self.desc.in_extra
+
+    def param_count(self):
+        g, m = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().niv_param_count(self._h, ctypes.byref(g), ctypes.byref(m)))
+        return g.value, m.value
+
+    def level_info(self, level):
+        r, d, f, e = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().niv_level_info(self._h, level, ctypes.byref(r), ctypes.byref(d), ctypes.byref(f),
+                                   ctypes.byref(e)))
+        return {"res": r.value, "dense": d.value, "first_entry": f.value, "entries": e.value}
+
+    def layer_shapes(self):
+        shapes, k = [], self.n_in
+        for _ in range(self.desc.n_hidden):
+            shapes.append((self.desc.width, k))
+            k = self.desc.width
+        shapes.append((self.desc.out_dim, k))
+        return shapes
+
+    def set_params(self, params):
+        """Load the flat FP32 vector [grid | network] (numpy array or torch tensor, host or device)."""
+        if isinstance(params, np.ndarray):
+            params = np.ascontiguousarray(params, np.float32)
+            ptr, n = params.ctypes.data, params.size
+        else:
+            params = params.contiguous().float()
+            ptr, n = params.data_ptr(), params.numel()
+        check(lib().niv_set_params(self._h, ctypes.c_void_p(ptr), n, _stream()))
+
+    def get_params(self):
+        g, m = self.param_count()
+        out = np.empty(g + m, np.float32)
+        check(lib().niv_get_params(self._h, ctypes.c_void_p(out.ctypes.data), out.size, _stream()))
+        return out
+
+    @staticmethod
+    def query_params(aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), t=0.0, image_width=0):
+        return QueryParams((ctypes.c_float * 3)(*aabb_min), (ctypes.c_float * 3)(*aabb_max), float(t),
+                           int(image_width))
+
+    def query(self, pos, nrm, out=None, precision="fp16", aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0),
+              t=0.0, image_width=0, out_dtype=None, stream=None):
+        """E(x, n) for every record of device tensors pos, nrm ([n][4]); returns out ([n][4])."""
+        _check_records(pos, "pos")
+        _check_records(nrm, "nrm")
+        if pos.shape != nrm.shape or pos.dtype != nrm.dtype:
+            raise ValueError("pos and nrm must have the same shape and dtype")
+        if out is None:
+            out = torch.empty(pos.shape, dtype=out_dtype or pos.dtype, device=pos.device)
+        _check_records(out, "out")
+        if out.shape[0] != pos.shape[0]:
+            raise ValueError("out must have one record per query")
+        qp = self.query_params(aabb_min, aabb_max, t, image_width)
+        check(lib().niv_query(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                              pos.shape[0], _rec_dtype(pos), ctypes.byref(qp), ctypes.c_void_p(out.data_ptr()),
+                              _rec_dtype(out), PRECISIONS[precision], _stream(stream)))
+        return out
+
+    def query_host(self, pos, nrm, out=None, precision="fp16", aabb_min=(0.0, 0.0, 0.0),
+                   aabb_max=(1.0, 1.0, 1.0), t=0.0, image_width=0, stream=None):
+        """Same as query for host arrays (numpy or CPU tensors); copies in and out inside the call."""
+        to_np = (lambda a: a.numpy()) if isinstance(pos, torch.Tensor) else (lambda a: a)
+        p, n = np.ascontiguousarray(to_np(pos)), np.ascontiguousarray(to_np(nrm))
+        if p.ndim != 2 or p.shape[1] != 4 or p.shape != n.shape or p.dtype != n.dtype:
+            raise ValueError("pos and nrm must be matching [n][4] arrays")
+        dt = _lib.NIV_F16 if p.dtype == np.float16 else _lib.NIV_F32
+        if out is None:
+            out = np.empty(p.shape, p.dtype)
+        o = to_np(out) if isinstance(out, torch.Tensor) else out
+        odt = _lib.NIV_F16 if o.dtype == np.float16 else _lib.NIV_F32
+        qp = self.query_params(aabb_min, aabb_max, t, image_width)
+        check(lib().niv_query_host(self._h, ctypes.c_void_p(p.ctypes.data), ctypes.c_void_p(n.ctypes.data),
+                                   p.shape[0], dt, ctypes.byref(qp), ctypes.c_void_p(o.ctypes.data), odt,
+                                   PRECISIONS[precision], _stream(stream)))
+        return out
+
+    def encode(self, pos, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), t=0.0, want_idx=True, stream=None):
+        """(features [n][L*F] float32, corner indices [n][L][2^dims] int32 or None) for device records."""
+        _check_records(pos, "pos")
+        n = pos.shape[0]
+        L, F, nc = self.desc.levels, self.desc.feat, 1 << self.desc.dims
+        enc = torch.empty((n, L * F), dtype=torch.float32, device=pos.device)
+        idx = torch.empty((n, L, nc), dtype=torch.int32, device=pos.device) if want_idx else None
+        qp = self.query_params(aabb_min, aabb_max, t, 0)
+        check(lib().niv_encode(self._h, ctypes.c_void_p(pos.data_ptr()), n, _rec_dtype(pos), ctypes.byref(qp),
+                               ctypes.c_void_p(enc.data_ptr()),
+                               ctypes.c_void_p(idx.data_ptr() if idx is not None else 0), _stream(stream)))
+        return enc, idx
+
+
+def shade(albedo, direct, E, out=None, stream=None):
+    """rgba = (albedo * E / pi + direct, 1) on FP16 [n][4] device tensors."""
+    for t, name in ((albedo, "albedo"), (direct, "direct"), (E, "E")):
+        _check_records(t, name)
+        if t.dtype != torch.float16:
+            raise TypeError("%s must be float16" % name)
+    if out is None:
+        out = torch.empty_like(E)
+    check(lib().niv_shade(ctypes.c_void_p(albedo.data_ptr()), ctypes.c_void_p(direct.data_ptr()),
+                          ctypes.c_void_p(E.data_ptr()), E.shape[0], ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def sync_status(stream=None):
+    check(lib().niv_sync_status(_stream(stream)))

@@ -1,0 +1,170 @@
+"""GPU parity of the query path (through the C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from niv_inputs import init_params, uniform_queries
+from niv_inputs.configs import MODEL_C0, MODEL_C1, MODEL_C3, ROOM_MIN, ROOM_MAX, room_gbuffer
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel_err(got, ref):
+    """max |got - ref| / max(|ref|, 1e-3 max|ref|) -- relative error guarded near zero."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    return float(np.max(np.abs(got - ref) / den))
+
+
+@pytest.fixture(scope="module")
+def niv():
+    from paper_2602_12949_gb300.build import build
+    build()
+    import paper_2602_12949_gb300 as P
+    assert torch.cuda.is_available()
+    return P
+
+
+def make(P, spec, seed=0, bias_std=0.0):
+    m = P.NIVModel(**spec)
+    g, _ = m.param_count()
+    params = init_params(g, m.layer_shapes(), seed=seed, bias_std=bias_std)
+    m.set_params(params)
+    return m, params, oracle.Model(**spec)
+
+
+def test_param_layout_matches_oracle(niv):
+    for spec in (MODEL_C0, MODEL_C1, MODEL_C3):
+        m = niv.NIVModel(**spec)
+        om = oracle.Model(**spec)
+        L = oracle.layout(om)
+        g, n_mlp = m.param_count()
+        assert g == L["total"] * om.feat and n_mlp == oracle.mlp_param_count(om)
+        for l in range(om.levels):
+            info = m.level_info(l)
+            assert (info["res"], info["dense"], info["first_entry"], info["entries"]) == (
+                L["res"][l], L["dense"][l], L["offset"][l], L["entries"][l])
+        m.close()
+
+
+def test_set_get_params_roundtrip(niv):
+    m, params, _ = make(niv, MODEL_C0, seed=3)
+    np.testing.assert_array_equal(m.get_params(), params)
+    m.set_params(torch.from_numpy(params * 2).cuda())
+    np.testing.assert_array_equal(m.get_params(), params * 2)
+    m.close()
+
+
+@pytest.mark.parametrize("spec,n,kw", [
+    (MODEL_C0, 65536, {}),
+    (MODEL_C1, 4096 + 61, dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
+    (MODEL_C3, 4096 + 5, dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=0.37)),
+])
+def test_corner_indices_bit_exact(niv, spec, n, kw):
+    m, params, om = make(niv, spec, seed=1)
+    lo, hi = kw.get("aabb_min", (0, 0, 0)), kw.get("aabb_max", (1, 1, 1))
+    pos, _ = uniform_queries(n, seed=2, lo=lo, hi=hi)
+    enc, idx = m.encode(torch.from_numpy(pos).cuda(), **kw)
+    ref_enc, ref_idx, _ = oracle.encode(om, params, pos, lo, hi, kw.get("t", 0.0), want_corners=True)
+    np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), ref_idx)
+    np.testing.assert_allclose(enc.cpu().numpy(), ref_enc, rtol=0, atol=2e-8)
+    m.close()
+
+
+def test_fp32_query_config0_full(niv):
+    """Config 0: 65,536 FP32 queries, the plain path within 1e-5 max relative error of the FP64 oracle."""
+    m, params, om = make(niv, MODEL_C0, seed=0)
+    pos, nrm = uniform_queries(65536, seed=0)
+    ref = oracle.query(om, params, pos, nrm)
+    E = m.query(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda(), precision="fp32")
+    assert rel_err(E[:, :3].cpu().numpy(), ref) <= 1e-5
+    assert torch.all(E[:, 3] == 0)
+    m.close()
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 65536 + 77])
+def test_fp32_ragged_sizes_and_biases(niv, n):
+    m, params, om = make(niv, MODEL_C0, seed=5, bias_std=0.3)
+    pos, nrm = uniform_queries(n, seed=n)
+    ref = oracle.query(om, params, pos, nrm)
+    E = m.query(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda(), precision="fp32")
+    assert rel_err(E[:, :3].cpu().numpy(), ref) <= 1e-5
+    m.close()
+
+
+@pytest.mark.parametrize("spec", [dict(MODEL_C0, width=16), dict(MODEL_C0, width=32, n_hidden=1),
+                                  dict(MODEL_C0, feat=4, levels=4, n_hidden=4), dict(MODEL_C3, levels=6),
+                                  dict(MODEL_C0, feat=1, out_act=0)])
+def test_fp32_other_shapes(niv, spec):
+    m, params, om = make(niv, spec, seed=7, bias_std=0.1)
+    pos, nrm = uniform_queries(3000, seed=1)
+    ref = oracle.query(om, params, pos, nrm, t=0.6)
+    E = m.query(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda(), precision="fp32", t=0.6)
+    got = E[:, :3].cpu().numpy()
+    if spec.get("out_act", 1) == 1:
+        assert rel_err(got, ref) <= 1e-5
+    else:  # signed outputs cross zero: error relative to the output scale
+        assert np.max(np.abs(got - ref)) / np.abs(ref).max() <= 1e-5
+    m.close()
+
+
+def test_empty_query_is_noop(niv):
+    m, _, _ = make(niv, MODEL_C0)
+    z = torch.zeros((0, 4), device="cuda")
+    m.query(z, z, precision="fp32")
+    m.close()
+
+
+def test_misaligned_pointer_rejected(niv):
+    m, _, _ = make(niv, MODEL_C0)
+    buf = torch.zeros(4 * 129, device="cuda")
+    bad = buf[1:1 + 4 * 128].view(128, 4)
+    with pytest.raises(niv.NivError) as e:
+        m.query(bad, bad, precision="fp32")
+    assert e.value.code == -2
+    m.close()
+
+
+@pytest.fixture(scope="module")
+def gbuf1080():
+    return room_gbuffer(1920, 1080)
+
+
+def test_fp32_full_frame_1080p_sampled(niv, gbuf1080):
+    """Config-1 model on the full 1080p FP16 G-buffer, image traversal; 8192 sampled pixels vs the oracle."""
+    pos, nrm, _ = gbuf1080
+    m, params, om = make(niv, MODEL_C1, seed=0)
+    dpos, dnrm = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+    E = m.query(dpos, dnrm, precision="fp32", aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, image_width=1920,
+                out_dtype=torch.float32)
+    E_lin = m.query(dpos, dnrm, precision="fp32", aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, out_dtype=torch.float32)
+    assert torch.equal(E, E_lin)  # tile traversal changes nothing
+    pick = np.random.default_rng(0).choice(len(pos), 8192, replace=False)
+    ref = oracle.query(om, params, pos[pick].astype(np.float32), nrm[pick].astype(np.float32), ROOM_MIN, ROOM_MAX)
+    assert rel_err(E[pick, :3].cpu().numpy(), ref) <= 1e-5
+    m.close()
+
+
+def test_query_host_matches_device_query(niv):
+    m, params, om = make(niv, MODEL_C0, seed=2)
+    pos, nrm = uniform_queries(10000, seed=3)
+    dev = m.query(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda(), precision="fp32").cpu().numpy()
+    host = m.query_host(pos, nrm, precision="fp32")
+    np.testing.assert_array_equal(host, dev)
+    m.close()
+
+
+def test_shade_matches_oracle(niv):
+    rng = np.random.default_rng(0)
+    n = 100000 + 3
+    alb = rng.uniform(0.1, 0.9, (n, 4)).astype(np.float16)
+    E = rng.uniform(0.0, 4.0, (n, 4)).astype(np.float16)
+    D = rng.uniform(0.0, 2.0, (n, 4)).astype(np.float16)
+    out = niv.shade(*(torch.from_numpy(a).cuda() for a in (alb, D, E))).cpu().numpy()
+    ref = oracle.shade(alb[:, :3].astype(np.float64), E[:, :3].astype(np.float64), D[:, :3].astype(np.float64))
+    # one FP16 rounding of the result: half an ulp, 2^-11 relative
+    np.testing.assert_allclose(out[:, :3].astype(np.float64), ref, rtol=2.0 ** -11, atol=1e-7)
+    assert np.all(out[:, 3] == 1.0)
