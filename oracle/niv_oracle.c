@@ -235,7 +235,8 @@ static void net_input(const orc_desc* d, const double* enc, const float* nrm, fl
     x[ne + 0] = nrm[0];
     x[ne + 1] = nrm[1];
     x[ne + 2] = nrm[2];
-    if (d->in_extra == 4) x[ne + 3] = t;
+    /* the scene parameter enters clamped to [0, 1], as it does the grid's 4th axis */
+    if (d->in_extra == 4) x[ne + 3] = t < 0.0f ? 0.0 : (t > 1.0f ? 1.0 : (double)t);
 }
 
 /*

@@ -15,6 +15,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-DNIV_BUILD"]
+# Extra compiler flags (e.g. kernel tuning defines); empty by default.
+EXTRA = os.environ.get("NIV_NVCC_EXTRA", "").split()
 
 
 def _sources():
@@ -35,7 +37,7 @@ def _stale(target, inputs):
 def _compile(src, extra=()):
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
     if _stale(obj, [src] + _deps()):
-        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *EXTRA, *extra, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))

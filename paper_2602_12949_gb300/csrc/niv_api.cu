@@ -71,6 +71,11 @@ void free_model(niv_model* m) {
 
 }  // namespace
 
+int niv_env_int(const char* name, int dflt) {
+    const char* v = getenv(name);
+    return (v && *v) ? atoi(v) : dflt;
+}
+
 int niv_fail(int code, const std::string& msg) {
     t_err = msg;
     return code;

@@ -6,7 +6,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <string>
+#include <type_traits>
 
 #include "niv.h"
 
@@ -82,6 +86,9 @@ int* niv_status_word();
 
 GridArgs niv_grid_args(const niv_model* m, const niv_query_params* p);
 
+// Integer value of an environment variable (tuning and diagnostics), or dflt.
+int niv_env_int(const char* name, int dflt);
+
 // ---- kernel launchers (one per translation unit) ----
 int niv_launch_query_fp32(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s);
 int niv_launch_encode(const niv_model* m, const GridArgs& g, const IoArgs& io, float* enc, uint32_t* idx,
@@ -122,12 +129,161 @@ __device__ __forceinline__ uint32_t niv_vertex_index(bool dense, uint32_t stride
     return h & mask;
 }
 
-// Linear record index of thread slot `k` of tile `tile` (128-record tiles; 16 x 8 pixels for images).
+// Corner entries and multilinear weights of level l at normalised coordinate u
+// (Sec. 4.1), with the per-corner work factored: one cell per axis, per-axis index
+// terms (dense strides or hash products) combined per corner, weights as products
+// of per-axis factors.  Corner c has offset bit d along dimension d.
+template <int DIMS>
+__device__ __forceinline__ void niv_level_corners(const GridArgs& g, int l, const float* u, uint32_t* e,
+                                                  float* wc) {
+    constexpr int NC = 1 << DIMS;
+    const int32_t N = g.res[l];
+    const float fN = (float)N, fmax = (float)(N - 1);
+    uint32_t ci[DIMS];
+    float w1[DIMS], w0[DIMS];
+#pragma unroll
+    for (int d = 0; d < DIMS; ++d) {
+        const float s = __fmul_rn(u[d], fN);
+        const float fl = fminf(floorf(s), fmax);
+        ci[d] = (uint32_t)(int)fl;
+        w1[d] = __fsub_rn(s, fl);
+        w0[d] = 1.0f - w1[d];
+    }
+    {
+        float wh[NC / 2];
+        wh[0] = w0[1] * w0[2];
+        wh[1] = w1[1] * w0[2];
+        wh[2] = w0[1] * w1[2];
+        wh[3] = w1[1] * w1[2];
+        if (DIMS == 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                wh[(q + 4) % (NC / 2)] = wh[q] * w1[DIMS - 1];
+                wh[q] = wh[q] * w0[DIMS - 1];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NC / 2; ++q) {
+            wc[2 * q] = w0[0] * wh[q];
+            wc[2 * q + 1] = w1[0] * wh[q];
+        }
+    }
+    if ((g.dense_mask >> l) & 1u) {
+        const uint32_t S = (uint32_t)N + 1u, S2 = S * S;
+        uint32_t base = ci[2] * S2 + ci[1] * S + ci[0];
+        if (DIMS == 4) base += ci[DIMS - 1] * S2 * S;
+        uint32_t oh[NC / 2];
+        oh[0] = base;
+        oh[1] = base + S;
+        oh[2] = base + S2;
+        oh[3] = base + S2 + S;
+        if (DIMS == 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) oh[(q + 4) % (NC / 2)] = oh[q] + S2 * S;
+        }
+#pragma unroll
+        for (int q = 0; q < NC / 2; ++q) {
+            e[2 * q] = oh[q];
+            e[2 * q + 1] = oh[q] + 1u;
+        }
+    } else {
+        const uint32_t hy0 = ci[1] * NIV_PI2, hy1 = hy0 + NIV_PI2;
+        const uint32_t hz0 = ci[2] * NIV_PI3, hz1 = hz0 + NIV_PI3;
+        uint32_t hh[NC / 2];
+        hh[0] = hy0 ^ hz0;
+        hh[1] = hy1 ^ hz0;
+        hh[2] = hy0 ^ hz1;
+        hh[3] = hy1 ^ hz1;
+        if (DIMS == 4) {
+            const uint32_t ht0 = ci[DIMS - 1] * g.prime_t, ht1 = ht0 + g.prime_t;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                hh[(q + 4) % (NC / 2)] = hh[q] ^ ht1;
+                hh[q] = hh[q] ^ ht0;
+            }
+        }
+        const uint32_t x0 = ci[0], x1 = ci[0] + 1u, m = g.hash_mask;
+#pragma unroll
+        for (int q = 0; q < NC / 2; ++q) {
+            e[2 * q] = (x0 ^ hh[q]) & m;
+            e[2 * q + 1] = (x1 ^ hh[q]) & m;
+        }
+    }
+}
+
+// Raw feature words of the corners: F features of type TabT per entry.
+template <int F, typename TabT>
+struct NivRaw {
+    using T = typename std::conditional<
+        sizeof(TabT) == 2, typename std::conditional<F == 4, uint2, typename std::conditional<F == 2, uint32_t, unsigned short>::type>::type,
+        typename std::conditional<F == 4, float4, typename std::conditional<F == 2, float2, float>::type>::type>::type;
+};
+
+template <int NC, int F, typename TabT>
+__device__ __forceinline__ void niv_level_gather(const TabT* __restrict__ tab, const uint32_t* e,
+                                                 typename NivRaw<F, TabT>::T* raw) {
+    using R = typename NivRaw<F, TabT>::T;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) raw[c] = __ldg(reinterpret_cast<const R*>(tab) + e[c]);
+}
+
+__device__ __forceinline__ void niv_unpack(uint32_t r, float* f) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r));
+    f[0] = a.x;
+    f[1] = a.y;
+}
+__device__ __forceinline__ void niv_unpack(uint2 r, float* f) {
+    niv_unpack(r.x, f);
+    niv_unpack(r.y, f + 2);
+}
+__device__ __forceinline__ void niv_unpack(unsigned short r, float* f) { f[0] = __half2float(__ushort_as_half(r)); }
+__device__ __forceinline__ void niv_unpack(float r, float* f) { f[0] = r; }
+__device__ __forceinline__ void niv_unpack(float2 r, float* f) {
+    f[0] = r.x;
+    f[1] = r.y;
+}
+__device__ __forceinline__ void niv_unpack(float4 r, float* f) {
+    f[0] = r.x;
+    f[1] = r.y;
+    f[2] = r.z;
+    f[3] = r.w;
+}
+
+template <int NC, int F, typename R>
+__device__ __forceinline__ void niv_level_blend(const R* raw, const float* wc, float* acc) {
+#pragma unroll
+    for (int j = 0; j < F; ++j) acc[j] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        float f[F];
+        niv_unpack(raw[c], f);
+#pragma unroll
+        for (int j = 0; j < F; ++j) acc[j] = fmaf(wc[c], f[j], acc[j]);
+    }
+}
+
+// Interpolated features of level l (corners, gathers, blend).
+template <int DIMS, int F, typename TabT>
+__device__ __forceinline__ void niv_encode_level(const GridArgs& g, const TabT* __restrict__ grid, int l,
+                                                 const float* u, float* acc) {
+    constexpr int NC = 1 << DIMS;
+    uint32_t e[NC];
+    float wc[NC];
+    niv_level_corners<DIMS>(g, l, u, e, wc);
+    typename NivRaw<F, TabT>::T raw[NC];
+    niv_level_gather<NC, F, TabT>(grid + (size_t)g.offset[l] * F, e, raw);
+    niv_level_blend<NC, F>(raw, wc, acc);
+}
+
+// Linear record index of thread slot `k` of tile `tile` (128-record tiles).  For images a tile
+// is a 16 x 8 pixel block and each warp of it an 8 x 4 sub-block, so the 32 queries of a warp
+// are as compact on screen (and so in the scene) as possible.
 __device__ __forceinline__ int64_t niv_record_of(int64_t tile, int k, int64_t n, int32_t width) {
     if (width <= 0) return tile * 128 + k;
     int64_t tiles_x = (width + 15) / 16;
     int64_t ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    int64_t px = tx * 16 + (k & 15), py = ty * 8 + (k >> 4);
+    const int w = k >> 5, lane = k & 31;
+    int64_t px = tx * 16 + (w & 1) * 8 + (lane & 7), py = ty * 8 + (w >> 1) * 4 + (lane >> 3);
     if (px >= width) return n;  // outside the image: no record
     return py * width + px;
 }

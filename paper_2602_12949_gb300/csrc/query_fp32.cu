@@ -40,41 +40,8 @@ __global__ void __launch_bounds__(kThreads) query_fp32_kernel(GridArgs g, IoArgs
 
         // ---- encoding ----
         for (int l = 0; l < g.levels; ++l) {
-            const int32_t N = g.res[l];
-            const bool dense = (g.dense_mask >> l) & 1u;
-            uint32_t ci[DIMS];
-            float cw[DIMS];
-#pragma unroll
-            for (int d = 0; d < DIMS; ++d) niv_cell(u[d], N, ci[d], cw[d]);
-            const float* tab = grid + (size_t)g.offset[l] * F;
             float acc[F];
-#pragma unroll
-            for (int j = 0; j < F; ++j) acc[j] = 0.0f;
-#pragma unroll
-            for (int c = 0; c < (1 << DIMS); ++c) {
-                uint32_t v[DIMS];
-                float wc = 1.0f;
-#pragma unroll
-                for (int d = 0; d < DIMS; ++d) {
-                    const int bit = (c >> d) & 1;
-                    v[d] = ci[d] + bit;
-                    wc *= bit ? cw[d] : 1.0f - cw[d];
-                }
-                const uint32_t e = niv_vertex_index<DIMS>(dense, (uint32_t)N + 1u, v, g.hash_mask, g.prime_t);
-                if (F == 4) {
-                    const float4 t4 = __ldg(reinterpret_cast<const float4*>(tab) + e);
-                    acc[0] = fmaf(wc, t4.x, acc[0]);
-                    acc[1 % F] = fmaf(wc, t4.y, acc[1 % F]);
-                    acc[2 % F] = fmaf(wc, t4.z, acc[2 % F]);
-                    acc[3 % F] = fmaf(wc, t4.w, acc[3 % F]);
-                } else if (F == 2) {
-                    const float2 t2 = __ldg(reinterpret_cast<const float2*>(tab) + e);
-                    acc[0] = fmaf(wc, t2.x, acc[0]);
-                    acc[1 % F] = fmaf(wc, t2.y, acc[1 % F]);
-                } else {
-                    acc[0] = fmaf(wc, __ldg(tab + e), acc[0]);
-                }
-            }
+            niv_encode_level<DIMS, F, float>(g, grid, l, u, acc);
 #pragma unroll
             for (int j = 0; j < F; ++j) s_x[(l * F + j) * kThreads + k] = acc[j];
         }
@@ -182,6 +149,7 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
     const int rows = g.n_in > W ? g.n_in : W;
     const size_t smem = (size_t)(stride + rows * kThreads) * sizeof(float);
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
     int dev = 0, sms = 0, per_sm = 0;
     NIV_CUDA(cudaGetDevice(&dev));
     NIV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -1,21 +1,30 @@
 // Fused query path on the 5th-generation tensor cores (sm_103a).
 //
-// One CTA of 128 threads owns a tile of 128 G-buffer records at a time (a 16 x 8
+// A warpgroup (128 threads) owns a tile of 128 G-buffer records at a time (a 16 x 8
 // pixel block for images) and walks tiles persistently.  Per tile:
 //   1. every thread encodes its own record (Sec. 4.1: per level the cell, the
-//      2^d corner indices -- dense or hashed --, FP16 feature gathers served from
+//      2^d corner entries -- dense or hashed --, FP16 feature gathers served from
 //      L2, multilinear weights in FP32) and writes its row of the network input
-//      [features, n, (t), 0-pad] as FP16 into a shared-memory tile laid out in the
-//      tensor core's canonical K-major format;
+//      [features | n, (t), 1 | 0-pad] as FP16, in 16-byte chunks, into a shared-memory
+//      tile laid out in the tensor core's canonical K-major format (the constant 1
+//      multiplies the first layer's bias, stored as an extra weight column);
 //   2. one thread issues tcgen05.mma (M = 128 records, N = width, K = 16 per
-//      instruction) with the weights resident in shared memory; the FP32
+//      instruction) against the weights resident in shared memory; the FP32
 //      accumulator lives in tensor memory (TMEM);
-//   3. each warp reads its 32 rows back with tcgen05.ld, adds the bias, applies
-//      ReLU and writes the next layer's FP16 input tile; repeat per hidden layer;
-//   4. the 3-wide output layer (192 multiply-adds per record) and softplus run in
-//      FP32 on the CUDA cores straight from the last accumulator, and E is stored.
-// Every wait on the MMA-completion barrier is bounded (2 s); on expiry the kernel
-// records a failure in the status word, releases its TMEM and returns.
+//   3. each warp reads its 32 rows back with tcgen05.ld, adds the bias (FP32),
+//      rounds to FP16, applies ReLU on packed halves and writes the next layer's
+//      input tile; repeat per hidden layer;
+//   4. the output layer (N = 16, three live columns) also runs on the tensor
+//      core; bias, softplus in FP32 and the store of E finish the record.
+// Parameters are FP16 (weights, biases, grid features: all parameters in half
+// precision, Table 1), accumulation FP32.  Every wait on the MMA-completion
+// barrier is bounded (2 s); on expiry the kernel records a failure in the status
+// word, releases its TMEM and returns.
+//
+// Tuning knobs (compile-time): NIV_TC_WG warpgroups per CTA sharing one copy of the
+// weights, NIV_TC_ILP levels whose gathers are in flight together, NIV_TC_MINB the
+// launch-bounds residency target, NIV_TC_OUT_FMA output layer on the CUDA cores.
+#include <string.h>
 #include <vector>
 
 #include "niv_internal.cuh"
@@ -23,9 +32,25 @@
 
 namespace {
 
-constexpr int kT = 128;
+#ifndef NIV_TC_WG
+#define NIV_TC_WG 1
+#endif
+#ifndef NIV_TC_ILP
+#define NIV_TC_ILP 1
+#endif
+#ifndef NIV_TC_MINB
+#define NIV_TC_MINB 8
+#endif
+constexpr int kT = 128;          // rows per tile = threads per warpgroup
+constexpr int kWG = NIV_TC_WG;   // warpgroups (independent tile pipelines) per CTA
+constexpr int kILP = NIV_TC_ILP; // levels whose gathers are in flight together (1 or 2)
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
-constexpr int kHdr = 128;  // barrier + TMEM address slot at the start of dynamic shared memory
+#ifndef NIV_TC_OUT_FMA
+#define NIV_TC_OUT_FMA 0
+#endif
+constexpr int kHdr = 128;    // barriers + TMEM address slot at the start of dynamic shared memory
+constexpr int kNO = 16;      // rows of the output-layer tile (3 live)
+constexpr bool kOutFma = NIV_TC_OUT_FMA != 0;  // output layer on the CUDA cores instead of the tensor core
 
 // Byte offset of element (row r, column k) of a K-major tile with K columns, built from
 // 8-row x 16-byte core matrices: adjacent along K 128 B apart, along rows (K/8)*128 B apart.
@@ -34,89 +59,109 @@ __host__ __device__ __forceinline__ uint32_t core_off(int r, int k, int K) {
 }
 
 struct TcLayout {
-    int32_t K1, W, n_hidden, pad;
-    uint32_t w1, wh, bias, wout, total;  // byte offsets inside the packed network
+    int32_t K1, W, n_hidden, col_extra;  // col_extra: tile column of n.x (features end before it)
+    int32_t col_one;                     // tile column holding the constant 1 (first-layer bias)
+    uint32_t w1, wh, wo, bias, wout, total;  // byte offsets inside the packed network
 };
 
-template <int DIMS, int F>
-__device__ __forceinline__ void encode_level(const GridArgs& g, const __half* __restrict__ grid16, int l,
-                                             const float* u, float* acc) {
-    const int32_t N = g.res[l];
-    const bool dense = (g.dense_mask >> l) & 1u;
-    uint32_t ci[DIMS];
-    float cw[DIMS];
-#pragma unroll
-    for (int d = 0; d < DIMS; ++d) niv_cell(u[d], N, ci[d], cw[d]);
-    uint32_t e[1 << DIMS];
-    float wc[1 << DIMS];
-#pragma unroll
-    for (int c = 0; c < (1 << DIMS); ++c) {
-        uint32_t v[DIMS];
-        float w = 1.0f;
-#pragma unroll
-        for (int d = 0; d < DIMS; ++d) {
-            const int bit = (c >> d) & 1;
-            v[d] = ci[d] + bit;
-            w *= bit ? cw[d] : 1.0f - cw[d];
-        }
-        e[c] = niv_vertex_index<DIMS>(dense, (uint32_t)N + 1u, v, g.hash_mask, g.prime_t);
-        wc[c] = w;
-    }
-#pragma unroll
-    for (int j = 0; j < F; ++j) acc[j] = 0.0f;
-    if (F == 2) {
-        const uint32_t* tab = reinterpret_cast<const uint32_t*>(grid16) + g.offset[l];
-        uint32_t raw[1 << DIMS];
-#pragma unroll
-        for (int c = 0; c < (1 << DIMS); ++c) raw[c] = __ldg(tab + e[c]);
-#pragma unroll
-        for (int c = 0; c < (1 << DIMS); ++c) {
-            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&raw[c]));
-            acc[0] = fmaf(wc[c], f.x, acc[0]);
-            acc[1 % F] = fmaf(wc[c], f.y, acc[1 % F]);
-        }
-    } else if (F == 4) {
-        const uint2* tab = reinterpret_cast<const uint2*>(grid16) + g.offset[l];
-        uint2 raw[1 << DIMS];
-#pragma unroll
-        for (int c = 0; c < (1 << DIMS); ++c) raw[c] = __ldg(tab + e[c]);
-#pragma unroll
-        for (int c = 0; c < (1 << DIMS); ++c) {
-            const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw[c].x));
-            const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw[c].y));
-            acc[0] = fmaf(wc[c], a.x, acc[0]);
-            acc[1 % F] = fmaf(wc[c], a.y, acc[1 % F]);
-            acc[2 % F] = fmaf(wc[c], b.x, acc[2 % F]);
-            acc[3 % F] = fmaf(wc[c], b.y, acc[3 % F]);
-        }
-    } else {
-        const __half* tab = grid16 + g.offset[l];
-#pragma unroll
-        for (int c = 0; c < (1 << DIMS); ++c) acc[0] = fmaf(wc[c], __half2float(tab[e[c]]), acc[0]);
-    }
+__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
 }
 
-template <int DIMS, int F>
-__global__ void __launch_bounds__(kT) query_tc_f16_kernel(GridArgs g, IoArgs io, const __half* __restrict__ grid16,
-                                                           const uint8_t* __restrict__ packed, TcLayout lay,
-                                                           int out_act, int64_t n_tiles, uint32_t tmem_cols,
-                                                           int* __restrict__ status) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + 8);
-    uint8_t* s_net = smem + kHdr;
-    uint8_t* s_act = s_net + ((lay.total + 1023u) & ~1023u);
+__device__ __forceinline__ uint32_t relu_half2(uint32_t x) {
+    __half2 h = __hmax2(*reinterpret_cast<__half2*>(&x), __float2half2_rn(0.0f));
+    return *reinterpret_cast<uint32_t*>(&h);
+}
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Issue one layer: sum over K/16 steps of act x W^T into TMEM, then signal `bar`.
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t act, uint32_t w, uint32_t K, uint32_t idesc,
+                                            uint32_t bar) {
+    const uint32_t sbo = (K >> 3) * 128u;
+    for (uint32_t ks = 0; ks < K / 16; ++ks)
+        tc::mma_f16(tmem, tc::smem_desc(act + ks * 256u, 128u, sbo), tc::smem_desc(w + ks * 256u, 128u, sbo), idesc,
+                    ks > 0 ? 1u : 0u);
+    tc::mma_commit(bar);
+}
+
+// Encode levels [l0, l0 + G) of one record into one 16-byte chunk of FP16 features,
+// kILP levels' gathers in flight at a time.
+template <int DIMS, int F>
+__device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const __half* __restrict__ grid16, int l0,
+                                              const float* u) {
+    constexpr int NC = 1 << DIMS, G = 8 / F;
+    using R = typename NivRaw<F, __half>::T;
+    uint32_t wd[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int q = 0; q < G; q += kILP) {
+        const int la = l0 + q, lb = l0 + q + 1;
+        const bool has_a = la < g.levels, has_b = kILP == 2 && (q + 1 < G) && lb < g.levels;
+        uint32_t ea[NC], eb[NC];
+        float wa[NC], wb[NC];
+        R ra[NC], rb[NC];
+        if (has_a) niv_level_corners<DIMS>(g, la, u, ea, wa);
+        if (has_b) niv_level_corners<DIMS>(g, lb, u, eb, wb);
+        if (has_a) niv_level_gather<NC, F, __half>(grid16 + (size_t)g.offset[la] * F, ea, ra);
+        if (has_b) niv_level_gather<NC, F, __half>(grid16 + (size_t)g.offset[lb] * F, eb, rb);
+        float acc[F];
+#pragma unroll
+        for (int h = 0; h < kILP; ++h) {
+            if (h == 0 ? !has_a : !has_b) continue;
+            niv_level_blend<NC, F>(h == 0 ? ra : rb, h == 0 ? wa : wb, acc);
+            const int qq = q + h;
+            if (F == 1) {
+                const uint32_t v = (uint32_t)__half_as_ushort(__float2half_rn(acc[0]));
+                wd[qq >> 1] |= (qq & 1) ? (v << 16) : v;
+            } else if (F == 2) {
+                wd[qq % 4] = pack_half2(acc[0], acc[1 % F]);
+            } else {
+                wd[(2 * qq) % 4] = pack_half2(acc[0], acc[1 % F]);
+                wd[(2 * qq + 1) % 4] = pack_half2(acc[2 % F], acc[3 % F]);
+            }
+        }
+    }
+    return make_uint4(wd[0], wd[1], wd[2], wd[3]);
+}
+
+__device__ __forceinline__ void group_sync(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory"); }
+
+// kWG independent warpgroups per CTA; each owns a 128-row tile pipeline (activation tile,
+// mbarrier, named barrier, 64 TMEM columns) and all share the weights in shared memory.
+template <int DIMS, int F>
+__global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(GridArgs g, IoArgs io,
+                                                                const __half* __restrict__ grid16,
+                                                                const uint8_t* __restrict__ packed, TcLayout lay,
+                                                                int out_act, int64_t n_tiles, uint32_t tmem_cols,
+                                                                int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);  // one per warpgroup
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + 64);
+    uint8_t* s_net = smem + kHdr;
+    const uint32_t act_bytes = (uint32_t)kT * (uint32_t)(lay.K1 > lay.W ? lay.K1 : lay.W) * 2u;
+
+    const int wg = threadIdx.x / kT, tid = threadIdx.x % kT, warp = tid >> 5;
+    uint8_t* s_act = s_net + ((lay.total + 127u) & ~127u) + wg * act_bytes;
     const int K1 = lay.K1, W = lay.W;
 
-    for (uint32_t i = tid; i < lay.total / 16; i += kT)
+    for (uint32_t i = threadIdx.x; i < lay.total / 16; i += kT * kWG)
         reinterpret_cast<uint4*>(s_net)[i] = __ldg(reinterpret_cast<const uint4*>(packed) + i);
-    if (tid == 0) {
-        tc::mbar_init(s_bar, 1);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kWG; ++i) tc::mbar_init(s_bar + i, 1);
         tc::fence_mbar_init();
     }
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
         tc::tmem_alloc(tc::smem_u32(s_tmem), tmem_cols);
         tc::tmem_relinquish();
     }
@@ -125,18 +170,19 @@ __global__ void __launch_bounds__(kT) query_tc_f16_kernel(GridArgs g, IoArgs io,
     __syncthreads();
     tc::fence_after_sync();
 
-    const uint32_t tmem = *s_tmem;
+    const uint32_t tmem = *s_tmem + (uint32_t)wg * (tmem_cols / kWG);
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint32_t bar = tc::smem_u32(s_bar);
+    const uint32_t bar = tc::smem_u32(s_bar + wg);
     const uint32_t act_a = tc::smem_u32(s_act), net_a = tc::smem_u32(s_net);
-    const uint32_t idesc = tc::idesc_f16(128, W);
-    const float* s_bias = reinterpret_cast<const float*>(s_net + lay.bias);
-    const float* s_wout = reinterpret_cast<const float*>(s_net + lay.wout);
-    const int LF = g.levels * F;
+    const float* s_bias = reinterpret_cast<const float*>(s_net + lay.bias);  // layers 1.. and b_out
+    const float* s_wout = reinterpret_cast<const float*>(s_net + lay.wout);  // FP32 [3][W]
+    const uint32_t idesc_h = tc::idesc_f16(128, W), idesc_o = tc::idesc_f16(128, kNO);
+    const int L = g.levels;
+    constexpr int G = 8 / F;
     uint32_t phase = 0;
     bool ok = true;
 
-    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    for (int64_t tile = (int64_t)blockIdx.x * kWG + wg; tile < n_tiles && ok; tile += (int64_t)gridDim.x * kWG) {
         const int64_t r = niv_record_of(tile, tid, io.n, io.image_width);
         const bool valid = r < io.n;
         const int64_t rr = valid ? r : 0;
@@ -148,47 +194,29 @@ __global__ void __launch_bounds__(kT) query_tc_f16_kernel(GridArgs g, IoArgs io,
         u[2] = niv_unit(p.z, g.aabb_min[2], g.inv_ext[2]);
         u[3] = fminf(fmaxf(g.t, 0.0f), 1.0f);
 
-        // ---- 1. encoding -> FP16 input row ----
-        for (int l = 0; l < g.levels; ++l) {
-            float acc[F];
-            encode_level<DIMS, F>(g, grid16, l, u, acc);
-            if (F == 2) {
-                *reinterpret_cast<__half2*>(s_act + core_off(tid, 2 * l, K1)) = __floats2half2_rn(acc[0], acc[1 % F]);
-            } else if (F == 4) {
-                __half2 a = __floats2half2_rn(acc[0], acc[1 % F]), b = __floats2half2_rn(acc[2 % F], acc[3 % F]);
-                uint2 w2;
-                w2.x = *reinterpret_cast<uint32_t*>(&a);
-                w2.y = *reinterpret_cast<uint32_t*>(&b);
-                *reinterpret_cast<uint2*>(s_act + core_off(tid, 4 * l, K1)) = w2;
-            } else {
-                *reinterpret_cast<__half*>(s_act + core_off(tid, l, K1)) = __float2half_rn(acc[0]);
-            }
+        // ---- 1. encoding -> FP16 input row, one 16-byte chunk per G levels ----
+        for (int l0 = 0; l0 < L; l0 += G)
+            *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid16, l0, u);
+        {   // [n.x, n.y, n.z, (t), 1, 0, ...]: the 1 multiplies the first layer's bias column
+            const bool has_t = g.n_in > L * F + 3;
+            const uint32_t one = (uint32_t)__half_as_ushort(__float2half_rn(1.0f));
+            uint4 c = make_uint4(pack_half2(nv.x, nv.y), has_t ? pack_half2(nv.z, u[3]) : (pack_half2(nv.z, 0.0f) & 0xFFFFu) | (one << 16), 0u, 0u);
+            if (has_t) c.z = one;
+            *reinterpret_cast<uint4*>(s_act + core_off(tid, lay.col_extra, K1)) = c;
         }
-        for (int k = LF; k < K1; ++k) {
-            float x = 0.0f;
-            if (k == LF) x = nv.x;
-            else if (k == LF + 1) x = nv.y;
-            else if (k == LF + 2) x = nv.z;
-            else if (k == LF + 3 && g.n_in > LF + 3) x = u[3];
-            *reinterpret_cast<__half*>(s_act + core_off(tid, k, K1)) = __float2half_rn(x);
-        }
+        for (int k = lay.col_extra + 8; k < K1; k += 8)
+            *reinterpret_cast<uint4*>(s_act + core_off(tid, k, K1)) = make_uint4(0u, 0u, 0u, 0u);
         tc::fence_async_smem();
         tc::fence_before_sync();
-        __syncthreads();
+        group_sync(wg);
 
-        // ---- 2..4. network ----
-        int K = K1;
-        uint32_t w_off = lay.w1;
-        for (int layer = 0; layer < lay.n_hidden; ++layer) {
+        // ---- 2, 3. hidden layers (the last one feeds the output layer) ----
+        uint32_t K = (uint32_t)K1, w_off = lay.w1;
+        float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
+        for (int layer = 0; layer < lay.n_hidden && ok; ++layer) {
             if (tid == 0) {
                 tc::fence_after_sync();
-                const uint32_t sbo = (uint32_t)(K >> 3) * 128u;
-                for (int ks = 0; ks < K / 16; ++ks) {
-                    const uint64_t ad = tc::smem_desc(act_a + ks * 256u, 128u, sbo);
-                    const uint64_t bd = tc::smem_desc(net_a + w_off + ks * 256u, 128u, sbo);
-                    tc::mma_f16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
-                }
-                tc::mma_commit(bar);
+                issue_layer(tmem, act_a, net_a + w_off, K, idesc_h, bar);
             }
             if (!tc::mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
                 atomicExch(status, 1);
@@ -197,76 +225,122 @@ __global__ void __launch_bounds__(kT) query_tc_f16_kernel(GridArgs g, IoArgs io,
             }
             phase ^= 1u;
             tc::fence_after_sync();
-            const float* bias = s_bias + layer * W;
-            if (layer < lay.n_hidden - 1) {
-                // hidden epilogue: relu(acc + b) -> FP16 input tile of the next layer (K = W)
-                for (int c = 0; c < W / 16; ++c) {
-                    float v[16];
-                    tc::tmem_ld16(tmem_row + (uint32_t)(c * 16), v);
-                    uint32_t h[8];
+            const float* bias = s_bias + (layer - 1) * W;  // layer 0's bias came through the MMA
+            const bool last = layer == lay.n_hidden - 1;
+            if (kOutFma && last) {
+                z0 = s_bias[(lay.n_hidden - 1) * W + 0];
+                z1 = s_bias[(lay.n_hidden - 1) * W + 1];
+                z2 = s_bias[(lay.n_hidden - 1) * W + 2];
+            }
+            for (int c = 0; c < W / 16; ++c) {
+                float v[16];
+                tc::tmem_ld16(tmem_row + (uint32_t)(c * 16), v);
+                if (layer > 0) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        __half2 hh = __floats2half2_rn(fmaxf(v[2 * j] + bias[c * 16 + 2 * j], 0.0f),
-                                                       fmaxf(v[2 * j + 1] + bias[c * 16 + 2 * j + 1], 0.0f));
-                        h[j] = *reinterpret_cast<uint32_t*>(&hh);
-                    }
-                    *reinterpret_cast<uint4*>(s_act + core_off(tid, c * 16, W)) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4*>(s_act + core_off(tid, c * 16 + 8, W)) = make_uint4(h[4], h[5], h[6], h[7]);
+                    for (int j = 0; j < 16; ++j) v[j] += bias[c * 16 + j];
                 }
-                tc::fence_async_smem();
-                tc::fence_before_sync();
-                __syncthreads();
-                w_off = (layer == 0) ? lay.wh : w_off + (uint32_t)(W * W * 2);
-                K = W;
-            } else {
-                // output layer on the CUDA cores: z = W_out relu(acc + b) + b_out, E = softplus(z)
-                float z0 = s_wout[3 * W + 0], z1 = s_wout[3 * W + 1], z2 = s_wout[3 * W + 2];
-                for (int c = 0; c < W / 16; ++c) {
-                    float v[16];
-                    tc::tmem_ld16(tmem_row + (uint32_t)(c * 16), v);
+                if (kOutFma && last) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int o = c * 16 + j;
-                        const float a = fmaxf(v[j] + bias[o], 0.0f);
+                        const float a = fmaxf(v[j], 0.0f);
                         z0 = fmaf(s_wout[o], a, z0);
                         z1 = fmaf(s_wout[W + o], a, z1);
                         z2 = fmaf(s_wout[2 * W + o], a, z2);
                     }
+                } else {
+                    uint32_t h[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = relu_half2(pack_half2(v[2 * j], v[2 * j + 1]));
+                    *reinterpret_cast<uint4*>(s_act + core_off(tid, c * 16, W)) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4*>(s_act + core_off(tid, c * 16 + 8, W)) = make_uint4(h[4], h[5], h[6], h[7]);
                 }
-                if (out_act == 1) {
-                    z0 = niv_softplus(z0);
-                    z1 = niv_softplus(z1);
-                    z2 = niv_softplus(z2);
-                }
-                if (valid) niv_store_rec(io.out, r, z0, z1, z2, io.out_f16);
-                tc::fence_before_sync();
             }
+            if (!(kOutFma && last)) {
+                tc::fence_async_smem();
+                tc::fence_before_sync();
+                group_sync(wg);
+            }
+            w_off = layer == 0 ? lay.wh : w_off + (uint32_t)(W * W * 2);
+            K = (uint32_t)W;
         }
+        if (!ok) break;
+
+        // ---- 4. output layer (tensor core, N = 16, or CUDA cores above) and softplus ----
+        if (!kOutFma) {
+            if (tid == 0) {
+                tc::fence_after_sync();
+                issue_layer(tmem, act_a, net_a + lay.wo, (uint32_t)W, idesc_o, bar);
+            }
+            if (!tc::mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
+                atomicExch(status, 1);
+                ok = false;
+                break;
+            }
+            phase ^= 1u;
+            tc::fence_after_sync();
+            float z[4];
+            tmem_ld4(tmem_row, z);
+            const float* bo = s_bias + (lay.n_hidden - 1) * W;
+            z0 = z[0] + bo[0];
+            z1 = z[1] + bo[1];
+            z2 = z[2] + bo[2];
+        }
+        if (out_act == 1) {
+            z0 = niv_softplus(z0);
+            z1 = niv_softplus(z1);
+            z2 = niv_softplus(z2);
+        }
+        if (valid) niv_store_rec(io.out, r, z0, z1, z2, io.out_f16);
+        tc::fence_before_sync();
+        group_sync(wg);  // the next tile's encoder overwrites the activation tile
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+    if (threadIdx.x < 32) tc::tmem_dealloc(*s_tmem, tmem_cols);
+}
+
+size_t tc_smem_bytes(const TcLayout& lay) {
+    const int kmax = lay.K1 > lay.W ? lay.K1 : lay.W;
+    return (size_t)kHdr + ((lay.total + 127u) & ~127u) + (size_t)kWG * kT * kmax * 2;
 }
 
 template <int DIMS, int F>
 int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
     const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
     auto kern = query_tc_f16_kernel<DIMS, F>;
-    const int kmax = lay->K1 > lay->W ? lay->K1 : lay->W;
-    const size_t smem = kHdr + ((lay->total + 1023u) & ~1023u) + (size_t)kT * kmax * 2;
+    const size_t smem = tc_smem_bytes(*lay);
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
+    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+    int dev = 0, sms = 0;
     NIV_CUDA(cudaGetDevice(&dev));
     NIV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    NIV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, smem));
-    const uint32_t cols = lay->W <= 32 ? 32u : 64u;
+    // Residency from the register and shared-memory budgets (the occupancy API reports a
+    // single CTA per SM for kernels that allocate tensor memory).
+    cudaFuncAttributes fa;
+    NIV_CUDA(cudaFuncGetAttributes(&fa, kern));
+    int smem_per_sm = 0, regs_per_sm = 0;
+    NIV_CUDA(cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    NIV_CUDA(cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    const int by_smem = smem_per_sm / (int)(smem + 1024);  // 1 KB per CTA reserved by the driver
+    const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 1;
+    const int by_regs = regs_per_sm / (kT * kWG * regs);
+    int per_sm = by_smem < by_regs ? by_smem : by_regs;
+    const uint32_t cols = (lay->W <= 32 ? 32u : 64u) * kWG;
+    const int forced = niv_env_int("NIV_TC_BLOCKS_PER_SM", 0);
+    if (forced > 0) per_sm = forced;
     if (per_sm > (int)(512 / cols)) per_sm = (int)(512 / cols);  // never oversubscribe TMEM
     if (per_sm < 1) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core query kernel does not fit on an SM");
+    if (niv_env_int("NIV_VERBOSE", 0))
+        fprintf(stderr, "niv: fp16 query: smem %zu B, regs %d, smem %d/SM, regs %d/SM, launching %d/SM\n", smem,
+                fa.numRegs, by_smem, by_regs, per_sm);
     int* status = niv_status_word();
     if (!status) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
     const int64_t tiles = niv_tile_count_host(io.n, io.image_width);
-    const int64_t blocks = tiles < (int64_t)sms * per_sm ? tiles : (int64_t)sms * per_sm;
-    kern<<<(unsigned)blocks, kT, smem, s>>>(g, io, m->grid_f16, m->mlp_tc, *lay, m->d.out_act, tiles, cols, status);
+    const int64_t need = (tiles + kWG - 1) / kWG;
+    const int64_t blocks = need < (int64_t)sms * per_sm ? need : (int64_t)sms * per_sm;
+    kern<<<(unsigned)blocks, kT * kWG, smem, s>>>(g, io, m->grid_f16, m->mlp_tc, *lay, m->d.out_act, tiles, cols,
+                                                 status);
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }
@@ -284,44 +358,58 @@ int by_feat(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_
 }  // namespace
 
 // Pack the network for the tensor-core kernel from host FP32 parameters:
-// [W1 fp16 tile (W x K1) | hidden fp16 tiles (W x W) | biases fp32 | W_out fp32 (3 x W) + b_out].
+// [W1 (W x K1, FP16 tile) | hidden W (W x W) ... | W_out (16 x W) | biases of layers 1.. and
+// b_out (FP32) | W_out (FP32, 3 x W)].  Input i of the network sits in tile column i for
+// the encoded features and in column col_extra + (i - L*F) for n and t, col_extra =
+// round_up(L*F, 8); the first layer's bias sits in column col_one, which the kernel
+// fills with 1 in every input row.
 int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s) {
-    const int W = m->d.width, nh = m->d.n_hidden, n_in = m->n_in;
-    const int K1 = (n_in + 15) & ~15;
+    const int W = m->d.width, nh = m->d.n_hidden, n_in = m->n_in, LF = m->d.levels * m->d.feat;
     TcLayout lay;
     memset(&lay, 0, sizeof lay);
-    lay.K1 = K1;
+    lay.col_extra = (LF + 7) & ~7;
+    lay.col_one = lay.col_extra + m->d.in_extra;
+    lay.K1 = (lay.col_one + 1 + 15) & ~15;
     lay.W = W;
     lay.n_hidden = nh;
     auto up = [](uint32_t x) { return (x + 127u) & ~127u; };
     lay.w1 = 0;
-    lay.wh = up(lay.w1 + (uint32_t)(W * K1 * 2));
-    lay.bias = up(lay.wh + (uint32_t)((nh - 1) * W * W * 2));
-    lay.wout = up(lay.bias + (uint32_t)(nh * W * 4));
-    lay.total = up(lay.wout + (uint32_t)((3 * W + 3) * 4));
+    lay.wh = up(lay.w1 + (uint32_t)(W * lay.K1 * 2));
+    lay.wo = up(lay.wh + (uint32_t)((nh - 1) * W * W * 2));
+    lay.bias = up(lay.wo + (uint32_t)(kNO * W * 2));
+    lay.wout = up(lay.bias + (uint32_t)(((nh - 1) * W + 4) * 4));
+    lay.total = up(lay.wout + (uint32_t)(3 * W * 4));
     static_assert(sizeof(TcLayout) <= sizeof(((niv_model*)0)->tc_layout), "layout slot too small");
     memcpy(m->tc_layout, &lay, sizeof lay);
     std::vector<uint8_t> buf(lay.total, 0);
-    auto put_tile = [&](uint32_t base, const float* Wsrc, int rows, int cols, int K) {
-        for (int r = 0; r < rows; ++r)
-            for (int k = 0; k < cols; ++k) {
-                __half h = __float2half_rn(Wsrc[(size_t)r * cols + k]);
-                memcpy(&buf[base + core_off(r, k, K)], &h, 2);
-            }
+    auto put = [&](uint32_t base, int r, int k, int K, float v) {
+        __half h = __float2half_rn(v);
+        memcpy(&buf[base + core_off(r, k, K)], &h, 2);
     };
-    const float* p = mlp_host;
     float* bias = reinterpret_cast<float*>(&buf[lay.bias]);
-    put_tile(lay.w1, p, W, n_in, K1);
+    float* wout = reinterpret_cast<float*>(&buf[lay.wout]);
+    auto h16 = [](float v) { return __half2float(__float2half_rn(v)); };  // FP16-stored parameters
+    const float* p = mlp_host;
+    for (int r = 0; r < W; ++r)
+        for (int i = 0; i < n_in; ++i) put(lay.w1, r, i < LF ? i : lay.col_extra + (i - LF), lay.K1, p[(size_t)r * n_in + i]);
     p += (size_t)W * n_in;
-    memcpy(bias, p, sizeof(float) * W);
+    for (int r = 0; r < W; ++r) put(lay.w1, r, lay.col_one, lay.K1, p[r]);
     p += W;
     for (int h = 1; h < nh; ++h) {
-        put_tile(lay.wh + (uint32_t)((h - 1) * W * W * 2), p, W, W, W);
+        const uint32_t base = lay.wh + (uint32_t)((h - 1) * W * W * 2);
+        for (int r = 0; r < W; ++r)
+            for (int k = 0; k < W; ++k) put(base, r, k, W, p[(size_t)r * W + k]);
         p += (size_t)W * W;
-        memcpy(bias + h * W, p, sizeof(float) * W);
+        for (int r = 0; r < W; ++r) bias[(h - 1) * W + r] = h16(p[r]);
         p += W;
     }
-    memcpy(&buf[lay.wout], p, sizeof(float) * (3 * W + 3));
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < W; ++k) {
+            put(lay.wo, r, k, W, p[(size_t)r * W + k]);
+            wout[r * W + k] = h16(p[(size_t)r * W + k]);
+        }
+    p += 3 * W;
+    for (int r = 0; r < 3; ++r) bias[(nh - 1) * W + r] = h16(p[r]);
     if (m->mlp_tc_bytes < lay.total) {
         cudaFree(m->mlp_tc);
         m->mlp_tc = nullptr;
@@ -336,7 +424,8 @@ int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s) {
 
 int niv_launch_query_tc(const niv_model* m, const GridArgs& g, const IoArgs& io, int precision, cudaStream_t s) {
     if (precision != NIV_FP16) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core path: precision not supported");
-    if (m->n_in > 64) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core path needs levels*feat + in_extra <= 64");
+    const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
+    if (lay->K1 > 128) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core path needs a network input of <= 120 values");
     return m->d.dims == 4 ? by_feat<4>(m, g, io, s) : by_feat<3>(m, g, io, s);
 }
 
