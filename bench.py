@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOP_PER_QUERY = {"c1": 2 * (35 * 64 + 64 * 64 + 64 * 3)}  # 13,056: network multiply-adds x 2
+METRIC = "ms/frame @1080p + Gqueries/s: FP16 fused vs FP32 plain at stated err vs FP64"
 GBUF_BYTES_PER_QUERY = 18  # 12 B of FP16 position/normal in, 6 B of FP16 E out (algorithmic)
 WORKLOAD = ("config1-1080p: seeded 10 m room (24 spheres, 8 boxes, sphere emitter) ray-cast to a "
             "1920x1080 FP16 G-buffer; model 16 levels x 2 features, base 16, growth 1.38, T=2^17, "
@@ -108,6 +109,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _profiled_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if the
+    kernel sources are unchanged since that capture; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "niv_query_fp16_1080p.md")
+    srcs = ["query_tc.cu", "niv_internal.cuh", "tc_ptx.cuh"]
+    try:
+        text = open(path).read()
+        rec = dict(l.split(":", 1) for l in text.splitlines()
+                   if l.startswith(("traffic_bytes_per_launch:", "source_sha256_16:")))
+        h = hashlib.sha256()
+        for f in srcs:
+            with open(os.path.join(ROOT, "paper_2602_12949_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] != rec["source_sha256_16"].strip():
+            return None
+        return int(rec["traffic_bytes_per_launch"].strip())
+    except Exception:
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -150,7 +172,7 @@ def run_reference(a):
     value = sample * a.steps / tot / 1e9
     cores = _oracle_threads()
     line = {
-        "impl": "reference", "metric": "Gqueries/s (ms/frame @1080p beside it)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "Gqueries/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * tot / a.steps, "ms_per_frame": 1e3 * (w * h) / (value * 1e9),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -253,8 +275,9 @@ def main():
     mean_ms = statistics.mean(ms)
     flop = FLOP_PER_QUERY["c1"] * npx
     achieved = flop / (mean_ms * 1e-3) / 1e12
+    traffic = _profiled_traffic() if (a.precision == "fp16" and a.res == "1080p") else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["tensor"], "unit": "TFLOP/s",
-                "frac": achieved / peaks["tensor"], "traffic": None,
+                "frac": achieved / peaks["tensor"], "traffic": traffic,
                 "peak_source": "%s bf16 burst (fp16 dense rate equal)" % peaks["src"],
                 "hbm_achieved_gbs": GBUF_BYTES_PER_QUERY * npx / (mean_ms * 1e-3) / 1e9}
 
@@ -283,9 +306,7 @@ def main():
                             "max_abs_normalised": float(np.max(np.abs(got32 - ref)) / np.abs(ref).max())}
 
     line = {
-        "metric": "Gqueries/s (ms/frame @1080p beside it): %s fused vs FP32 plain, error vs FP64 oracle" %
-                  a.precision.upper(),
-        "value": value, "unit": "Gqueries/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "metric": METRIC, "value": value, "unit": "Gqueries/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_step, "ms_per_frame": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "fp8": "e4m3"}[a.precision],
         "data": "synthetic",
