@@ -167,6 +167,35 @@ NIV_API int niv_query_host(niv_handle h, const void* pos, const void* nrm, int64
                    niv_stream stream);
 
 /*
+ * Largest n accepted by niv_query_host_noalloc: the number of records its fixed
+ * staging area holds.
+ */
+#define NIV_NOALLOC_MAX_RECORDS 65536
+
+/*
+ * niv_query_host for callers that must not have the library allocate device
+ * memory, e.g. a real-time render loop that fixes its GPU memory budget at
+ * start-up and forbids allocation while frames are in flight, or a plug-in whose
+ * host application owns every device allocation.  The paper has no counterpart:
+ * this is an integration variant of the query.
+ *
+ * Same arguments and results as niv_query_host (host buffers in and out,
+ * precision NIV_FP32 or NIV_FP16, synchronises `stream`), but the records are
+ * staged in a fixed file-scope device array of NIV_NOALLOC_MAX_RECORDS records
+ * (about 3 MiB, held by every GPU that loads the library until the process exits)
+ * instead of a library allocation.  No cudaMalloc or cudaFree is called.
+ *  - n > NIV_NOALLOC_MAX_RECORDS: NIV_ERR_ARG with a message, nothing runs.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any stream
+ *    capture begins.
+ *  - Every call shares the one array, which keeps the last call's contents; calls
+ *    whose work overlaps on the GPU race with each other, so serialise them.
+ */
+NIV_API int niv_query_host_noalloc(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+                                   const niv_query_params* params, void* out_E, int32_t dtype_out,
+                                   int32_t precision, niv_stream stream);
+
+/*
  * Encoding only (Sec. 4.1), for inspection and parity checks: for each of the n
  * position records, out_enc (device float32 [n][levels*feat], nullable)
  * receives the interpolated level features in FP32 from the FP32 master grid,

@@ -96,7 +96,9 @@ int niv_launch_encode(const niv_model* m, const GridArgs& g, const IoArgs& io, f
 int niv_launch_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out, cudaStream_t s);
 int niv_pack_plain(niv_model* m, const float* mlp_host, cudaStream_t s);
 int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s);
-int niv_launch_query_tc(const niv_model* m, const GridArgs& g, const IoArgs& io, int precision, cudaStream_t s);
+// status: device word for kernel-side failures (nullptr = this device's library status word).
+int niv_launch_query_tc(const niv_model* m, const GridArgs& g, const IoArgs& io, int precision, cudaStream_t s,
+                        int* status = nullptr);
 
 // ---- device helpers shared by the query kernels ----
 

@@ -306,7 +306,7 @@ size_t tc_smem_bytes(const TcLayout& lay) {
 }
 
 template <int DIMS, int F>
-int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
+int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s, int* status) {
     const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
     auto kern = query_tc_f16_kernel<DIMS, F>;
     const size_t smem = tc_smem_bytes(*lay);
@@ -334,7 +334,7 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
     if (niv_env_int("NIV_VERBOSE", 0))
         fprintf(stderr, "niv: fp16 query: smem %zu B, regs %d, smem %d/SM, regs %d/SM, launching %d/SM\n", smem,
                 fa.numRegs, by_smem, by_regs, per_sm);
-    int* status = niv_status_word();
+    if (!status) status = niv_status_word();
     if (!status) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
     const int64_t tiles = niv_tile_count_host(io.n, io.image_width);
     const int64_t need = (tiles + kWG - 1) / kWG;
@@ -346,11 +346,11 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
 }
 
 template <int DIMS>
-int by_feat(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
+int by_feat(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s, int* status) {
     switch (m->d.feat) {
-        case 1: return launch<DIMS, 1>(m, g, io, s);
-        case 2: return launch<DIMS, 2>(m, g, io, s);
-        case 4: return launch<DIMS, 4>(m, g, io, s);
+        case 1: return launch<DIMS, 1>(m, g, io, s, status);
+        case 2: return launch<DIMS, 2>(m, g, io, s, status);
+        case 4: return launch<DIMS, 4>(m, g, io, s, status);
     }
     return niv_fail(NIV_ERR_UNSUPPORTED, "feat must be 1, 2 or 4");
 }
@@ -422,11 +422,12 @@ int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s) {
     return NIV_OK;
 }
 
-int niv_launch_query_tc(const niv_model* m, const GridArgs& g, const IoArgs& io, int precision, cudaStream_t s) {
+int niv_launch_query_tc(const niv_model* m, const GridArgs& g, const IoArgs& io, int precision, cudaStream_t s,
+                        int* status) {
     if (precision != NIV_FP16) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core path: precision not supported");
     const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
     if (lay->K1 > 128) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core path needs a network input of <= 120 values");
-    return m->d.dims == 4 ? by_feat<4>(m, g, io, s) : by_feat<3>(m, g, io, s);
+    return m->d.dims == 4 ? by_feat<4>(m, g, io, s, status) : by_feat<3>(m, g, io, s, status);
 }
 
 // ---- tensor-core operand-layout self-test ----
