@@ -184,6 +184,69 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def _time_launches(fn, steps, warmup, flush, stream):
+    """Mean device time (ms) of fn() over `steps` launches, L2 flushed before each one."""
+    import torch
+    from paper_2602_12949_gb300 import sync_status
+    for _ in range(warmup):
+        fn()
+    sync_status()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s, e in evs:
+        flush.zero_()
+        s.record(stream)
+        fn()
+        e.record(stream)
+    torch.cuda.synchronize()
+    sync_status()
+    return statistics.mean(s.elapsed_time(e) for s, e in evs)
+
+
+def _more_workloads(a, dev, flush, stream, steps=10, warmup=3):
+    """Beside the headline: the config-1 model at 4K, the 4-D config-3 model at 4K in FP8 /
+    FP16 / FP32 (t drawn from the seed per frame), and shading at 1080p and 4K."""
+    import torch
+    from paper_2602_12949_gb300 import NIVModel, shade
+    from niv_inputs import init_params
+    from niv_inputs.configs import MODEL_C1, MODEL_C3, ROOM_MIN, ROOM_MAX, room_gbuffer
+    res = {}
+    w, h = 3840, 2160
+    pos, nrm, alb = room_gbuffer(w, h)
+    npx = w * h
+    dpos, dnrm = torch.from_numpy(pos).to(dev), torch.from_numpy(nrm).to(dev)
+    out16 = torch.empty((npx, 4), dtype=torch.float16, device=dev)
+    out32 = torch.empty((npx, 4), dtype=torch.float32, device=dev)
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, image_width=w)
+    m1 = NIVModel(**MODEL_C1)
+    g, _ = m1.param_count()
+    m1.set_params(init_params(g, m1.layer_shapes(), seed=0))
+    r = {}
+    for prec, o in (("fp16", out16), ("fp32", out32)):
+        ms = _time_launches(lambda: m1.query(dpos, dnrm, out=o, precision=prec, **kw), steps, warmup, flush, stream)
+        r[prec] = {"ms_per_frame": ms, "gqueries_per_s": npx / (ms * 1e-3) / 1e9}
+    res["config1_4k"] = r
+    m1.close()
+    t = float(np.random.default_rng(0).random())  # per-frame scene parameter from the seed
+    m3 = NIVModel(**MODEL_C3)
+    g, _ = m3.param_count()
+    m3.set_params(init_params(g, m3.layer_shapes(), seed=0))
+    m3.fp8_calibrate(dpos[::31].contiguous(), dnrm[::31].contiguous(), aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=t)
+    r = {"t": t}
+    for prec, o in (("fp8", out16), ("fp16", out16), ("fp32", out32)):
+        ms = _time_launches(lambda: m3.query(dpos, dnrm, out=o, precision=prec, t=t, **kw), steps, warmup, flush,
+                            stream)
+        r[prec] = {"ms_per_frame": ms, "gqueries_per_s": npx / (ms * 1e-3) / 1e9}
+    res["config3_4k"] = r
+    m3.close()
+    dalb = torch.from_numpy(alb).to(dev)
+    direct = torch.rand((npx, 4), device=dev, generator=torch.Generator(device=dev).manual_seed(0)).half()
+    rgba = torch.empty_like(out16)
+    ms = _time_launches(lambda: shade(dalb, direct, out16, out=rgba), steps, warmup, flush, stream)
+    res["shade_4k"] = {"ms": ms, "gb_per_s": 32 * npx / (ms * 1e-3) / 1e9}
+    return res
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -252,6 +315,7 @@ def main():
         ms32 = timed("fp32", out32, max(5, a.steps // 2), 3)
         extra["fp32_plain"] = {"ms_per_frame": statistics.mean(ms32),
                                "gqueries_per_s": npx / (statistics.mean(ms32) * 1e-3) / 1e9}
+        extra["more"] = _more_workloads(a, dev, flush, stream)
 
     # e2e: host buffers through niv_query_host (H2D + kernel + D2H inside the call)
     hp = torch.from_numpy(pos).pin_memory().numpy()

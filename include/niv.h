@@ -167,6 +167,24 @@ NIV_API int niv_query_host(niv_handle h, const void* pos, const void* nrm, int64
                    niv_stream stream);
 
 /*
+ * Calibrate the E4M3 network path (NIV_FP8).  Runs the FP32 network over the n
+ * device records pos/nrm ([n][4], dtype_in) and takes, for every matrix product,
+ * the amax of its FP32 input; the activation scale is s_a = 2^ceil(log2(amax/448))
+ * (1 if amax = 0).  Weight scales s_w = 2^ceil(log2(amax|W|/448)) per layer.  Packs
+ * e4m3(W / s_w) for the tensor cores.  Must be called again after niv_set_params.
+ * Synchronises `stream`.  NIV_ERR_UNSUPPORTED for width 16.
+ */
+NIV_API int niv_fp8_calibrate(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+                              const niv_query_params* params, niv_stream stream);
+
+/*
+ * The scales of the last calibration, count = n_hidden + 1 entries each (one per
+ * matrix product; entry 0 is the network input): activation scale, weight scale
+ * and the measured activation amax.  Host pointers, any may be NULL.
+ */
+NIV_API int niv_fp8_get_scales(niv_handle h, float* s_act, float* s_w, float* amax, int32_t count);
+
+/*
  * Largest n accepted by niv_query_host_noalloc: the number of records its fixed
  * staging area holds.
  */
@@ -215,14 +233,15 @@ NIV_API int niv_shade(const void* albedo, const void* direct, const void* E, int
               niv_stream stream);
 
 /*
- * Diagnostic (no counterpart in the paper): one 128 x 64 x 32 FP16 tensor-core
- * product of fixed small-integer operands, A[m][k] = (3m + 5k) mod 7 - 3 and
+ * Diagnostic (no counterpart in the paper): one 128 x 64 x K tensor-core product
+ * of fixed small-integer operands, A[m][k] = (3m + 5k) mod 7 - 3 and
  * B[n][k] = (5n + 3k) mod 5 - 2, written to out (device float32 [128][64],
- * D = A B^T, exact).  swap_strides = 1 exchanges the two stride fields of the
- * operand descriptors (a layout-convention probe that stays inside the operands).
+ * D = A B^T, exact).  mode 0: FP16 operands, K = 32; mode 1: the same with the
+ * two stride fields of the operand descriptors exchanged (a layout-convention
+ * probe that stays inside the operands); mode 2: E4M3 operands, K = 64.
  * Asynchronous; a timeout of the completion wait is reported by niv_sync_status.
  */
-NIV_API int niv_selftest_mma(int32_t swap_strides, float* out, niv_stream stream);
+NIV_API int niv_selftest_mma(int32_t mode, float* out, niv_stream stream);
 
 #ifdef __cplusplus
 }

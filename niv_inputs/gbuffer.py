@@ -4,11 +4,41 @@ This stands in for the rasterisation pass that produces the G-buffer in an
 engine: per pixel it returns the first-hit world position, the unit surface
 normal and the surface albedo.  Pixels are in row-major order, row 0 at the top.
 """
+import ctypes
 import math
+import os
+import subprocess
 
 import numpy as np
 
 from .scenes import CAMERA_POS, SPHERE_LEN, BOX_LEN
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_C_LIB = None
+
+
+def _c_raycaster():
+    """The C version of the ray cast (raycast.c, same rules), compiled on first use; None if gcc fails."""
+    global _C_LIB
+    if _C_LIB is None:
+        src = os.path.join(_HERE, "raycast.c")
+        so = os.path.join(_HERE, "libraycast.so")
+        try:
+            if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+                tmp = so + ".tmp%d" % os.getpid()
+                base = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", src, "-o", tmp, "-lm"]
+                try:
+                    subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+                except subprocess.CalledProcessError:
+                    subprocess.run(base, check=True, capture_output=True)
+                os.replace(tmp, so)
+            lib = ctypes.CDLL(so)
+            lib.niv_raycast.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double] + [ctypes.c_void_p] * 5
+            lib.niv_raycast.restype = None
+            _C_LIB = lib
+        except (OSError, subprocess.CalledProcessError):
+            _C_LIB = False
+    return _C_LIB or None
 
 
 def camera_rays(width, height, vfov_deg=60.0, origin=CAMERA_POS):
@@ -85,8 +115,23 @@ def _cast_chunk(scene, o, d):
     return pos, nrm, alb, hit_any
 
 
-def raycast_gbuffer(scene, width, height, vfov_deg=60.0, chunk=1 << 20):
-    """Return float64 ``(pos[n][3], nrm[n][3], albedo[n][3], hit[n])`` for a ``width x height`` frame."""
+def raycast_gbuffer(scene, width, height, vfov_deg=60.0, chunk=1 << 20, impl="auto"):
+    """Return float64 ``(pos[n][3], nrm[n][3], albedo[n][3], hit[n])`` for a ``width x height`` frame.
+
+    impl: "c" (raycast.c), "numpy", or "auto" (C when it compiles, else numpy).
+    """
+    lib = _c_raycaster() if impl in ("auto", "c") else None
+    if impl == "c" and lib is None:
+        raise RuntimeError("C ray caster unavailable")
+    if lib is not None:
+        n = width * height
+        pos, nrm, alb = (np.zeros((n, 3)) for _ in range(3))
+        hit = np.zeros(n, np.uint8)
+        blob = np.ascontiguousarray(scene.blob(), np.float32)
+        origin = np.asarray(CAMERA_POS, np.float64)
+        lib.niv_raycast(blob.ctypes.data, width, height, float(vfov_deg), origin.ctypes.data, pos.ctypes.data,
+                        nrm.ctypes.data, alb.ctypes.data, hit.ctypes.data)
+        return pos, nrm, alb, hit.astype(bool)
     o, d = camera_rays(width, height, vfov_deg)
     n = len(d)
     pos = np.empty((n, 3))

@@ -104,6 +104,10 @@ def lib():
         L.orc_e4m3.restype = d
         L.orc_e4m3_array.argtypes = [vp, i64, vp]
         L.orc_e4m3_array.restype = None
+        L.orc_fp8_scale.argtypes = [d]
+        L.orc_fp8_scale.restype = d
+        L.orc_fp8_act_amax.argtypes = [P(Desc), vp, vp, vp, i64, vp, vp, f, vp]
+        L.orc_query_fp8.argtypes = [P(Desc), vp, vp, vp, vp, i64, vp, vp, f, vp]
         L.orc_philox4x32_10.argtypes = [vp, vp, vp]
         L.orc_philox4x32_10.restype = None
         L.orc_mc_irradiance.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, u64, u64, ctypes.c_int, vp, vp]
@@ -224,6 +228,32 @@ def e4m3(x):
     out = np.zeros_like(x)
     lib().orc_e4m3_array(_p(x), x.size, _p(out))
     return out
+
+
+def fp8_scale(amax):
+    """Power-of-two E4M3 scale 2^ceil(log2(amax / 448))."""
+    return lib().orc_fp8_scale(float(amax))
+
+
+def fp8_act_amax(model, params, pos4, nrm4, aabb_min=(0, 0, 0), aabb_max=(1, 1, 1), t=0.0):
+    """amax of each matrix product's input (network input, then each hidden layer's output)."""
+    out = np.zeros(model.n_hidden + 1)
+    rc = lib().orc_fp8_act_amax(ctypes.byref(model.cdesc()), _p(_f64(params)), _p(_f32(pos4)), _p(_f32(nrm4)),
+                                len(pos4), _p(_f32(aabb_min)), _p(_f32(aabb_max)), float(t), _p(out))
+    if rc:
+        raise ValueError("orc_fp8_act_amax failed")
+    return out
+
+
+def query_fp8(model, params, s_act, pos4, nrm4, aabb_min=(0, 0, 0), aabb_max=(1, 1, 1), t=0.0):
+    """E(x, n) of the E4M3 network path with activation scales s_act (one per matrix product)."""
+    pos4, nrm4 = _f32(pos4), _f32(nrm4)
+    E = np.zeros((len(pos4), model.out_dim))
+    rc = lib().orc_query_fp8(ctypes.byref(model.cdesc()), _p(_f64(params)), _p(_f64(s_act)), _p(pos4), _p(nrm4),
+                             len(pos4), _p(_f32(aabb_min)), _p(_f32(aabb_max)), float(t), _p(E))
+    if rc:
+        raise ValueError("orc_query_fp8 failed")
+    return E
 
 
 def philox(ctr, key):

@@ -428,3 +428,111 @@ void orc_e4m3_array(const double* x, int64_t n, double* out)
 {
     for (int64_t i = 0; i < n; ++i) out[i] = orc_e4m3(x[i]);
 }
+
+/* ------------------------------------------------------------------------
+ * FP8 (E4M3) network path.  Reading of "FP8 E4M3 with per-layer scales" (the
+ * paper runs FP16; the FP8 form is an extension): every matrix product takes
+ * E4M3 operands with one power-of-two scale per operand and layer,
+ *   s = 2^ceil(log2(amax / 448)),
+ * so that scaling is exact.  Weights: s_w from amax|W| of the layer.
+ * Activations: s_a from the amax of the layer's FP32 input over a calibration
+ * batch (the unquantised network).  Layer l computes
+ *   z = (sum_i e4m3(W/s_w)[o][i] * e4m3(a/s_a)[i]) * s_w * s_a + b,
+ * ReLU on hidden layers, softplus on the output.  Biases stay in FP32.
+ * ------------------------------------------------------------------------ */
+
+/* 2^ceil(log2(amax / 448)) (1 when amax is 0) */
+double orc_fp8_scale(double amax)
+{
+    if (!(amax > 0.0)) return 1.0;
+    int e;
+    double m = frexp(amax / 448.0, &e); /* amax/448 = m * 2^e, m in [0.5, 1) */
+    return m == 0.5 ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+}
+
+/*
+ * Per-layer input amax of the unquantised network over n records:
+ * amax[0] for the network input, amax[l] for the input of matrix l (l = 1..n_hidden).
+ */
+int orc_fp8_act_amax(const orc_desc* d, const double* params, const float* pos4, const float* nrm4, int64_t n,
+                     const float* aabb_min, const float* aabb_max, float t, double* amax)
+{
+    orc_layout_t L;
+    if (fill_layout(d, &L)) return -1;
+    const double* mlp = params + L.total * d->feat;
+    const int n_in = orc_net_inputs(d), layers = d->n_hidden + 1;
+    for (int l = 0; l < layers; ++l) amax[l] = 0.0;
+    double* z_all = (double*)malloc(sizeof(double) * ORC_MAX_LAYERS * ORC_MAX_WIDTH);
+    double* a_all = (double*)malloc(sizeof(double) * ORC_MAX_LAYERS * ORC_MAX_WIDTH);
+    for (int64_t q = 0; q < n; ++q) {
+        float u[ORC_MAX_DIMS];
+        double enc[ORC_MAX_LEVELS * 8], x[ORC_MAX_LEVELS * 8 + 8], E[8];
+        normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
+        encode_point(d, &L, params, u, enc, NULL, NULL);
+        net_input(d, enc, nrm4 + 4 * q, t, x);
+        mlp_forward(d, mlp, x, z_all, a_all, E);
+        for (int i = 0; i < n_in; ++i) amax[0] = fabs(x[i]) > amax[0] ? fabs(x[i]) : amax[0];
+        for (int l = 1; l < layers; ++l)
+            for (int o = 0; o < d->width; ++o) {
+                double a = a_all[(l - 1) * ORC_MAX_WIDTH + o];
+                amax[l] = a > amax[l] ? a : amax[l];
+            }
+    }
+    free(z_all);
+    free(a_all);
+    return 0;
+}
+
+/*
+ * FP8 query with the activation scales s_act[0..n_hidden] given (as computed from
+ * orc_fp8_act_amax); weight scales are derived here from the parameters.
+ */
+int orc_query_fp8(const orc_desc* d, const double* params, const double* s_act, const float* pos4,
+                  const float* nrm4, int64_t n, const float* aabb_min, const float* aabb_max, float t, double* Eout)
+{
+    orc_layout_t L;
+    if (fill_layout(d, &L)) return -1;
+    const double* mlp = params + L.total * d->feat;
+    const int n_in = orc_net_inputs(d), layers = d->n_hidden + 1;
+    double s_w[ORC_MAX_LAYERS];
+    {
+        const double* p = mlp;
+        int k_in = n_in;
+        for (int l = 0; l < layers; ++l) {
+            int n_out = l == layers - 1 ? d->out_dim : d->width;
+            double amax = 0.0;
+            for (int64_t i = 0; i < (int64_t)n_out * k_in; ++i) amax = fabs(p[i]) > amax ? fabs(p[i]) : amax;
+            s_w[l] = orc_fp8_scale(amax);
+            p += (int64_t)n_out * k_in + n_out;
+            k_in = n_out;
+        }
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) {
+        float u[ORC_MAX_DIMS];
+        double enc[ORC_MAX_LEVELS * 8], a[ORC_MAX_WIDTH + ORC_MAX_LEVELS * 8], z[ORC_MAX_WIDTH];
+        normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
+        encode_point(d, &L, params, u, enc, NULL, NULL);
+        net_input(d, enc, nrm4 + 4 * q, t, a);
+        const double* p = mlp;
+        int k_in = n_in;
+        for (int l = 0; l < layers; ++l) {
+            int last = l == layers - 1, n_out = last ? d->out_dim : d->width;
+            const double* W = p;
+            const double* b = p + (int64_t)n_out * k_in;
+            for (int o = 0; o < n_out; ++o) {
+                double acc = 0.0;
+                for (int i = 0; i < k_in; ++i)
+                    acc += orc_e4m3(W[(int64_t)o * k_in + i] / s_w[l]) * orc_e4m3(a[i] / s_act[l]);
+                z[o] = acc * s_w[l] * s_act[l] + b[o];
+            }
+            for (int o = 0; o < n_out; ++o) {
+                if (!last) a[o] = z[o] > 0.0 ? z[o] : 0.0;
+                else Eout[q * d->out_dim + o] = d->out_act == 1 ? softplus(z[o]) : z[o];
+            }
+            p = b + n_out;
+            k_in = n_out;
+        }
+    }
+    return 0;
+}

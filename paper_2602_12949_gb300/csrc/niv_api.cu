@@ -65,6 +65,8 @@ void free_model(niv_model* m) {
     cudaFree(m->grid_f16);
     cudaFree(m->mlp_plain);
     cudaFree(m->mlp_tc);
+    cudaFree(m->mlp_f8);
+    cudaFree(m->fp8_amax);
     cudaFree(m->stage);
     delete m;
 }
@@ -251,6 +253,7 @@ int niv_set_params(niv_handle h, const float* params, int64_t n, niv_stream stre
     if (rc) return rc;
     rc = niv_pack_tc(h, mlp_host.data(), s);
     if (rc) return rc;
+    h->fp8_ready = 0;  // the E4M3 network must be recalibrated for new parameters
     NIV_CUDA(cudaStreamSynchronize(s));
     return NIV_OK;
 }
@@ -293,6 +296,7 @@ int niv_query(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t
     switch (precision) {
         case NIV_FP32: return niv_launch_query_fp32(h, g, io, (cudaStream_t)stream);
         case NIV_FP16: return niv_launch_query_tc(h, g, io, precision, (cudaStream_t)stream);
+        case NIV_FP8: return niv_launch_query_f8(h, g, io, (cudaStream_t)stream);
         default: return niv_fail(NIV_ERR_UNSUPPORTED, "precision not supported");
     }
 }
@@ -347,6 +351,40 @@ int niv_encode(niv_handle h, const void* pos, int64_t n, int32_t dtype_in, const
     io.n = n;
     io.in_f16 = dtype_in == NIV_F16;
     return niv_launch_encode(h, g, io, out_enc, out_idx, (cudaStream_t)stream);
+}
+
+int niv_fp8_calibrate(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+                      const niv_query_params* params, niv_stream stream) {
+    if (!h || !params) return niv_fail(NIV_ERR_ARG, "handle or params is NULL");
+    if (n <= 0) return niv_fail(NIV_ERR_ARG, "calibration needs at least one record");
+    if (!pos || !nrm) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if (!aligned16(pos) || !aligned16(nrm)) return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    if (dtype_in != NIV_F32 && dtype_in != NIV_F16) return niv_fail(NIV_ERR_ARG, "bad dtype");
+    if (h->d.width < 32) return niv_fail(NIV_ERR_UNSUPPORTED, "the FP8 path needs width 32 or 64");
+    for (int k = 0; k < 3; ++k)
+        if (!(params->aabb_max[k] > params->aabb_min[k])) return niv_fail(NIV_ERR_ARG, "empty aabb");
+    int rc = check_device(h);
+    if (rc) return rc;
+    GridArgs g = niv_grid_args(h, params);
+    IoArgs io;
+    memset(&io, 0, sizeof io);
+    io.pos = pos;
+    io.nrm = nrm;
+    io.n = n;
+    io.in_f16 = dtype_in == NIV_F16;
+    return niv_calibrate_f8(h, g, io, (cudaStream_t)stream);
+}
+
+int niv_fp8_get_scales(niv_handle h, float* s_act, float* s_w, float* amax, int32_t count) {
+    if (!h) return niv_fail(NIV_ERR_ARG, "handle is NULL");
+    if (!h->fp8_ready) return niv_fail(NIV_ERR_ARG, "not calibrated");
+    if (count != h->d.n_hidden + 1) return niv_fail(NIV_ERR_ARG, "count must be n_hidden + 1");
+    for (int l = 0; l < count; ++l) {
+        if (s_act) s_act[l] = h->fp8_sact[l];
+        if (s_w) s_w[l] = h->fp8_sw[l];
+        if (amax) amax[l] = h->fp8_amax_host[l];
+    }
+    return NIV_OK;
 }
 
 int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out_rgba,

@@ -66,6 +66,12 @@ struct niv_model {
     uint8_t* mlp_tc;         // network packed for the tensor-core kernels (FP16 tiles)
     uint32_t mlp_tc_bytes;
     alignas(8) uint8_t tc_layout[64];  // offsets inside mlp_tc (query_tc.cu)
+    uint8_t* mlp_f8;         // network packed for the E4M3 kernel (query_f8.cu)
+    uint32_t mlp_f8_bytes;
+    alignas(8) uint8_t f8_layout[64];
+    float fp8_sact[8], fp8_sw[8], fp8_amax_host[8];  // per matrix product: activation / weight scales
+    unsigned* fp8_amax;      // calibration scratch (device)
+    int fp8_ready;           // calibrated since the last parameter change
     // Host staging for niv_query_host.
     void* stage;
     size_t stage_bytes;
@@ -93,6 +99,9 @@ int niv_env_int(const char* name, int dflt);
 int niv_launch_query_fp32(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s);
 int niv_launch_encode(const niv_model* m, const GridArgs& g, const IoArgs& io, float* enc, uint32_t* idx,
                       cudaStream_t s);
+int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s);
+int niv_calibrate_f8(niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s);
+int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s);
 int niv_launch_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out, cudaStream_t s);
 int niv_pack_plain(niv_model* m, const float* mlp_host, cudaStream_t s);
 int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s);

@@ -1,0 +1,433 @@
+// FP8 (E4M3) fused query on the tensor cores, its calibration and its weight packing.
+//
+// Same tile pipeline as the FP16 path (query_tc.cu): a warpgroup encodes 128 records
+// (FP16 grid features, FP32 interpolation), writes the network input as E4M3 bytes
+// into a K-major shared-memory tile, and every layer runs as tcgen05.mma of
+// kind::f8f6f4 (E4M3 x E4M3, K = 32 per instruction) into an FP32 TMEM accumulator.
+// Per-layer power-of-two scales (the FP8 reading of the design notes): weights
+// e4m3(W / s_w), inputs e4m3(a / s_a), and the epilogue forms
+//   z = acc * (s_w * s_a) + b,  ReLU,  then e4m3(z / s_a') for the next layer;
+// the output layer finishes with softplus in FP32.  s_a comes from niv_fp8_calibrate
+// (amax of each layer's FP32 input over a calibration batch), s_w from amax|W|.
+#include <cuda_fp8.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "niv_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int kT = 128;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr int kHdr = 128;
+constexpr int kNO = 16;
+
+// Byte offset of (row r, column k) in a K-major tile of 8-bit elements with K columns:
+// 8-row x 16-byte core matrices, 128 B apart along K, (K/16)*128 B apart along rows.
+__host__ __device__ __forceinline__ uint32_t core_off8(int r, int k, int K) {
+    return (uint32_t)((r >> 3) * (K >> 4) * 128 + (k >> 4) * 128 + (r & 7) * 16 + (k & 15));
+}
+
+struct F8Layout {
+    int32_t K1, W, n_hidden, col_extra;  // col_extra: tile column of n.x (features end before it)
+    uint32_t w1, wh, wo, scal, total;    // byte offsets; scal = FP32 block [c | qmul | biases]
+};
+
+__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return (lo & 0xFFFFu) | (hi << 16);
+}
+
+__device__ __forceinline__ uint4 e4m3x16(const float* v, float mul) {
+    return make_uint4(e4m3x4(v[0] * mul, v[1] * mul, v[2] * mul, v[3] * mul),
+                      e4m3x4(v[4] * mul, v[5] * mul, v[6] * mul, v[7] * mul),
+                      e4m3x4(v[8] * mul, v[9] * mul, v[10] * mul, v[11] * mul),
+                      e4m3x4(v[12] * mul, v[13] * mul, v[14] * mul, v[15] * mul));
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void issue_layer8(uint32_t tmem, uint32_t act, uint32_t w, uint32_t K, uint32_t idesc,
+                                             uint32_t bar) {
+    const uint32_t sbo = (K >> 4) * 128u;
+    for (uint32_t ks = 0; ks < K / 32; ++ks)
+        tc::mma_e4m3(tmem, tc::smem_desc(act + ks * 256u, 128u, sbo), tc::smem_desc(w + ks * 256u, 128u, sbo), idesc,
+                     ks > 0 ? 1u : 0u);
+    tc::mma_commit(bar);
+}
+
+template <int DIMS, int F>
+__global__ void __launch_bounds__(kT, 8) query_f8_kernel(GridArgs g, IoArgs io, const __half* __restrict__ grid16,
+                                                         const uint8_t* __restrict__ packed, F8Layout lay, int out_act,
+                                                         int64_t n_tiles, uint32_t tmem_cols, int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + 64);
+    uint8_t* s_net = smem + kHdr;
+    uint8_t* s_act = s_net + ((lay.total + 127u) & ~127u);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int K1 = lay.K1, W = lay.W, nh = lay.n_hidden;
+
+    for (uint32_t i = tid; i < lay.total / 16; i += kT)
+        reinterpret_cast<uint4*>(s_net)[i] = __ldg(reinterpret_cast<const uint4*>(packed) + i);
+    if (tid == 0) {
+        tc::mbar_init(s_bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(s_tmem), tmem_cols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
+    const uint32_t tmem = *s_tmem;
+    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t bar = tc::smem_u32(s_bar);
+    const uint32_t act_a = tc::smem_u32(s_act), net_a = tc::smem_u32(s_net);
+    const uint32_t idesc_h = tc::idesc_e4m3(128, W), idesc_o = tc::idesc_e4m3(128, kNO);
+    const float* s_c = reinterpret_cast<const float*>(s_net + lay.scal);  // acc -> z multipliers
+    const float* s_q = s_c + (nh + 1);                                   // 1 / s_a per matrix input
+    const float* s_b = s_q + (nh + 1);                                   // biases
+    const int L = g.levels, LF = L * F;
+    constexpr int G = 16 / F;  // levels per 16-byte chunk of E4M3 inputs
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int64_t r = niv_record_of(tile, tid, io.n, io.image_width);
+        const bool valid = r < io.n;
+        const int64_t rr = valid ? r : 0;
+        const float4 p = niv_load_rec(io.pos, rr, io.in_f16);
+        const float4 nv = niv_load_rec(io.nrm, rr, io.in_f16);
+        float u[4];
+        u[0] = niv_unit(p.x, g.aabb_min[0], g.inv_ext[0]);
+        u[1] = niv_unit(p.y, g.aabb_min[1], g.inv_ext[1]);
+        u[2] = niv_unit(p.z, g.aabb_min[2], g.inv_ext[2]);
+        u[3] = fminf(fmaxf(g.t, 0.0f), 1.0f);
+
+        // ---- encoding -> E4M3 input row ----
+        const float q0 = s_q[0];
+        for (int l0 = 0; l0 < L; l0 += G) {
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                if (l0 + q < L) {
+                    float acc[F];
+                    niv_encode_level<DIMS, F, __half>(g, grid16, l0 + q, u, acc);
+#pragma unroll
+                    for (int j = 0; j < F; ++j) v[q * F + j] = acc[j];
+                }
+            }
+            *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K1)) = e4m3x16(v, q0);
+        }
+        {
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+            v[0] = nv.x;
+            v[1] = nv.y;
+            v[2] = nv.z;
+            if (g.n_in > LF + 3) v[3] = u[3];
+            *reinterpret_cast<uint4*>(s_act + core_off8(tid, lay.col_extra, K1)) = e4m3x16(v, q0);
+        }
+        for (int k = lay.col_extra + 16; k < K1; k += 16)
+            *reinterpret_cast<uint4*>(s_act + core_off8(tid, k, K1)) = make_uint4(0u, 0u, 0u, 0u);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+
+        // ---- hidden layers ----
+        uint32_t K = (uint32_t)K1, w_off = lay.w1;
+        for (int layer = 0; layer < nh && ok; ++layer) {
+            if (tid == 0) {
+                tc::fence_after_sync();
+                issue_layer8(tmem, act_a, net_a + w_off, K, idesc_h, bar);
+            }
+            if (!tc::mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
+                atomicExch(status, 1);
+                ok = false;
+                break;
+            }
+            phase ^= 1u;
+            tc::fence_after_sync();
+            const float c = s_c[layer], qn = s_q[layer + 1];
+            const float* bias = s_b + layer * W;
+            for (int ch = 0; ch < W / 16; ++ch) {
+                float v[16];
+                tc::tmem_ld16(tmem_row + (uint32_t)(ch * 16), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = fmaxf(fmaf(v[j], c, bias[ch * 16 + j]), 0.0f);
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, ch * 16, W)) = e4m3x16(v, qn);
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            w_off = layer == 0 ? lay.wh : w_off + (uint32_t)(W * W);
+            K = (uint32_t)W;
+        }
+        if (!ok) break;
+
+        // ---- output layer (N = 16, three live columns) ----
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue_layer8(tmem, act_a, net_a + lay.wo, (uint32_t)W, idesc_o, bar);
+        }
+        if (!tc::mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
+            atomicExch(status, 1);
+            ok = false;
+            break;
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+        float zz[4];
+        tmem_ld4(tmem_row, zz);
+        const float c = s_c[nh];
+        const float* bo = s_b + nh * W;
+        float z0 = fmaf(zz[0], c, bo[0]), z1 = fmaf(zz[1], c, bo[1]), z2 = fmaf(zz[2], c, bo[2]);
+        if (out_act == 1) {
+            z0 = niv_softplus(z0);
+            z1 = niv_softplus(z1);
+            z2 = niv_softplus(z2);
+        }
+        if (valid) niv_store_rec(io.out, r, z0, z1, z2, io.out_f16);
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
+template <int DIMS, int F>
+int launch8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
+    const F8Layout* lay = reinterpret_cast<const F8Layout*>(m->f8_layout);
+    auto kern = query_f8_kernel<DIMS, F>;
+    const int kmax = lay->K1 > lay->W ? lay->K1 : lay->W;
+    const size_t smem = (size_t)kHdr + ((lay->total + 127u) & ~127u) + (size_t)kT * kmax;
+    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+    int dev = 0, sms = 0, smem_per_sm = 0, regs_per_sm = 0;
+    NIV_CUDA(cudaGetDevice(&dev));
+    NIV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    NIV_CUDA(cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    NIV_CUDA(cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    cudaFuncAttributes fa;
+    NIV_CUDA(cudaFuncGetAttributes(&fa, kern));
+    // residency from the register and shared-memory budgets (see query_tc.cu)
+    const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 1;
+    int per_sm = smem_per_sm / (int)(smem + 1024);
+    if (regs_per_sm / (kT * regs) < per_sm) per_sm = regs_per_sm / (kT * regs);
+    const uint32_t cols = lay->W <= 32 ? 32u : 64u;
+    if (per_sm > (int)(512 / cols)) per_sm = (int)(512 / cols);
+    if (per_sm < 1) return niv_fail(NIV_ERR_UNSUPPORTED, "FP8 query kernel does not fit on an SM");
+    int* status = niv_status_word();
+    if (!status) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
+    const int64_t tiles = niv_tile_count_host(io.n, io.image_width);
+    const int64_t blocks = tiles < (int64_t)sms * per_sm ? tiles : (int64_t)sms * per_sm;
+    kern<<<(unsigned)blocks, kT, smem, s>>>(g, io, m->grid_f16, m->mlp_f8, *lay, m->d.out_act, tiles, cols, status);
+    NIV_CUDA(cudaGetLastError());
+    return NIV_OK;
+}
+
+// ---- calibration: amax of every matrix product's FP32 input over n records ----
+__device__ __forceinline__ void amax_update(unsigned* slot, float v) {
+    // non-negative floats order like their bit patterns
+    const unsigned bits = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(v));
+    if ((threadIdx.x & 31) == 0) atomicMax(slot, bits);
+}
+
+template <int DIMS, int F>
+__global__ void __launch_bounds__(128) calib_kernel(GridArgs g, IoArgs io, const float* __restrict__ grid,
+                                                    const float* __restrict__ mlp, int W, int nh,
+                                                    unsigned* __restrict__ amax) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = q < io.n;
+    const int64_t qq = valid ? q : 0;
+    const float4 p = niv_load_rec(io.pos, qq, io.in_f16);
+    const float4 nv = niv_load_rec(io.nrm, qq, io.in_f16);
+    float u[4];
+    u[0] = niv_unit(p.x, g.aabb_min[0], g.inv_ext[0]);
+    u[1] = niv_unit(p.y, g.aabb_min[1], g.inv_ext[1]);
+    u[2] = niv_unit(p.z, g.aabb_min[2], g.inv_ext[2]);
+    u[3] = fminf(fmaxf(g.t, 0.0f), 1.0f);
+    float x[NIV_MAX_IN], h[64], h2[64];
+    float mx = 0.0f;
+    for (int l = 0; l < g.levels; ++l) {
+        float acc[F];
+        niv_encode_level<DIMS, F, float>(g, grid, l, u, acc);
+        for (int j = 0; j < F; ++j) {
+            x[l * F + j] = acc[j];
+            mx = fmaxf(mx, fabsf(acc[j]));
+        }
+    }
+    const int LF = g.levels * F;
+    x[LF] = nv.x;
+    x[LF + 1] = nv.y;
+    x[LF + 2] = nv.z;
+    if (g.n_in > LF + 3) x[LF + 3] = u[3];
+    for (int i = LF; i < g.n_in; ++i) mx = fmaxf(mx, fabsf(x[i]));
+    amax_update(amax, valid ? mx : 0.0f);
+    const float* w = mlp;
+    int k_in = g.n_in;
+    const float* in = x;
+    for (int layer = 0; layer < nh; ++layer) {
+        float* out = (layer & 1) ? h2 : h;
+        float m2 = 0.0f;
+        for (int o = 0; o < W; ++o) {
+            float z = w[W * k_in + o];
+            for (int i = 0; i < k_in; ++i) z = fmaf(w[o * k_in + i], in[i], z);
+            out[o] = fmaxf(z, 0.0f);
+            m2 = fmaxf(m2, out[o]);
+        }
+        amax_update(amax + layer + 1, valid ? m2 : 0.0f);
+        w += W * k_in + W;
+        k_in = W;
+        in = out;
+    }
+}
+
+double pow2_scale(double amax) {  // 2^ceil(log2(amax / 448)), 1 for amax = 0
+    if (!(amax > 0.0)) return 1.0;
+    int e;
+    const double mnt = frexp(amax / 448.0, &e);
+    return mnt == 0.5 ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+}
+
+uint8_t to_e4m3(float v) { return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3); }
+
+}  // namespace
+
+// Pack the E4M3 network from host FP32 parameters and the activation scales m->fp8_sact:
+// [W1 (W x K1) | hidden (W x W) ... | W_out (16 x W) bytes | c[nh+1] | qmul[nh+1] | biases].
+int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s) {
+    const int W = m->d.width, nh = m->d.n_hidden, n_in = m->n_in, LF = m->d.levels * m->d.feat;
+    F8Layout lay;
+    memset(&lay, 0, sizeof lay);
+    lay.col_extra = (LF + 15) & ~15;
+    lay.K1 = (lay.col_extra + m->d.in_extra + 31) & ~31;
+    lay.W = W;
+    lay.n_hidden = nh;
+    auto up = [](uint32_t x) { return (x + 127u) & ~127u; };
+    lay.w1 = 0;
+    lay.wh = up(lay.w1 + (uint32_t)(W * lay.K1));
+    lay.wo = up(lay.wh + (uint32_t)((nh - 1) * W * W));
+    lay.scal = up(lay.wo + (uint32_t)(kNO * W));
+    lay.total = up(lay.scal + (uint32_t)((2 * (nh + 1) + nh * W + 4) * 4));
+    static_assert(sizeof(F8Layout) <= sizeof(((niv_model*)0)->f8_layout), "layout slot too small");
+    std::vector<uint8_t> buf(lay.total, 0);
+    float* c = reinterpret_cast<float*>(&buf[lay.scal]);
+    float* qm = c + (nh + 1);
+    float* bias = qm + (nh + 1);
+    const float* p = mlp_host;
+    int k_in = n_in;
+    for (int l = 0; l <= nh; ++l) {
+        const bool last = l == nh;
+        const int n_out = last ? 3 : W;
+        float amax = 0.0f;
+        for (int i = 0; i < n_out * k_in; ++i) amax = fmaxf(amax, fabsf(p[i]));
+        const double sw = pow2_scale(amax);
+        m->fp8_sw[l] = (float)sw;
+        const float inv = (float)(1.0 / sw);  // exact: a power of two
+        const uint32_t base = l == 0 ? lay.w1 : last ? lay.wo : lay.wh + (uint32_t)((l - 1) * W * W);
+        const int K = l == 0 ? lay.K1 : W;
+        for (int r = 0; r < n_out; ++r)
+            for (int i = 0; i < k_in; ++i) {
+                const int col = (l == 0 && i >= LF) ? lay.col_extra + (i - LF) : i;
+                buf[base + core_off8(r, col, K)] = to_e4m3(p[(size_t)r * k_in + i] * inv);
+            }
+        p += (size_t)n_out * k_in;
+        for (int r = 0; r < n_out; ++r) bias[l * W + r] = p[r];
+        p += n_out;
+        c[l] = (float)(sw * (double)m->fp8_sact[l]);
+        qm[l] = (float)(1.0 / (double)m->fp8_sact[l]);
+        k_in = n_out;
+    }
+    memcpy(m->f8_layout, &lay, sizeof lay);
+    if (m->mlp_f8_bytes < lay.total) {
+        cudaFree(m->mlp_f8);
+        m->mlp_f8 = nullptr;
+        m->mlp_f8_bytes = 0;
+        NIV_CUDA(cudaMalloc(&m->mlp_f8, lay.total));
+        m->mlp_f8_bytes = lay.total;
+    }
+    NIV_CUDA(cudaMemcpyAsync(m->mlp_f8, buf.data(), lay.total, cudaMemcpyHostToDevice, s));
+    NIV_CUDA(cudaStreamSynchronize(s));
+    return NIV_OK;
+}
+
+// Run the calibration pass over n records and set the activation scales (host side waits).
+int niv_calibrate_f8(niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
+    if (m->d.width > 64 || m->n_in > NIV_MAX_IN) return niv_fail(NIV_ERR_UNSUPPORTED, "calibration shape");
+    const int nh = m->d.n_hidden;
+    if (!m->fp8_amax) NIV_CUDA(cudaMalloc(&m->fp8_amax, sizeof(unsigned) * 8));
+    NIV_CUDA(cudaMemsetAsync(m->fp8_amax, 0, sizeof(unsigned) * 8, s));
+    const unsigned blocks = (unsigned)((io.n + 127) / 128);
+    const float* mlp = m->params + m->n_grid;
+    if (m->d.dims == 4) {
+        switch (m->d.feat) {
+            case 1: calib_kernel<4, 1><<<blocks, 128, 0, s>>>(g, io, m->params, mlp, m->d.width, nh, m->fp8_amax); break;
+            case 2: calib_kernel<4, 2><<<blocks, 128, 0, s>>>(g, io, m->params, mlp, m->d.width, nh, m->fp8_amax); break;
+            default: calib_kernel<4, 4><<<blocks, 128, 0, s>>>(g, io, m->params, mlp, m->d.width, nh, m->fp8_amax); break;
+        }
+    } else {
+        switch (m->d.feat) {
+            case 1: calib_kernel<3, 1><<<blocks, 128, 0, s>>>(g, io, m->params, mlp, m->d.width, nh, m->fp8_amax); break;
+            case 2: calib_kernel<3, 2><<<blocks, 128, 0, s>>>(g, io, m->params, mlp, m->d.width, nh, m->fp8_amax); break;
+            default: calib_kernel<3, 4><<<blocks, 128, 0, s>>>(g, io, m->params, mlp, m->d.width, nh, m->fp8_amax); break;
+        }
+    }
+    NIV_CUDA(cudaGetLastError());
+    unsigned bits[8];
+    NIV_CUDA(cudaMemcpyAsync(bits, m->fp8_amax, sizeof bits, cudaMemcpyDeviceToHost, s));
+    NIV_CUDA(cudaStreamSynchronize(s));
+    for (int l = 0; l <= nh; ++l) {
+        float a;
+        memcpy(&a, &bits[l], 4);
+        m->fp8_amax_host[l] = a;
+        m->fp8_sact[l] = (float)pow2_scale(a);
+    }
+    std::vector<float> mlp_host((size_t)m->n_mlp);
+    NIV_CUDA(cudaMemcpyAsync(mlp_host.data(), mlp, sizeof(float) * m->n_mlp, cudaMemcpyDeviceToHost, s));
+    NIV_CUDA(cudaStreamSynchronize(s));
+    int rc = niv_pack_f8(m, mlp_host.data(), s);
+    if (rc) return rc;
+    m->fp8_ready = 1;
+    return NIV_OK;
+}
+
+int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
+    if (!m->fp8_ready) return niv_fail(NIV_ERR_ARG, "FP8 path needs niv_fp8_calibrate after the last niv_set_params");
+    const F8Layout* lay = reinterpret_cast<const F8Layout*>(m->f8_layout);
+    if (lay->K1 > 128) return niv_fail(NIV_ERR_UNSUPPORTED, "FP8 path needs a network input of <= 112 values");
+    if (m->d.dims == 4) {
+        switch (m->d.feat) {
+            case 1: return launch8<4, 1>(m, g, io, s);
+            case 2: return launch8<4, 2>(m, g, io, s);
+            default: return launch8<4, 4>(m, g, io, s);
+        }
+    }
+    switch (m->d.feat) {
+        case 1: return launch8<3, 1>(m, g, io, s);
+        case 2: return launch8<3, 2>(m, g, io, s);
+        default: return launch8<3, 4>(m, g, io, s);
+    }
+}

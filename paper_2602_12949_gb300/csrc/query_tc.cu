@@ -24,7 +24,9 @@
 // Tuning knobs (compile-time): NIV_TC_WG warpgroups per CTA sharing one copy of the
 // weights, NIV_TC_ILP levels whose gathers are in flight together, NIV_TC_MINB the
 // launch-bounds residency target, NIV_TC_OUT_FMA output layer on the CUDA cores.
+#include <cuda_fp8.h>
 #include <string.h>
+
 #include <vector>
 
 #include "niv_internal.cuh"
@@ -431,22 +433,32 @@ int niv_launch_query_tc(const niv_model* m, const GridArgs& g, const IoArgs& io,
 }
 
 // ---- tensor-core operand-layout self-test ----
-// D[128][64] = A[128][32] * B[64][32]^T with small integers (exact in FP32), A and B
-// written in the same canonical layout as the query kernels use.  `swap` exchanges
-// the two descriptor stride fields (a diagnostic of the layout convention); both
-// variants address only inside the 12 KB operand area.
+// D[128][64] = A[128][K] * B[64][K]^T with small integers (exact in FP32), A and B written
+// in the same canonical layouts the query kernels use.  mode 0: FP16, K = 32; mode 1: the
+// same with the two descriptor stride fields exchanged (a diagnostic of the layout
+// convention; both variants address only inside the operand buffers); mode 2: E4M3, K = 64.
 namespace {
-__global__ void __launch_bounds__(128) tc_selftest_kernel(int swap, float* __restrict__ out, int* __restrict__ status) {
+__global__ void __launch_bounds__(128) tc_selftest_kernel(int mode, float* __restrict__ out, int* __restrict__ status) {
     __shared__ __align__(1024) uint8_t s_a[128 * 32 * 2];
     __shared__ __align__(1024) uint8_t s_b[64 * 32 * 2];
     __shared__ uint64_t s_bar;
     __shared__ uint32_t s_tmem;
     const int t = threadIdx.x, warp = t >> 5;
-    for (int k = 0; k < 32; ++k)
-        *reinterpret_cast<__half*>(s_a + core_off(t, k, 32)) = __int2half_rn((t * 3 + k * 5) % 7 - 3);
+    const bool f8 = mode == 2;
+    const int K = f8 ? 64 : 32;
+    for (int k = 0; k < K; ++k) {
+        const int a = (t * 3 + k * 5) % 7 - 3;
+        if (f8) s_a[(t >> 3) * 512 + (k >> 4) * 128 + (t & 7) * 16 + (k & 15)] =
+            (uint8_t)__nv_cvt_float_to_fp8((float)a, __NV_SATFINITE, __NV_E4M3);
+        else *reinterpret_cast<__half*>(s_a + core_off(t, k, 32)) = __int2half_rn(a);
+    }
     if (t < 64)
-        for (int k = 0; k < 32; ++k)
-            *reinterpret_cast<__half*>(s_b + core_off(t, k, 32)) = __int2half_rn((t * 5 + k * 3) % 5 - 2);
+        for (int k = 0; k < K; ++k) {
+            const int b = (t * 5 + k * 3) % 5 - 2;
+            if (f8) s_b[(t >> 3) * 512 + (k >> 4) * 128 + (t & 7) * 16 + (k & 15)] =
+                (uint8_t)__nv_cvt_float_to_fp8((float)b, __NV_SATFINITE, __NV_E4M3);
+            else *reinterpret_cast<__half*>(s_b + core_off(t, k, 32)) = __int2half_rn(b);
+        }
     if (t == 0) {
         tc::mbar_init(&s_bar, 1);
         tc::fence_mbar_init();
@@ -460,12 +472,14 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(int swap, float* __res
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    const uint32_t lbo = swap ? 512u : 128u, sbo = swap ? 128u : 512u;
+    const uint32_t lbo = mode == 1 ? 512u : 128u, sbo = mode == 1 ? 128u : 512u;
     if (t == 0) {
         for (int ks = 0; ks < 2; ++ks) {
             const uint32_t kstep = (uint32_t)ks * 256u;  // two core matrices along K
-            tc::mma_f16(tmem, tc::smem_desc(tc::smem_u32(s_a) + kstep, lbo, sbo),
-                        tc::smem_desc(tc::smem_u32(s_b) + kstep, lbo, sbo), tc::idesc_f16(128, 64), ks > 0);
+            const uint64_t ad = tc::smem_desc(tc::smem_u32(s_a) + kstep, lbo, sbo);
+            const uint64_t bd = tc::smem_desc(tc::smem_u32(s_b) + kstep, lbo, sbo);
+            if (f8) tc::mma_e4m3(tmem, ad, bd, tc::idesc_e4m3(128, 64), ks > 0);
+            else tc::mma_f16(tmem, ad, bd, tc::idesc_f16(128, 64), ks > 0);
         }
         tc::mma_commit(tc::smem_u32(&s_bar));
     }
@@ -486,11 +500,12 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(int swap, float* __res
 }
 }  // namespace
 
-extern "C" int niv_selftest_mma(int32_t swap_strides, float* out, niv_stream stream) {
+extern "C" int niv_selftest_mma(int32_t mode, float* out, niv_stream stream) {
     if (!out) return niv_fail(NIV_ERR_ARG, "out is NULL");
+    if (mode < 0 || mode > 2) return niv_fail(NIV_ERR_ARG, "mode must be 0, 1 or 2");
     int* status = niv_status_word();
     if (!status) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
-    tc_selftest_kernel<<<1, 128, 0, (cudaStream_t)stream>>>(swap_strides, out, status);
+    tc_selftest_kernel<<<1, 128, 0, (cudaStream_t)stream>>>(mode, out, status);
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }

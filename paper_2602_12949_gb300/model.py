@@ -142,6 +142,22 @@ class NIVModel:
                                    PRECISIONS[precision], _stream(stream)))
         return out
 
+    def fp8_calibrate(self, pos, nrm, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), t=0.0, stream=None):
+        """Set the E4M3 path's activation scales from device records pos, nrm ([n][4])."""
+        _check_records(pos, "pos")
+        _check_records(nrm, "nrm")
+        qp = self.query_params(aabb_min, aabb_max, t, 0)
+        check(lib().niv_fp8_calibrate(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                                      pos.shape[0], _rec_dtype(pos), ctypes.byref(qp), _stream(stream)))
+
+    def fp8_scales(self):
+        """(activation scales, weight scales, activation amax), one entry per matrix product."""
+        n = self.desc.n_hidden + 1
+        sa, sw, am = (np.zeros(n, np.float32) for _ in range(3))
+        check(lib().niv_fp8_get_scales(self._h, ctypes.c_void_p(sa.ctypes.data), ctypes.c_void_p(sw.ctypes.data),
+                                       ctypes.c_void_p(am.ctypes.data), n))
+        return sa, sw, am
+
     def encode(self, pos, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), t=0.0, want_idx=True, stream=None):
         """(features [n][L*F] float32, corner indices [n][L][2^dims] int32 or None) for device records."""
         _check_records(pos, "pos")
