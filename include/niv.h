@@ -166,6 +166,47 @@ NIV_API int niv_query_host(niv_handle h, const void* pos, const void* nrm, int64
                    const niv_query_params* params, void* out_E, int32_t dtype_out, int32_t precision,
                    niv_stream stream);
 
+/* Optimiser settings of niv_fit (Sec. 4.5: Adam, learning rate 1e-2). */
+typedef struct niv_fit_params {
+    float lr;        /* learning rate */
+    float beta1;     /* Adam first-moment decay, e.g. 0.9 */
+    float beta2;     /* Adam second-moment decay, e.g. 0.99 */
+    float adam_eps;  /* Adam denominator epsilon, e.g. 1e-15 */
+    float loss_eps;  /* epsilon of the relative L2 loss (Eq. 3): 0.01 */
+} niv_fit_params;
+
+/*
+ * Loss and gradient of one batch (Sec. 4.5, Eq. 3): the relative L2 loss
+ * (E_theta - E)^2 / (sg(E_theta^2) + loss_eps), averaged over the n samples and the
+ * 3 channels, and its gradient w.r.t. every parameter, written to the handle's
+ * gradient buffer (read it with niv_get_grads).  The forward pass runs in FP32
+ * against the FP32 master parameters.  pos, nrm, target: device float32 [n][4]
+ * records (x, normal, target E); t: device float32 [n] per-sample scene parameter
+ * of a 4-D model, or NULL to use params->t.  loss_out (host, nullable): the loss,
+ * which makes the call synchronise `stream`.  The first call allocates the training
+ * state (gradients, Adam moments, activation scratch).
+ */
+NIV_API int niv_grad(niv_handle h, const float* pos, const float* nrm, const float* t, const float* target, int64_t n,
+                     const niv_query_params* params, float loss_eps, double* loss_out, niv_stream stream);
+
+/* Copy the n gradient values of the last niv_grad to `out` (host or device).  Synchronises. */
+NIV_API int niv_get_grads(niv_handle h, float* out, int64_t n, niv_stream stream);
+
+/* Overwrite the gradient buffer with n values (host or device), e.g. to drive niv_adam_step. */
+NIV_API int niv_set_grads(niv_handle h, const float* grads, int64_t n, niv_stream stream);
+
+/*
+ * One Adam step (Kingma & Ba; Sec. 4.5) on every parameter from the gradient
+ * buffer: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2, theta -= lr m_hat / (sqrt(v_hat) + eps)
+ * with bias corrections 1 - b^step (step counts calls since the last niv_set_params).
+ * The inference copies are rebuilt on the next niv_query.  Asynchronous.
+ */
+NIV_API int niv_adam_step(niv_handle h, float lr, float beta1, float beta2, float eps, niv_stream stream);
+
+/* niv_grad followed by niv_adam_step with the settings in fp. */
+NIV_API int niv_fit(niv_handle h, const float* pos, const float* nrm, const float* t, const float* target, int64_t n,
+                    const niv_query_params* params, const niv_fit_params* fp, double* loss_out, niv_stream stream);
+
 /*
  * Calibrate the E4M3 network path (NIV_FP8).  Runs the FP32 network over the n
  * device records pos/nrm ([n][4], dtype_in) and takes, for every matrix product,

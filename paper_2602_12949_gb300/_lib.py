@@ -41,6 +41,11 @@ class QueryParams(ctypes.Structure):
                 ("image_width", ctypes.c_int32)]
 
 
+class FitParams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("adam_eps", ctypes.c_float), ("loss_eps", ctypes.c_float)]
+
+
 _lib = None
 
 # (name, restype, argtypes); pointer arguments are passed as integers (c_void_p).
@@ -57,6 +62,11 @@ _SIGNATURES = [
     ("niv_get_params", ctypes.c_int, [_VP, _VP, _I64, _VP]),
     ("niv_query", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),
     ("niv_query_host", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),
+    ("niv_grad", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, ctypes.POINTER(QueryParams), _F, _VP, _VP]),
+    ("niv_get_grads", ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    ("niv_set_grads", ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    ("niv_adam_step", ctypes.c_int, [_VP, _F, _F, _F, _F, _VP]),
+    ("niv_fit", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, ctypes.POINTER(QueryParams), ctypes.POINTER(FitParams), _VP, _VP]),
     ("niv_fp8_calibrate", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP]),
     ("niv_fp8_get_scales", ctypes.c_int, [_VP, _VP, _VP, _VP, _I32]),
     ("niv_query_host_noalloc", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),

@@ -67,8 +67,44 @@ void free_model(niv_model* m) {
     cudaFree(m->mlp_tc);
     cudaFree(m->mlp_f8);
     cudaFree(m->fp8_amax);
+    cudaFree(m->grad);
+    cudaFree(m->adam_m);
+    cudaFree(m->adam_v);
+    cudaFree(m->stash);
+    cudaFree(m->loss_acc);
     cudaFree(m->stage);
     delete m;
+}
+
+// Rebuild the FP16 grid and the packed networks from the master parameters on the device.
+int refresh_inference(niv_model* h, cudaStream_t s) {
+    int rc = convert_grid_f16(h, s);
+    if (rc) return rc;
+    std::vector<float> mlp_host((size_t)h->n_mlp);
+    NIV_CUDA(cudaMemcpyAsync(mlp_host.data(), h->params + h->n_grid, sizeof(float) * h->n_mlp, cudaMemcpyDeviceToHost, s));
+    NIV_CUDA(cudaStreamSynchronize(s));
+    rc = niv_pack_plain(h, mlp_host.data(), s);
+    if (rc) return rc;
+    rc = niv_pack_tc(h, mlp_host.data(), s);
+    if (rc) return rc;
+    h->fp8_ready = 0;  // the E4M3 network must be recalibrated for new parameters
+    h->infer_dirty = 0;
+    return NIV_OK;
+}
+
+int ensure_training_state(niv_model* h) {
+    const int64_t n = h->n_grid + h->n_mlp;
+    if (!h->grad) NIV_CUDA(cudaMalloc(&h->grad, sizeof(float) * n));
+    if (!h->adam_m) {
+        NIV_CUDA(cudaMalloc(&h->adam_m, sizeof(float) * n));
+        NIV_CUDA(cudaMemset(h->adam_m, 0, sizeof(float) * n));
+    }
+    if (!h->adam_v) {
+        NIV_CUDA(cudaMalloc(&h->adam_v, sizeof(float) * n));
+        NIV_CUDA(cudaMemset(h->adam_v, 0, sizeof(float) * n));
+    }
+    if (!h->loss_acc) NIV_CUDA(cudaMalloc(&h->loss_acc, sizeof(double)));
+    return NIV_OK;
 }
 
 }  // namespace
@@ -244,16 +280,12 @@ int niv_set_params(niv_handle h, const float* params, int64_t n, niv_stream stre
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     NIV_CUDA(cudaMemcpyAsync(h->params, params, sizeof(float) * n, cudaMemcpyDefault, s));
-    rc = convert_grid_f16(h, s);
+    rc = refresh_inference(h, s);
     if (rc) return rc;
-    std::vector<float> mlp_host((size_t)h->n_mlp);
-    NIV_CUDA(cudaMemcpyAsync(mlp_host.data(), h->params + h->n_grid, sizeof(float) * h->n_mlp, cudaMemcpyDeviceToHost, s));
-    NIV_CUDA(cudaStreamSynchronize(s));
-    rc = niv_pack_plain(h, mlp_host.data(), s);
-    if (rc) return rc;
-    rc = niv_pack_tc(h, mlp_host.data(), s);
-    if (rc) return rc;
-    h->fp8_ready = 0;  // the E4M3 network must be recalibrated for new parameters
+    // new parameters start a new optimisation
+    h->adam_step = 0;
+    if (h->adam_m) NIV_CUDA(cudaMemsetAsync(h->adam_m, 0, sizeof(float) * n, s));
+    if (h->adam_v) NIV_CUDA(cudaMemsetAsync(h->adam_v, 0, sizeof(float) * n, s));
     NIV_CUDA(cudaStreamSynchronize(s));
     return NIV_OK;
 }
@@ -284,6 +316,10 @@ int niv_query(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t
     if (params->image_width < 0) return niv_fail(NIV_ERR_ARG, "image_width < 0");
     int rc = check_device(h);
     if (rc) return rc;
+    if (h->infer_dirty) {  // trained since the inference copies were built
+        rc = refresh_inference(h, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
     GridArgs g = niv_grid_args(h, params);
     IoArgs io;
     io.pos = pos;
@@ -385,6 +421,73 @@ int niv_fp8_get_scales(niv_handle h, float* s_act, float* s_w, float* amax, int3
         if (amax) amax[l] = h->fp8_amax_host[l];
     }
     return NIV_OK;
+}
+
+int niv_grad(niv_handle h, const float* pos, const float* nrm, const float* t, const float* target, int64_t n,
+             const niv_query_params* params, float eps, double* loss_out, niv_stream stream) {
+    if (!h || !params) return niv_fail(NIV_ERR_ARG, "handle or params is NULL");
+    if (n <= 0) return niv_fail(NIV_ERR_ARG, "n must be positive");
+    if (!pos || !nrm || !target) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if (!aligned16(pos) || !aligned16(nrm) || !aligned16(target))
+        return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    if (t && ((uintptr_t)t & 3u)) return niv_fail(NIV_ERR_ALIGN, "t must be 4-byte aligned");
+    if (!(eps > 0.0f)) return niv_fail(NIV_ERR_ARG, "eps must be positive");
+    for (int k = 0; k < 3; ++k)
+        if (!(params->aabb_max[k] > params->aabb_min[k])) return niv_fail(NIV_ERR_ARG, "empty aabb");
+    int rc = check_device(h);
+    if (rc) return rc;
+    rc = ensure_training_state(h);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    GridArgs g = niv_grid_args(h, params);
+    rc = niv_train_grad(h, g, (const float4*)pos, (const float4*)nrm, t, (const float4*)target, n, eps, s);
+    if (rc) return rc;
+    if (loss_out) {
+        double acc = 0.0;
+        NIV_CUDA(cudaMemcpyAsync(&acc, h->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+        NIV_CUDA(cudaStreamSynchronize(s));
+        *loss_out = acc / (3.0 * (double)n);
+    }
+    return NIV_OK;
+}
+
+int niv_get_grads(niv_handle h, float* out, int64_t n, niv_stream stream) {
+    if (!h || !out) return niv_fail(NIV_ERR_ARG, "handle or out is NULL");
+    if (n != h->n_grid + h->n_mlp) return niv_fail(NIV_ERR_ARG, "gradient count mismatch");
+    if (!h->grad) return niv_fail(NIV_ERR_ARG, "no gradients computed yet");
+    NIV_CUDA(cudaMemcpyAsync(out, h->grad, sizeof(float) * n, cudaMemcpyDefault, (cudaStream_t)stream));
+    NIV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return NIV_OK;
+}
+
+int niv_set_grads(niv_handle h, const float* grads, int64_t n, niv_stream stream) {
+    if (!h || !grads) return niv_fail(NIV_ERR_ARG, "handle or grads is NULL");
+    if (n != h->n_grid + h->n_mlp) return niv_fail(NIV_ERR_ARG, "gradient count mismatch");
+    int rc = check_device(h);
+    if (rc) return rc;
+    rc = ensure_training_state(h);
+    if (rc) return rc;
+    NIV_CUDA(cudaMemcpyAsync(h->grad, grads, sizeof(float) * n, cudaMemcpyDefault, (cudaStream_t)stream));
+    NIV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return NIV_OK;
+}
+
+int niv_adam_step(niv_handle h, float lr, float beta1, float beta2, float eps, niv_stream stream) {
+    if (!h) return niv_fail(NIV_ERR_ARG, "handle is NULL");
+    if (!h->grad) return niv_fail(NIV_ERR_ARG, "no gradients computed yet");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f))
+        return niv_fail(NIV_ERR_ARG, "betas must lie in [0, 1) and eps >= 0");
+    int rc = check_device(h);
+    if (rc) return rc;
+    return niv_train_adam(h, lr, beta1, beta2, eps, (cudaStream_t)stream);
+}
+
+int niv_fit(niv_handle h, const float* pos, const float* nrm, const float* t, const float* target, int64_t n,
+            const niv_query_params* params, const niv_fit_params* fp, double* loss_out, niv_stream stream) {
+    if (!fp) return niv_fail(NIV_ERR_ARG, "fit params is NULL");
+    int rc = niv_grad(h, pos, nrm, t, target, n, params, fp->loss_eps, loss_out, stream);
+    if (rc) return rc;
+    return niv_adam_step(h, fp->lr, fp->beta1, fp->beta2, fp->adam_eps, stream);
 }
 
 int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out_rgba,

@@ -72,6 +72,15 @@ struct niv_model {
     float fp8_sact[8], fp8_sw[8], fp8_amax_host[8];  // per matrix product: activation / weight scales
     unsigned* fp8_amax;      // calibration scratch (device)
     int fp8_ready;           // calibrated since the last parameter change
+    // Training state (allocated on the first training call).
+    float* grad;             // dLoss/dparams, same layout as params
+    float* adam_m;
+    float* adam_v;
+    int64_t adam_step;
+    float* stash;            // per-step activation / gradient scratch
+    int64_t stash_floats;
+    double* loss_acc;        // device loss accumulator
+    int infer_dirty;         // parameters changed on the device since the inference copies were built
     // Host staging for niv_query_host.
     void* stage;
     size_t stage_bytes;
@@ -102,6 +111,10 @@ int niv_launch_encode(const niv_model* m, const GridArgs& g, const IoArgs& io, f
 int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s);
 int niv_calibrate_f8(niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s);
 int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s);
+int64_t niv_train_stash_floats(const niv_model* m, int64_t n);
+int niv_train_grad(niv_model* m, const GridArgs& g, const float4* pos, const float4* nrm, const float* t,
+                   const float4* target, int64_t n, float eps, cudaStream_t s);
+int niv_train_adam(niv_model* m, float lr, float b1, float b2, float eps, cudaStream_t s);
 int niv_launch_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out, cudaStream_t s);
 int niv_pack_plain(niv_model* m, const float* mlp_host, cudaStream_t s);
 int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s);

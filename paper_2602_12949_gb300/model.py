@@ -9,7 +9,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import check, lib, ModelDesc, QueryParams
+from ._lib import check, lib, ModelDesc, QueryParams, FitParams
 
 PRECISIONS = {"fp32": _lib.NIV_FP32, "fp16": _lib.NIV_FP16, "fp8": _lib.NIV_FP8}
 
@@ -141,6 +141,54 @@ class NIVModel:
                                    p.shape[0], dt, ctypes.byref(qp), ctypes.c_void_p(o.ctypes.data), odt,
                                    PRECISIONS[precision], _stream(stream)))
         return out
+
+    def _train_args(self, pos, nrm, target, t):
+        for a, name in ((pos, "pos"), (nrm, "nrm"), (target, "target")):
+            _check_records(a, name)
+            if a.dtype != torch.float32:
+                raise TypeError("%s must be float32 for training" % name)
+        tp = 0
+        if t is not None:
+            if t.dtype != torch.float32 or not t.is_cuda or t.numel() != pos.shape[0]:
+                raise ValueError("t must be a float32 device vector with one value per sample")
+            tp = t.contiguous().data_ptr()
+        return tp
+
+    def grad(self, pos, nrm, target, t=None, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), loss_eps=0.01,
+             stream=None):
+        """Loss (Eq. 3) of the batch; gradients land in the model's gradient buffer."""
+        tp = self._train_args(pos, nrm, target, t)
+        qp = self.query_params(aabb_min, aabb_max, 0.0, 0)
+        loss = ctypes.c_double()
+        check(lib().niv_grad(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                             ctypes.c_void_p(tp), ctypes.c_void_p(target.data_ptr()), pos.shape[0], ctypes.byref(qp),
+                             float(loss_eps), ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def get_grads(self):
+        g, m = self.param_count()
+        out = np.empty(g + m, np.float32)
+        check(lib().niv_get_grads(self._h, ctypes.c_void_p(out.ctypes.data), out.size, _stream()))
+        return out
+
+    def set_grads(self, grads):
+        grads = np.ascontiguousarray(grads, np.float32)
+        check(lib().niv_set_grads(self._h, ctypes.c_void_p(grads.ctypes.data), grads.size, _stream()))
+
+    def adam_step(self, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15, stream=None):
+        check(lib().niv_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps), _stream(stream)))
+
+    def fit(self, pos, nrm, target, t=None, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), lr=1e-2,
+            beta1=0.9, beta2=0.99, adam_eps=1e-15, loss_eps=0.01, want_loss=True, stream=None):
+        """One optimisation step (Sec. 4.5) on the batch; returns the batch loss (or None)."""
+        tp = self._train_args(pos, nrm, target, t)
+        qp = self.query_params(aabb_min, aabb_max, 0.0, 0)
+        fp = FitParams(lr, beta1, beta2, adam_eps, loss_eps)
+        loss = ctypes.c_double()
+        check(lib().niv_fit(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                            ctypes.c_void_p(tp), ctypes.c_void_p(target.data_ptr()), pos.shape[0], ctypes.byref(qp),
+                            ctypes.byref(fp), ctypes.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None
 
     def fp8_calibrate(self, pos, nrm, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), t=0.0, stream=None):
         """Set the E4M3 path's activation scales from device records pos, nrm ([n][4])."""

@@ -1,0 +1,114 @@
+"""GPU parity of the training kernels (Sec. 4.5) against the FP64 oracle.
+
+The oracle's gradient is itself pinned to central differences of Eq. 3 (with the
+stop-gradient denominator frozen) in tests/test_oracle_network.py; here the
+hand-written backward kernels (FP32, through the C ABI) must reproduce it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from niv_inputs import init_params, uniform_queries
+from niv_inputs.configs import MODEL_C0, ROOM_MIN, ROOM_MAX
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GRAD_BOUND = 1e-4  # max |g - g_ref| / max |g_ref| per parameter group (FP32 sums over the batch)
+
+
+@pytest.fixture(scope="module")
+def niv():
+    from paper_2602_12949_gb300.build import build
+    build()
+    import paper_2602_12949_gb300 as P
+    return P
+
+
+def _groups(om):
+    n_grid = oracle.grid_value_count(om)
+    out, off = [("grid", 0, n_grid)], n_grid
+    for li, (o, i) in enumerate(oracle.layer_shapes(om)):
+        out.append(("W%d" % li, off, off + o * i))
+        out.append(("b%d" % li, off + o * i, off + o * i + o))
+        off += o * i + o
+    return out
+
+
+@pytest.mark.parametrize("spec,n,use_t", [
+    (dict(MODEL_C0, log2_T=10), 4096 + 33, False),                           # hash collisions in the grid
+    (dict(MODEL_C0, levels=4, feat=4, n_hidden=3, width=32), 2048, False),
+    (dict(dims=4, levels=6, feat=2, log2_T=12, base=3.0, growth=1.6, n_hidden=3, width=64, in_extra=4), 3000, True),
+    (dict(MODEL_C0, width=16, n_hidden=1), 1000, False),
+])
+def test_gradient_matches_oracle(niv, spec, n, use_t):
+    m = niv.NIVModel(**spec)
+    g, _ = m.param_count()
+    params = init_params(g, m.layer_shapes(), seed=3, feat_range=0.3, bias_std=0.2)
+    m.set_params(params)
+    om = oracle.Model(**spec)
+    pos, nrm = uniform_queries(n, seed=4)
+    target = np.zeros((n, 4), np.float32)
+    target[:, :3] = np.random.default_rng(5).uniform(0.1, 2.0, (n, 3))
+    t = np.random.default_rng(6).random(n).astype(np.float32) if use_t else None
+    dev = lambda a: torch.from_numpy(a).cuda()
+    loss = m.grad(dev(pos), dev(nrm), dev(target), t=dev(t) if use_t else None)
+    got = m.get_grads().astype(np.float64)
+    ref_loss, ref = oracle.loss_grad(om, params, pos, nrm, target[:, :3], t=t)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    for name, a, b in _groups(om):
+        scale = np.abs(ref[a:b]).max()
+        err = np.abs(got[a:b] - ref[a:b]).max() / scale
+        print("%s: %.3g" % (name, err))
+        assert err <= GRAD_BOUND, name
+    m.close()
+
+
+def test_adam_matches_oracle(niv):
+    m = niv.NIVModel(**MODEL_C0)
+    g, nm = m.param_count()
+    params = init_params(g, m.layer_shapes(), seed=1)
+    m.set_params(params)
+    theta = params.astype(np.float64)
+    mm, vv = np.zeros_like(theta), np.zeros_like(theta)
+    rng = np.random.default_rng(2)
+    for step in range(1, 4):
+        grads = (rng.standard_normal(g + nm) * 10.0 ** rng.uniform(-4, 0, g + nm)).astype(np.float32)
+        m.set_grads(grads)
+        m.adam_step(lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15)
+        oracle.adam(theta, mm, vv, grads.astype(np.float64), 1e-2, 0.9, 0.99, 1e-15, step)
+    got = m.get_params().astype(np.float64)
+    np.testing.assert_allclose(got, theta, rtol=0, atol=2e-6)
+    m.close()
+
+
+def test_fit_reduces_loss_and_trained_model_queries_match_oracle(niv):
+    """Fitting a smooth synthetic target lowers the loss; the refreshed inference copies follow."""
+    spec = dict(MODEL_C0)
+    m = niv.NIVModel(**spec)
+    g, _ = m.param_count()
+    m.set_params(init_params(g, m.layer_shapes(), seed=0))
+    n = 1 << 15
+    pos, nrm = uniform_queries(n, seed=9)
+    tgt = np.zeros((n, 4), np.float32)
+    p3, n3 = pos[:, :3].astype(np.float64), nrm[:, :3].astype(np.float64)
+    tgt[:, 0] = 1.0 + 0.5 * np.sin(3 * p3[:, 0]) * n3[:, 1]
+    tgt[:, 1] = 0.5 + 0.4 * p3[:, 1] * p3[:, 2]
+    tgt[:, 2] = 0.8 + 0.3 * np.cos(2 * p3[:, 2] + n3[:, 0])
+    dev = lambda a: torch.from_numpy(a).cuda()
+    dp, dn, dt = dev(pos), dev(nrm), dev(tgt)
+    first = m.fit(dp, dn, dt)
+    for _ in range(300):
+        last = m.fit(dp, dn, dt, want_loss=False)
+    last = m.grad(dp, dn, dt)
+    print("loss %.4g -> %.4g" % (first, last))
+    assert last < 0.05 * first
+    om = oracle.Model(**spec)
+    trained = m.get_params()
+    E = m.query(dp, dn, precision="fp32")[:, :3].cpu().numpy()
+    ref = oracle.query(om, trained, pos, nrm)
+    assert np.max(np.abs(E - ref) / np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())) <= 1e-5
+    E16 = m.query(dp, dn, precision="fp16", out_dtype=torch.float32)[:, :3].cpu().numpy()
+    ref16 = oracle.query(om, trained.astype(np.float16).astype(np.float64), pos, nrm)
+    assert np.max(np.abs(E16 - ref16) / np.maximum(np.abs(ref16), 1e-3 * np.abs(ref16).max())) <= 2e-3
+    m.close()
