@@ -225,6 +225,28 @@ NIV_API int niv_fp8_calibrate(niv_handle h, const void* pos, const void* nrm, in
  */
 NIV_API int niv_fp8_get_scales(niv_handle h, float* s_act, float* s_w, float* amax, int32_t count);
 
+/* Monte Carlo modes: every radiance reaching x, or only light that bounced at least once. */
+#define NIV_MC_TOTAL 0
+#define NIV_MC_INDIRECT 1
+
+/*
+ * Monte Carlo irradiance of the analytic scene (Eq. 1): the training targets of
+ * Sec. 4.5.  For each of m points x (device float32 [m][4]) with normal n
+ * ([m][4]): E = (pi / spp) sum_j L_i(x, w_j), w_j cosine-distributed about n; paths
+ * use next-event estimation toward emitting spheres and Russian roulette after three
+ * bounces.  NIV_MC_INDIRECT (the paper's E, Sec. 3) omits emission seen directly
+ * from x and direct sky light.  out_E: device float64 [m][3].  out_keep (device
+ * uint8 [m], nullable): 0 for points whose first hits are mostly back faces (inside
+ * geometry, Sec. 4.5) or whose E is zero (App. I), else 1.  t (device float32 [m],
+ * nullable): time of the rotating sphere per point.  Random numbers:
+ * Philox4x32-10, counter (point index_base + i, path j, bounce, purpose), key seed.
+ * scene: the host float32 scene description (niv_inputs.scenes layout, at most 56
+ * objects) of scene_len values.  Asynchronous.
+ */
+NIV_API int niv_mc_irradiance(const float* scene, int64_t scene_len, const float* x4, const float* n4, const float* t,
+                              int64_t m, int32_t spp, uint64_t seed, uint64_t index_base, int32_t mode, double* out_E,
+                              uint8_t* out_keep, niv_stream stream);
+
 /*
  * Largest n accepted by niv_query_host_noalloc: the number of records its fixed
  * staging area holds.

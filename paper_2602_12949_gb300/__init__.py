@@ -4,6 +4,6 @@
 all the work; this package marshals torch tensors into it.
 """
 from ._lib import lib, NivError, LIB_PATH
-from .model import NIVModel, shade, sync_status, PRECISIONS
+from .model import NIVModel, shade, sync_status, mc_irradiance, PRECISIONS
 
-__all__ = ["lib", "NivError", "LIB_PATH", "NIVModel", "shade", "sync_status", "PRECISIONS"]
+__all__ = ["lib", "NivError", "LIB_PATH", "NIVModel", "shade", "sync_status", "mc_irradiance", "PRECISIONS"]

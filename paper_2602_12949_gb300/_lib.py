@@ -18,6 +18,7 @@ NIV_ERR_DEVICE = -5
 NIV_ERR_NOMEM = -6
 
 NIV_FP32, NIV_FP16, NIV_FP8 = 0, 1, 2
+NIV_MC_TOTAL, NIV_MC_INDIRECT = 0, 1
 NIV_F32, NIV_F16 = 0, 1
 
 
@@ -62,6 +63,7 @@ _SIGNATURES = [
     ("niv_get_params", ctypes.c_int, [_VP, _VP, _I64, _VP]),
     ("niv_query", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),
     ("niv_query_host", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),
+    ("niv_mc_irradiance", ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _I64, _I32, _U64, _U64, _I32, _VP, _VP, _VP]),
     ("niv_grad", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, ctypes.POINTER(QueryParams), _F, _VP, _VP]),
     ("niv_get_grads", ctypes.c_int, [_VP, _VP, _I64, _VP]),
     ("niv_set_grads", ctypes.c_int, [_VP, _VP, _I64, _VP]),

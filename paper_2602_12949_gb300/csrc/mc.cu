@@ -1,0 +1,337 @@
+// Monte Carlo irradiance (Eq. 1) of the analytic scenes: the training targets of Sec. 4.5.
+//
+// One thread per query point.  E(x, n) = (pi / S) sum_j L_i(x, w_j) over S cosine-
+// distributed directions w_j about n; L_i follows a path with next-event estimation
+// toward every emitting sphere (uniform sampling of the subtended cone), cosine
+// continuation and Russian roulette after three bounces (at most 32 segments).
+// INDIRECT mode (what the paper caches; direct light is added at runtime, Sec. 3)
+// drops emission seen by the first segment and sky light reaching x directly.
+// A point is flagged for discard when more than half of its first hits are back
+// faces (it lies inside geometry, Sec. 4.5) or when its irradiance is zero in
+// every channel (App. I).  Geometry runs in FP32; the per-point sum is FP64.
+//
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11) on counter
+// (point lo, point hi, j + (depth << 16), purpose) with key (seed lo, seed hi);
+// purpose 0 = bounce direction + roulette, 1 + e = light sample toward emitter e;
+// the first direction of path j uses depth 0xFFFF.  u32 -> (0,1): (x >> 8) 2^-24 + 2^-25.
+#include <math.h>
+
+#include "niv_internal.cuh"
+
+namespace {
+
+constexpr int kHdr = 48, kSph = 12, kBox = 12;
+constexpr int kMaxObjects = 56;
+constexpr int kMaxDepth = 32;
+constexpr float kTEps = 1e-4f;
+
+struct SceneArg {
+    float v[kHdr + kSph * kMaxObjects];
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f) + (1.0f / 33554432.0f); }
+
+struct Rng {
+    uint64_t point, seed;
+    __device__ float4 draw(uint32_t j, uint32_t depth, uint32_t purpose) const {
+        const uint4 o = philox4x32_10(make_uint4((uint32_t)point, (uint32_t)(point >> 32), j + (depth << 16), purpose),
+                                      (uint32_t)seed, (uint32_t)(seed >> 32));
+        return make_float4(u01(o.x), u01(o.y), u01(o.z), u01(o.w));
+    }
+};
+
+struct Hit {
+    int kind;  // 0 none, 1 sphere, 2 box, 3 wall
+    int id;
+    float t;
+    float3 p, n;  // n: outward for objects, into the room for walls
+};
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float comp(float3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+struct SceneView {
+    const float* h;    // the scene description, in shared memory
+    const float* sph;
+    const float* box;
+    int ns, nb, room, rot;
+    float3 rotc;       // centre of the rotating sphere at this point's time
+
+    __device__ void init(const float* blob, float t) {
+        h = blob;
+        ns = (int)blob[0];
+        nb = (int)blob[1];
+        room = blob[2] != 0.0f;
+        sph = blob + kHdr;
+        box = sph + kSph * ns;
+        rot = (int)blob[3];
+        rotc = make_float3(0.0f, 0.0f, 0.0f);
+        if (rot >= 0 && rot < ns) {  // rotate by 2 pi t about +y through the axis point
+            const float* c = sph + kSph * rot;
+            const float a = 6.283185307179586f * t, ca = cosf(a), sa = sinf(a);
+            const float dx = c[0] - blob[36], dz = c[2] - blob[38];
+            rotc = make_float3(blob[36] + ca * dx + sa * dz, c[1], blob[38] - sa * dx + ca * dz);
+        }
+    }
+
+    __device__ __forceinline__ float3 centre(int i) const {
+        const float* c = sph + kSph * i;
+        return i == rot ? rotc : make_float3(c[0], c[1], c[2]);
+    }
+
+    __device__ bool emits(int i) const {
+        const float* e = sph + kSph * i + 7;
+        return e[0] > 0.0f || e[1] > 0.0f || e[2] > 0.0f;
+    }
+
+    __device__ bool intersect(float3 o, float3 d, Hit& hit) const {
+        hit.kind = 0;
+        hit.t = INFINITY;
+        for (int i = 0; i < ns; ++i) {
+            const float r = sph[kSph * i + 3];
+            const float3 ci = centre(i);
+            const float3 oc = make_float3(o.x - ci.x, o.y - ci.y, o.z - ci.z);
+            const float b = dot3(oc, d), disc = b * b - (dot3(oc, oc) - r * r);
+            if (disc < 0.0f) continue;
+            const float sq = sqrtf(disc);
+            float t = -b - sq;
+            if (t <= kTEps) t = -b + sq;
+            if (t > kTEps && t < hit.t) {
+                hit.t = t;
+                hit.kind = 1;
+                hit.id = i;
+            }
+        }
+        for (int i = 0; i < nb; ++i) {
+            const float* B = box + kBox * i;
+            float tn = -INFINITY, tf = INFINITY;
+            int an = 0, af = 0;
+            for (int k = 0; k < 3; ++k) {
+                const float t1 = (B[k] - comp(o, k)) / comp(d, k), t2 = (B[3 + k] - comp(o, k)) / comp(d, k);
+                const float lo = fminf(t1, t2), hi = fmaxf(t1, t2);
+                if (lo > tn) { tn = lo; an = k; }
+                if (hi < tf) { tf = hi; af = k; }
+            }
+            if (tf < tn) continue;
+            float t;
+            int ax;
+            if (tn > kTEps) { t = tn; ax = an; }
+            else if (tf > kTEps) { t = tf; ax = af; }
+            else continue;
+            if (t < hit.t) {
+                hit.t = t;
+                hit.kind = 2;
+                hit.id = i * 3 + ax;
+            }
+        }
+        if (room) {
+            float tw = INFINITY;
+            int wall = -1;
+            for (int k = 0; k < 3; ++k) {
+                const float dk = comp(d, k), ok = comp(o, k);
+                float t;
+                if (dk > 0.0f) t = (h[7 + k] - ok) / dk;
+                else if (dk < 0.0f) t = (h[4 + k] - ok) / dk;
+                else continue;
+                if (t < tw) { tw = t; wall = 2 * k + (dk > 0.0f); }
+            }
+            if (wall >= 0 && tw < hit.t) {
+                const float px = o.x + tw * d.x, pz = o.z + tw * d.z;
+                const float* sk = h + 13;
+                const bool open = wall == 3 && sk[0] < sk[1] && px >= sk[0] && px <= sk[1] && pz >= sk[2] && pz <= sk[3];
+                if (!open) {
+                    hit.t = tw;
+                    hit.kind = 3;
+                    hit.id = wall;
+                }
+            }
+        }
+        if (hit.kind == 0) return false;
+        hit.p = make_float3(o.x + hit.t * d.x, o.y + hit.t * d.y, o.z + hit.t * d.z);
+        if (hit.kind == 1) {
+            const float r = sph[kSph * hit.id + 3];
+            const float3 c = centre(hit.id);
+            hit.n = make_float3((hit.p.x - c.x) / r, (hit.p.y - c.y) / r, (hit.p.z - c.z) / r);
+        } else if (hit.kind == 2) {
+            const int ax = hit.id % 3;
+            const float* B = box + kBox * (hit.id / 3);
+            const float mid = 0.5f * (B[ax] + B[3 + ax]);
+            const float s = comp(hit.p, ax) > mid ? 1.0f : -1.0f;
+            hit.n = make_float3(ax == 0 ? s : 0.0f, ax == 1 ? s : 0.0f, ax == 2 ? s : 0.0f);
+            hit.id /= 3;
+        } else {
+            const int ax = hit.id / 2;
+            const float s = (hit.id & 1) ? -1.0f : 1.0f;
+            hit.n = make_float3(ax == 0 ? s : 0.0f, ax == 1 ? s : 0.0f, ax == 2 ? s : 0.0f);
+        }
+        return true;
+    }
+
+    __device__ float3 albedo(const Hit& hh) const {
+        const float* a = hh.kind == 1 ? sph + kSph * hh.id + 4 : hh.kind == 2 ? box + kBox * hh.id + 6 : h + 18 + 3 * hh.id;
+        return make_float3(a[0], a[1], a[2]);
+    }
+
+    __device__ float3 emission(const Hit& hh) const {
+        if (hh.kind == 1) {
+            const float* e = sph + kSph * hh.id + 7;
+            return make_float3(e[0], e[1], e[2]);
+        }
+        return hh.kind == 3 ? make_float3(h[17], h[17], h[17]) : make_float3(0.0f, 0.0f, 0.0f);
+    }
+};
+
+// orthonormal basis around unit n (Duff et al., JCGT 2017)
+__device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
+    const float sgn = copysignf(1.0f, n.z), a = -1.0f / (sgn + n.z), bb = n.x * n.y * a;
+    t = make_float3(1.0f + sgn * n.x * n.x * a, sgn * bb, -sgn * n.x);
+    b = make_float3(bb, sgn + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ float3 cosine_dir(float3 n, float u1, float u2) {
+    float3 t, b;
+    onb(n, t, b);
+    const float r = sqrtf(u1), phi = 6.283185307179586f * u2;
+    const float x = r * cosf(phi), y = r * sinf(phi), z = sqrtf(fmaxf(1.0f - u1, 0.0f));
+    return make_float3(x * t.x + y * b.x + z * n.x, x * t.y + y * b.y + z * n.y, x * t.z + y * b.z + z * n.z);
+}
+
+// Incident radiance along one path starting at o in direction d.
+__device__ float3 path_radiance(const SceneView& S, const Rng& rng, uint32_t j, float3 o, float3 d, int mode,
+                                bool& first_hit, bool& first_back) {
+    float3 beta = make_float3(1.0f, 1.0f, 1.0f), L = make_float3(0.0f, 0.0f, 0.0f);
+    first_hit = false;
+    first_back = false;
+    for (int depth = 0; depth < kMaxDepth; ++depth) {
+        Hit hh;
+        if (!S.intersect(o, d, hh)) {
+            if (depth > 0 || mode == 0) {
+                L.x += beta.x * S.h[10];
+                L.y += beta.y * S.h[11];
+                L.z += beta.z * S.h[12];
+            }
+            return L;
+        }
+        const float cosi = dot3(d, hh.n);
+        if (depth == 0) {
+            first_hit = true;
+            first_back = cosi > 0.0f;
+        }
+        const float3 Le = S.emission(hh);
+        const bool nee_target = hh.kind == 1 && S.emits(hh.id);
+        if (depth == 0 ? mode == 0 : !nee_target) {
+            L.x += beta.x * Le.x;
+            L.y += beta.y * Le.y;
+            L.z += beta.z * Le.z;
+        }
+        const float3 rho = S.albedo(hh);
+        if (rho.x <= 0.0f && rho.y <= 0.0f && rho.z <= 0.0f) return L;
+        const float3 nf = cosi < 0.0f ? hh.n : make_float3(-hh.n.x, -hh.n.y, -hh.n.z);
+        const float3 p = make_float3(hh.p.x + kTEps * nf.x, hh.p.y + kTEps * nf.y, hh.p.z + kTEps * nf.z);
+        for (int e = 0; e < S.ns; ++e) {
+            if (!S.emits(e)) continue;
+            const float3 c = S.centre(e);
+            const float r = S.sph[kSph * e + 3];
+            float3 w = make_float3(c.x - p.x, c.y - p.y, c.z - p.z);
+            const float dist2 = dot3(w, w), dist = sqrtf(dist2);
+            if (dist <= r) continue;
+            w = make_float3(w.x / dist, w.y / dist, w.z / dist);
+            const float cmax = sqrtf(fmaxf(1.0f - r * r / dist2, 0.0f));
+            const float4 u = rng.draw(j, (uint32_t)depth, 1u + (uint32_t)e);
+            const float ct = 1.0f - u.x * (1.0f - cmax);
+            const float st = sqrtf(fmaxf(1.0f - ct * ct, 0.0f)), phi = 6.283185307179586f * u.y;
+            float3 tt, bb;
+            onb(w, tt, bb);
+            const float cs = st * cosf(phi), sn = st * sinf(phi);
+            const float3 wl = make_float3(cs * tt.x + sn * bb.x + ct * w.x, cs * tt.y + sn * bb.y + ct * w.y,
+                                          cs * tt.z + sn * bb.z + ct * w.z);
+            const float cosl = dot3(nf, wl);
+            if (cosl <= 0.0f) continue;
+            Hit hs;
+            if (!S.intersect(p, wl, hs) || hs.kind != 1 || hs.id != e) continue;
+            const float pdf_inv = 6.283185307179586f * (1.0f - cmax);
+            const float* Ee = S.sph + kSph * e + 7;
+            const float f = cosl * pdf_inv * 0.3183098861837907f;
+            L.x += beta.x * rho.x * Ee[0] * f;
+            L.y += beta.y * rho.y * Ee[1] * f;
+            L.z += beta.z * rho.z * Ee[2] * f;
+        }
+        const float4 u = rng.draw(j, (uint32_t)depth, 0u);
+        if (depth >= 3) {
+            const float q = fminf(fmaxf(fmaxf(beta.x, beta.y), beta.z), 0.95f);
+            if (u.z >= q) return L;
+            beta = make_float3(beta.x / q, beta.y / q, beta.z / q);
+        }
+        d = cosine_dir(nf, u.x, u.y);
+        beta = make_float3(beta.x * rho.x, beta.y * rho.y, beta.z * rho.z);
+        o = p;
+    }
+    return L;
+}
+
+__global__ void __launch_bounds__(128) mc_irradiance_kernel(SceneArg scene, const float4* __restrict__ x4,
+                                                            const float4* __restrict__ n4, const float* __restrict__ tq,
+                                                            int64_t m, int spp, uint64_t seed, uint64_t index_base,
+                                                            int mode, double* __restrict__ outE,
+                                                            uint8_t* __restrict__ keep) {
+    __shared__ float s_scene[kHdr + kSph * kMaxObjects];
+    const int len = kHdr + kSph * ((int)scene.v[0] + (int)scene.v[1]);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s_scene[k] = scene.v[k];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    SceneView S;
+    S.init(s_scene, tq ? tq[i] : 0.0f);
+    const Rng rng{index_base + (uint64_t)i, seed};
+    const float4 xq = x4[i], nq4 = n4[i];
+    const float3 x = make_float3(xq.x, xq.y, xq.z);
+    float3 n = make_float3(nq4.x, nq4.y, nq4.z);
+    const float nl = sqrtf(dot3(n, n));
+    n = make_float3(n.x / nl, n.y / nl, n.z / nl);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    int back = 0;
+    for (int j = 0; j < spp; ++j) {
+        const float4 u = rng.draw((uint32_t)j, 0xFFFFu, 0u);
+        const float3 w = cosine_dir(n, u.x, u.y);
+        bool fh, fb;
+        const float3 L = path_radiance(S, rng, (uint32_t)j, x, w, mode, fh, fb);
+        back += fb;
+        ax += L.x;
+        ay += L.y;
+        az += L.z;
+    }
+    const double k = 3.141592653589793 / (double)spp;
+    outE[3 * i + 0] = ax * k;
+    outE[3 * i + 1] = ay * k;
+    outE[3 * i + 2] = az * k;
+    if (keep) keep[i] = (uint8_t)(!(2 * back > spp) && !(ax == 0.0 && ay == 0.0 && az == 0.0));
+}
+
+}  // namespace
+
+int niv_launch_mc(const float* blob, int64_t blob_len, const float* x4, const float* n4, const float* t, int64_t m,
+                  int spp, uint64_t seed, uint64_t index_base, int mode, double* outE, uint8_t* keep, cudaStream_t s) {
+    const int ns = (int)blob[0], nb = (int)blob[1];
+    if (ns < 0 || nb < 0 || ns + nb > kMaxObjects) return niv_fail(NIV_ERR_UNSUPPORTED, "at most 56 scene objects");
+    if (blob_len != kHdr + kSph * ns + kBox * nb) return niv_fail(NIV_ERR_ARG, "scene description length mismatch");
+    SceneArg arg;
+    memset(&arg, 0, sizeof arg);
+    memcpy(arg.v, blob, sizeof(float) * blob_len);
+    const unsigned blocks = (unsigned)((m + 127) / 128);
+    mc_irradiance_kernel<<<blocks, 128, 0, s>>>(arg, (const float4*)x4, (const float4*)n4, t, m, spp, seed, index_base,
+                                                mode, outE, keep);
+    NIV_CUDA(cudaGetLastError());
+    return NIV_OK;
+}

@@ -490,6 +490,20 @@ int niv_fit(niv_handle h, const float* pos, const float* nrm, const float* t, co
     return niv_adam_step(h, fp->lr, fp->beta1, fp->beta2, fp->adam_eps, stream);
 }
 
+int niv_mc_irradiance(const float* scene, int64_t scene_len, const float* x4, const float* n4, const float* t,
+                      int64_t m, int32_t spp, uint64_t seed, uint64_t index_base, int32_t mode, double* out_E,
+                      uint8_t* out_keep, niv_stream stream) {
+    if (!scene || scene_len < 48) return niv_fail(NIV_ERR_ARG, "scene description missing or too short");
+    if (m < 0) return niv_fail(NIV_ERR_ARG, "m < 0");
+    if (m == 0) return NIV_OK;
+    if (!x4 || !n4 || !out_E) return niv_fail(NIV_ERR_ARG, "NULL pointer");
+    if (!aligned16(x4) || !aligned16(n4)) return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    if (spp < 1 || spp > 65535) return niv_fail(NIV_ERR_ARG, "spp must be in 1..65535");
+    if (mode != NIV_MC_TOTAL && mode != NIV_MC_INDIRECT) return niv_fail(NIV_ERR_ARG, "mode must be total or indirect");
+    return niv_launch_mc(scene, scene_len, x4, n4, t, m, spp, seed, index_base, mode, out_E, out_keep,
+                         (cudaStream_t)stream);
+}
+
 int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out_rgba,
               niv_stream stream) {
     if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");

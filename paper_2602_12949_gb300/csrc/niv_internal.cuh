@@ -115,6 +115,8 @@ int64_t niv_train_stash_floats(const niv_model* m, int64_t n);
 int niv_train_grad(niv_model* m, const GridArgs& g, const float4* pos, const float4* nrm, const float* t,
                    const float4* target, int64_t n, float eps, cudaStream_t s);
 int niv_train_adam(niv_model* m, float lr, float b1, float b2, float eps, cudaStream_t s);
+int niv_launch_mc(const float* blob, int64_t blob_len, const float* x4, const float* n4, const float* t, int64_t m,
+                  int spp, uint64_t seed, uint64_t index_base, int mode, double* outE, uint8_t* keep, cudaStream_t s);
 int niv_launch_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out, cudaStream_t s);
 int niv_pack_plain(niv_model* m, const float* mlp_host, cudaStream_t s);
 int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s);

@@ -233,5 +233,27 @@ def shade(albedo, direct, E, out=None, stream=None):
     return out
 
 
+def mc_irradiance(scene_blob, x4, n4, spp, seed=0, mode="indirect", t=None, index_base=0, stream=None):
+    """Monte Carlo irradiance (Eq. 1) at device points x4 / normals n4 ([m][4] float32).
+
+    Returns (E [m][3] float64 device tensor, keep [m] uint8 device tensor)."""
+    blob = np.ascontiguousarray(scene_blob, np.float32)
+    _check_records(x4, "x4")
+    _check_records(n4, "n4")
+    m = x4.shape[0]
+    E = torch.empty((m, 3), dtype=torch.float64, device=x4.device)
+    keep = torch.empty(m, dtype=torch.uint8, device=x4.device)
+    tp = 0
+    if t is not None:
+        t = t.contiguous().float()
+        tp = t.data_ptr()
+    md = {"total": _lib.NIV_MC_TOTAL, "indirect": _lib.NIV_MC_INDIRECT}[mode]
+    check(lib().niv_mc_irradiance(ctypes.c_void_p(blob.ctypes.data), blob.size, ctypes.c_void_p(x4.data_ptr()),
+                                  ctypes.c_void_p(n4.data_ptr()), ctypes.c_void_p(tp), m, int(spp), int(seed),
+                                  int(index_base), md, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(keep.data_ptr()),
+                                  _stream(stream)))
+    return E, keep
+
+
 def sync_status(stream=None):
     check(lib().niv_sync_status(_stream(stream)))
