@@ -248,6 +248,44 @@ NIV_API int niv_mc_irradiance(const float* scene, int64_t scene_len, const float
                               uint8_t* out_keep, niv_stream stream);
 
 /*
+ * Keep the samples niv_mc_irradiance flagged out_keep = 1 (Sec. 4.5 culling, App. I
+ * null discard), in their original order: out_x4, out_n4 (device float32 [m][4]),
+ * out_t (device float32 [m], nullable; copies t, or 0 when t is NULL) and
+ * out_target4 (device float32 [m][4]: E rounded to FP32, w = 0) receive the first
+ * *out_count (host) entries.  Synchronises `stream`.
+ */
+NIV_API int niv_compact_targets(const float* x4, const float* n4, const float* t, const double* E, const uint8_t* keep,
+                                int64_t m, float* out_x4, float* out_n4, float* out_t, float* out_target4,
+                                int64_t* out_count, niv_stream stream);
+
+/*
+ * Bake the SH probe grid of Sec. 5.1 / App. A: second-order real SH (9 coefficients
+ * per RGB channel) of the indirect incident radiance at every probe, projected from
+ * `rays` directions uniform on the sphere (one indirect path each).  Probes sit at the
+ * lattice vertices lo + (hi - lo) * ijk / (P - 1), x fastest; P, lo, hi are host
+ * arrays of 3.  out_coef64 (device float64 [Np][27], coefficient q of channel c at
+ * 3q + c; nullable) and/or out_coef16 (device float16 [Np][28], the same rounded to
+ * half precision plus one zero pad: 54 bytes of coefficients per probe; nullable).
+ * Random numbers: Philox4x32-10 as in niv_mc_irradiance (directions: counter
+ * (probe, ray + (0xFFFE << 16), 0); paths: stream index_base + probe * rays + ray).
+ * Asynchronous.
+ */
+NIV_API int niv_probe_bake(const float* scene, int64_t scene_len, const int32_t* P, const float* lo, const float* hi,
+                           int32_t rays, uint64_t seed, uint64_t index_base, double* out_coef64, void* out_coef16,
+                           niv_stream stream);
+
+/*
+ * Probe-grid irradiance at G-buffer records (App. A): trilinear weights over the 8
+ * probes of the cell around x, times the cosine fall-off max(0, n . normalize(p - x)),
+ * clamped below at 1e-6 and renormalised; each probe contributes its SH irradiance
+ * (Ramamoorthi & Hanrahan).  coef16: device float16 [Np][28] from niv_probe_bake.
+ * Records as in niv_query (image_width > 0: image traversal).  Asynchronous.
+ */
+NIV_API int niv_probe_query(const void* coef16, const int32_t* P, const float* lo, const float* hi, const void* pos,
+                            const void* nrm, int64_t n, int32_t dtype_in, void* out_E, int32_t dtype_out,
+                            int32_t image_width, niv_stream stream);
+
+/*
  * Largest n accepted by niv_query_host_noalloc: the number of records its fixed
  * staging area holds.
  */

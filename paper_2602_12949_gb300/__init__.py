@@ -4,6 +4,6 @@
 all the work; this package marshals torch tensors into it.
 """
 from ._lib import lib, NivError, LIB_PATH
-from .model import NIVModel, shade, sync_status, mc_irradiance, PRECISIONS
+from .model import NIVModel, ProbeGrid, shade, sync_status, mc_irradiance, compact_targets, PRECISIONS
 
-__all__ = ["lib", "NivError", "LIB_PATH", "NIVModel", "shade", "sync_status", "mc_irradiance", "PRECISIONS"]
+__all__ = ["lib", "NivError", "LIB_PATH", "NIVModel", "ProbeGrid", "shade", "sync_status", "mc_irradiance", "compact_targets", "PRECISIONS"]

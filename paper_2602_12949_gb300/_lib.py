@@ -64,6 +64,9 @@ _SIGNATURES = [
     ("niv_query", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),
     ("niv_query_host", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),
     ("niv_mc_irradiance", ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _I64, _I32, _U64, _U64, _I32, _VP, _VP, _VP]),
+    ("niv_compact_targets", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("niv_probe_bake", ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _I32, _U64, _U64, _VP, _VP, _VP]),
+    ("niv_probe_query", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _I64, _I32, _VP, _I32, _I32, _VP]),
     ("niv_grad", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, ctypes.POINTER(QueryParams), _F, _VP, _VP]),
     ("niv_get_grads", ctypes.c_int, [_VP, _VP, _I64, _VP]),
     ("niv_set_grads", ctypes.c_int, [_VP, _VP, _I64, _VP]),

@@ -15,6 +15,7 @@
 // purpose 0 = bounce direction + roulette, 1 + e = light sample toward emitter e;
 // the first direction of path j uses depth 0xFFFF.  u32 -> (0,1): (x >> 8) 2^-24 + 2^-25.
 #include <math.h>
+#include <string.h>
 
 #include "niv_internal.cuh"
 
@@ -332,6 +333,172 @@ int niv_launch_mc(const float* blob, int64_t blob_len, const float* x4, const fl
     const unsigned blocks = (unsigned)((m + 127) / 128);
     mc_irradiance_kernel<<<blocks, 128, 0, s>>>(arg, (const float4*)x4, (const float4*)n4, t, m, spp, seed, index_base,
                                                 mode, outE, keep);
+    NIV_CUDA(cudaGetLastError());
+    return NIV_OK;
+}
+
+// ---- SH probe bake (Sec. 5.1, App. A) ----
+// Per probe: second-order real SH (9 coefficients x RGB) of the indirect incident
+// radiance, L_lm = (4 pi / S) sum_j L_i(w_j) Y_lm(w_j), directions uniform on the sphere
+// from Philox counter (probe lo, probe hi, j + (0xFFFE << 16), 0); the path of ray j uses
+// stream index_base + probe * rays + j.  Probes sit at the lattice vertices
+// lo + (hi - lo) * ijk / (P - 1), x fastest.
+namespace {
+
+__device__ __forceinline__ void sh9(float3 w, float* Y) {
+    const float c0 = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
+    const float c1 = 0.4886025119029199f;   // sqrt(3 / (4 pi))
+    const float c2 = 1.0925484305920792f;   // sqrt(15 / pi) / 2
+    const float c20 = 0.31539156525252005f; // sqrt(5 / pi) / 4
+    const float c22 = 0.5462742152960396f;  // sqrt(15 / pi) / 4
+    Y[0] = c0;
+    Y[1] = c1 * w.y;
+    Y[2] = c1 * w.z;
+    Y[3] = c1 * w.x;
+    Y[4] = c2 * w.x * w.y;
+    Y[5] = c2 * w.y * w.z;
+    Y[6] = c20 * (3.0f * w.z * w.z - 1.0f);
+    Y[7] = c2 * w.x * w.z;
+    Y[8] = c22 * (w.x * w.x - w.y * w.y);
+}
+
+__global__ void __launch_bounds__(128) probe_bake_kernel(SceneArg scene, int px, int py, int pz, float3 lo, float3 hi,
+                                                         int rays, uint64_t seed, uint64_t index_base,
+                                                         double* __restrict__ out64, __half* __restrict__ out16) {
+    __shared__ float s_scene[kHdr + kSph * kMaxObjects];
+    const int len = kHdr + kSph * ((int)scene.v[0] + (int)scene.v[1]);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s_scene[k] = scene.v[k];
+    __syncthreads();
+    const int64_t np = (int64_t)px * py * pz;
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    SceneView S;
+    S.init(s_scene, 0.0f);
+    const int64_t i = p % px, j = (p / px) % py, k = p / ((int64_t)px * py);
+    const float3 x = make_float3(lo.x + (hi.x - lo.x) * (float)i / (float)(px - 1),
+                                 lo.y + (hi.y - lo.y) * (float)j / (float)(py - 1),
+                                 lo.z + (hi.z - lo.z) * (float)k / (float)(pz - 1));
+    double c[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) c[q] = 0.0;
+    for (int r = 0; r < rays; ++r) {
+        const uint4 o = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)(p >> 32), (uint32_t)r + (0xFFFEu << 16), 0u),
+                                      (uint32_t)seed, (uint32_t)(seed >> 32));
+        const float z = 1.0f - 2.0f * u01(o.x), rr = sqrtf(fmaxf(1.0f - z * z, 0.0f));
+        const float phi = 6.283185307179586f * u01(o.y);
+        const float3 w = make_float3(rr * cosf(phi), rr * sinf(phi), z);
+        const Rng rng{index_base + (uint64_t)p * (uint64_t)rays + (uint64_t)r, seed};
+        bool fh, fb;
+        const float3 L = path_radiance(S, rng, 0u, x, w, 1, fh, fb);
+        float Y[9];
+        sh9(w, Y);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            c[3 * q + 0] += (double)(L.x * Y[q]);
+            c[3 * q + 1] += (double)(L.y * Y[q]);
+            c[3 * q + 2] += (double)(L.z * Y[q]);
+        }
+    }
+    const double sc = 4.0 * 3.141592653589793 / (double)rays;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        if (out64) out64[p * 27 + q] = c[q] * sc;
+        if (out16) out16[p * 28 + q] = __float2half_rn((float)(c[q] * sc));
+    }
+    if (out16) out16[p * 28 + 27] = __float2half_rn(0.0f);
+}
+
+// ---- order-preserving compaction of kept Monte Carlo samples ----
+constexpr int kCB = 1024;  // elements per block
+
+__global__ void count_kept_kernel(const uint8_t* __restrict__ keep, int64_t m, int* __restrict__ block_counts) {
+    __shared__ int s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)kCB + threadIdx.x;
+    int c = 0;
+    for (int64_t k = i; k < min(m, (int64_t)(blockIdx.x + 1) * kCB); k += blockDim.x) c += keep[k] != 0;
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s, c);
+    __syncthreads();
+    if (threadIdx.x == 0) block_counts[blockIdx.x] = s;
+}
+
+__global__ void scan_blocks_kernel(int* __restrict__ counts, int nb, int64_t* __restrict__ total) {
+    // single thread: nb is small (m / 1024)
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            const int c = counts[b];
+            counts[b] = (int)acc;
+            acc += c;
+        }
+        *total = acc;
+    }
+}
+
+__global__ void __launch_bounds__(kCB) scatter_kept_kernel(const float4* __restrict__ x4, const float4* __restrict__ n4,
+                                                           const float* __restrict__ t, const double* __restrict__ E,
+                                                           const uint8_t* __restrict__ keep, int64_t m,
+                                                           const int* __restrict__ offsets, float4* __restrict__ ox4,
+                                                           float4* __restrict__ on4, float* __restrict__ ot,
+                                                           float4* __restrict__ otarget) {
+    __shared__ int warp_sums[kCB / 32];
+    const int64_t i = blockIdx.x * (int64_t)kCB + threadIdx.x;
+    const int flag = (i < m && keep[i]) ? 1 : 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = flag;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int v = warp_sums[lane];
+        int sc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xFFFFFFFFu, sc, o);
+            if (lane >= o) sc += u;
+        }
+        warp_sums[lane] = sc - v;  // exclusive prefix over warps
+    }
+    __syncthreads();
+    if (flag) {
+        const int64_t dst = (int64_t)offsets[blockIdx.x] + warp_sums[wid] + incl - 1;
+        ox4[dst] = x4[i];
+        on4[dst] = n4[i];
+        if (ot) ot[dst] = t ? t[i] : 0.0f;
+        otarget[dst] = make_float4((float)E[3 * i], (float)E[3 * i + 1], (float)E[3 * i + 2], 0.0f);
+    }
+}
+
+}  // namespace
+
+int niv_launch_probe_bake(const float* blob, int64_t blob_len, const int* P, const float* lo, const float* hi, int rays,
+                          uint64_t seed, uint64_t index_base, double* out64, __half* out16, cudaStream_t s) {
+    const int ns = (int)blob[0], nb = (int)blob[1];
+    if (ns < 0 || nb < 0 || ns + nb > kMaxObjects) return niv_fail(NIV_ERR_UNSUPPORTED, "at most 56 scene objects");
+    if (blob_len != kHdr + kSph * ns + kBox * nb) return niv_fail(NIV_ERR_ARG, "scene description length mismatch");
+    SceneArg arg;
+    memset(&arg, 0, sizeof arg);
+    memcpy(arg.v, blob, sizeof(float) * blob_len);
+    const int64_t np = (int64_t)P[0] * P[1] * P[2];
+    probe_bake_kernel<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(arg, P[0], P[1], P[2], make_float3(lo[0], lo[1], lo[2]),
+                                                                  make_float3(hi[0], hi[1], hi[2]), rays, seed, index_base,
+                                                                  out64, out16);
+    NIV_CUDA(cudaGetLastError());
+    return NIV_OK;
+}
+
+int niv_launch_compact(const float* x4, const float* n4, const float* t, const double* E, const uint8_t* keep, int64_t m,
+                       float* ox4, float* on4, float* ot, float* otarget, int64_t* count_dev, int* scratch,
+                       cudaStream_t s) {
+    const int nb = (int)((m + kCB - 1) / kCB);
+    count_kept_kernel<<<nb, 256, 0, s>>>(keep, m, scratch);
+    scan_blocks_kernel<<<1, 32, 0, s>>>(scratch, nb, count_dev);
+    scatter_kept_kernel<<<nb, kCB, 0, s>>>((const float4*)x4, (const float4*)n4, t, E, keep, m, scratch, (float4*)ox4,
+                                           (float4*)on4, ot, (float4*)otarget);
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }

@@ -20,6 +20,11 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 std::mutex g_status_mu;
 int* g_status[64] = {nullptr};
 
+// Scratch of the sample compaction (block offsets + count), per device ordinal, grown on demand.
+std::mutex g_compact_mu;
+void* g_compact[64] = {nullptr};
+size_t g_compact_bytes[64] = {0};
+
 __global__ void f32_to_f16_kernel(const float* __restrict__ src, __half* __restrict__ dst, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = __float2half_rn(src[i]);
@@ -502,6 +507,82 @@ int niv_mc_irradiance(const float* scene, int64_t scene_len, const float* x4, co
     if (mode != NIV_MC_TOTAL && mode != NIV_MC_INDIRECT) return niv_fail(NIV_ERR_ARG, "mode must be total or indirect");
     return niv_launch_mc(scene, scene_len, x4, n4, t, m, spp, seed, index_base, mode, out_E, out_keep,
                          (cudaStream_t)stream);
+}
+
+int niv_probe_bake(const float* scene, int64_t scene_len, const int32_t* P, const float* lo, const float* hi,
+                   int32_t rays, uint64_t seed, uint64_t index_base, double* out_coef64, void* out_coef16,
+                   niv_stream stream) {
+    if (!scene || scene_len < 48 || !P || !lo || !hi) return niv_fail(NIV_ERR_ARG, "NULL argument");
+    for (int a = 0; a < 3; ++a) {
+        if (P[a] < 2) return niv_fail(NIV_ERR_ARG, "every lattice axis needs at least 2 probes");
+        if (!(hi[a] > lo[a])) return niv_fail(NIV_ERR_ARG, "empty probe box");
+    }
+    if (rays < 1) return niv_fail(NIV_ERR_ARG, "rays must be positive");
+    if (!out_coef64 && !out_coef16) return niv_fail(NIV_ERR_ARG, "no output");
+    if (out_coef16 && !aligned16(out_coef16)) return niv_fail(NIV_ERR_ALIGN, "out_coef16 must be 16-byte aligned");
+    return niv_launch_probe_bake(scene, scene_len, P, lo, hi, rays, seed, index_base, out_coef64, (__half*)out_coef16,
+                                 (cudaStream_t)stream);
+}
+
+int niv_probe_query(const void* coef16, const int32_t* P, const float* lo, const float* hi, const void* pos,
+                    const void* nrm, int64_t n, int32_t dtype_in, void* out_E, int32_t dtype_out, int32_t image_width,
+                    niv_stream stream) {
+    if (!coef16 || !P || !lo || !hi) return niv_fail(NIV_ERR_ARG, "NULL argument");
+    if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
+    if (n == 0) return NIV_OK;
+    if (!pos || !nrm || !out_E) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if (!aligned16(pos) || !aligned16(nrm) || !aligned16(out_E) || !aligned16(coef16))
+        return niv_fail(NIV_ERR_ALIGN, "pointers must be 16-byte aligned");
+    if ((dtype_in != NIV_F32 && dtype_in != NIV_F16) || (dtype_out != NIV_F32 && dtype_out != NIV_F16))
+        return niv_fail(NIV_ERR_ARG, "record dtype must be NIV_F32 or NIV_F16");
+    for (int a = 0; a < 3; ++a) {
+        if (P[a] < 2) return niv_fail(NIV_ERR_ARG, "every lattice axis needs at least 2 probes");
+        if (!(hi[a] > lo[a])) return niv_fail(NIV_ERR_ARG, "empty probe box");
+    }
+    if (image_width < 0) return niv_fail(NIV_ERR_ARG, "image_width < 0");
+    IoArgs io;
+    io.pos = pos;
+    io.nrm = nrm;
+    io.out = out_E;
+    io.n = n;
+    io.image_width = image_width;
+    io.in_f16 = dtype_in == NIV_F16;
+    io.out_f16 = dtype_out == NIV_F16;
+    return niv_launch_probe_query(coef16, P, lo, hi, io, (cudaStream_t)stream);
+}
+
+int niv_compact_targets(const float* x4, const float* n4, const float* t, const double* E, const uint8_t* keep,
+                        int64_t m, float* out_x4, float* out_n4, float* out_t, float* out_target4, int64_t* out_count,
+                        niv_stream stream) {
+    if (!x4 || !n4 || !E || !keep || !out_x4 || !out_n4 || !out_target4 || !out_count)
+        return niv_fail(NIV_ERR_ARG, "NULL argument");
+    if (m < 0) return niv_fail(NIV_ERR_ARG, "m < 0");
+    *out_count = 0;
+    if (m == 0) return NIV_OK;
+    if (!aligned16(x4) || !aligned16(n4) || !aligned16(out_x4) || !aligned16(out_n4) || !aligned16(out_target4))
+        return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    int dev = 0;
+    NIV_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return niv_fail(NIV_ERR_UNSUPPORTED, "device ordinal above 63");
+    const size_t nb = (size_t)((m + 1023) / 1024);
+    const size_t need = 64 + nb * sizeof(int);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_compact_mu);
+    if (g_compact_bytes[dev] < need) {
+        NIV_CUDA(cudaStreamSynchronize(s));
+        cudaFree(g_compact[dev]);
+        g_compact[dev] = nullptr;
+        g_compact_bytes[dev] = 0;
+        NIV_CUDA(cudaMalloc(&g_compact[dev], need));
+        g_compact_bytes[dev] = need;
+    }
+    int64_t* count_dev = (int64_t*)g_compact[dev];
+    int* offsets = (int*)((char*)g_compact[dev] + 64);
+    int rc = niv_launch_compact(x4, n4, t, E, keep, m, out_x4, out_n4, out_t, out_target4, count_dev, offsets, s);
+    if (rc) return rc;
+    NIV_CUDA(cudaMemcpyAsync(out_count, count_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    NIV_CUDA(cudaStreamSynchronize(s));
+    return NIV_OK;
 }
 
 int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out_rgba,

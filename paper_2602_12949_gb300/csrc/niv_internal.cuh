@@ -117,6 +117,13 @@ int niv_train_grad(niv_model* m, const GridArgs& g, const float4* pos, const flo
 int niv_train_adam(niv_model* m, float lr, float b1, float b2, float eps, cudaStream_t s);
 int niv_launch_mc(const float* blob, int64_t blob_len, const float* x4, const float* n4, const float* t, int64_t m,
                   int spp, uint64_t seed, uint64_t index_base, int mode, double* outE, uint8_t* keep, cudaStream_t s);
+int niv_launch_probe_bake(const float* blob, int64_t blob_len, const int* P, const float* lo, const float* hi, int rays,
+                          uint64_t seed, uint64_t index_base, double* out64, __half* out16, cudaStream_t s);
+int niv_launch_probe_query(const void* coef16, const int* P, const float* lo, const float* hi, const IoArgs& io,
+                           cudaStream_t s);
+int niv_launch_compact(const float* x4, const float* n4, const float* t, const double* E, const uint8_t* keep, int64_t m,
+                       float* ox4, float* on4, float* ot, float* otarget, int64_t* count_dev, int* scratch,
+                       cudaStream_t s);
 int niv_launch_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out, cudaStream_t s);
 int niv_pack_plain(niv_model* m, const float* mlp_host, cudaStream_t s);
 int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s);

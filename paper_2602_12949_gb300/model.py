@@ -255,5 +255,58 @@ def mc_irradiance(scene_blob, x4, n4, spp, seed=0, mode="indirect", t=None, inde
     return E, keep
 
 
+def compact_targets(x4, n4, E, keep, t=None, stream=None):
+    """Kept samples in order: (x4, n4, target4, t or None), each cut to the kept count."""
+    m = x4.shape[0]
+    ox, on, ot4 = (torch.empty((m, 4), dtype=torch.float32, device=x4.device) for _ in range(3))
+    ot = torch.empty(m, dtype=torch.float32, device=x4.device) if t is not None else None
+    cnt = ctypes.c_int64()
+    check(lib().niv_compact_targets(ctypes.c_void_p(x4.data_ptr()), ctypes.c_void_p(n4.data_ptr()),
+                                    ctypes.c_void_p(t.data_ptr() if t is not None else 0),
+                                    ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(keep.data_ptr()), m,
+                                    ctypes.c_void_p(ox.data_ptr()), ctypes.c_void_p(on.data_ptr()),
+                                    ctypes.c_void_p(ot.data_ptr() if ot is not None else 0),
+                                    ctypes.c_void_p(ot4.data_ptr()), ctypes.byref(cnt), _stream(stream)))
+    k = cnt.value
+    return ox[:k], on[:k], ot4[:k], (ot[:k] if ot is not None else None)
+
+
+class ProbeGrid:
+    """SH probe lattice over [lo, hi] with P[0] x P[1] x P[2] probes (App. A); FP16 coefficients."""
+
+    def __init__(self, P, lo, hi, device="cuda"):
+        self.P = np.ascontiguousarray(P, np.int32)
+        self.lo = np.ascontiguousarray(lo, np.float32)
+        self.hi = np.ascontiguousarray(hi, np.float32)
+        self.count = int(np.prod(self.P))
+        self.coef16 = torch.zeros((self.count, 28), dtype=torch.float16, device=device)
+
+    @property
+    def nbytes(self):
+        return 54 * self.count  # coefficient bytes (the stored records add a 2-byte pad)
+
+    def bake(self, scene_blob, rays, seed=0, index_base=0, want_f64=False, stream=None):
+        blob = np.ascontiguousarray(scene_blob, np.float32)
+        c64 = torch.empty((self.count, 27), dtype=torch.float64, device=self.coef16.device) if want_f64 else None
+        check(lib().niv_probe_bake(ctypes.c_void_p(blob.ctypes.data), blob.size, ctypes.c_void_p(self.P.ctypes.data),
+                                   ctypes.c_void_p(self.lo.ctypes.data), ctypes.c_void_p(self.hi.ctypes.data),
+                                   int(rays), int(seed), int(index_base),
+                                   ctypes.c_void_p(c64.data_ptr() if c64 is not None else 0),
+                                   ctypes.c_void_p(self.coef16.data_ptr()), _stream(stream)))
+        return c64
+
+    def query(self, pos, nrm, out=None, image_width=0, out_dtype=None, stream=None):
+        _check_records(pos, "pos")
+        _check_records(nrm, "nrm")
+        if out is None:
+            out = torch.empty(pos.shape, dtype=out_dtype or pos.dtype, device=pos.device)
+        check(lib().niv_probe_query(ctypes.c_void_p(self.coef16.data_ptr()), ctypes.c_void_p(self.P.ctypes.data),
+                                    ctypes.c_void_p(self.lo.ctypes.data), ctypes.c_void_p(self.hi.ctypes.data),
+                                    ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()), pos.shape[0],
+                                    _rec_dtype(pos), ctypes.c_void_p(out.data_ptr()), _rec_dtype(out), int(image_width),
+                                    _stream(stream)))
+        return out
+
+
 def sync_status(stream=None):
     check(lib().niv_sync_status(_stream(stream)))
