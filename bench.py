@@ -239,11 +239,37 @@ def _more_workloads(a, dev, flush, stream, steps=10, warmup=3):
         r[prec] = {"ms_per_frame": ms, "gqueries_per_s": npx / (ms * 1e-3) / 1e9}
     res["config3_4k"] = r
     m3.close()
-    dalb = torch.from_numpy(alb).to(dev)
-    direct = torch.rand((npx, 4), device=dev, generator=torch.Generator(device=dev).manual_seed(0)).half()
+    # config 4: room + three inserted meshes, fused query + shading into FP16 rgba
+    from niv_inputs.configs import MODEL_C4
+    from niv_inputs.meshes import shading_frame
+    p4, n4, a4, d4, cov = shading_frame(w, h)
+    dp4, dn4, da4, dd4 = (torch.from_numpy(x).to(dev) for x in (p4, n4, a4, d4))
     rgba = torch.empty_like(out16)
-    ms = _time_launches(lambda: shade(dalb, direct, out16, out=rgba), steps, warmup, flush, stream)
-    res["shade_4k"] = {"ms": ms, "gb_per_s": 32 * npx / (ms * 1e-3) / 1e9}
+    m4 = NIVModel(**MODEL_C4)
+    g, _ = m4.param_count()
+    m4.set_params(init_params(g, m4.layer_shapes(), seed=0))
+    r = {"coverage": cov}
+    for prec in ("fp16", "fp32"):
+        ms = _time_launches(lambda: m4.query_shade(dp4, dn4, da4, dd4, out=rgba, precision=prec, **kw), steps, warmup,
+                            flush, stream)
+        r[prec + "_fused"] = {"ms_per_frame": ms, "gqueries_per_s": npx / (ms * 1e-3) / 1e9}
+    ms_q = _time_launches(lambda: m4.query(dp4, dn4, out=out16, precision="fp16", **kw), steps, warmup, flush, stream)
+    ms_s = _time_launches(lambda: shade(da4, dd4, out16, out=rgba), steps, warmup, flush, stream)
+    r["fp16_query_then_shade"] = {"ms_per_frame": ms_q + ms_s, "shade_ms": ms_s,
+                                  "shade_gb_per_s": 32 * npx / (ms_s * 1e-3) / 1e9}
+    res["config4_4k"] = r
+    m4.close()
+    # the non-neural path beside it: SH probe grid with the config-1 model's memory, 1080p frame
+    from paper_2602_12949_gb300 import ProbeGrid
+    from niv_inputs import room_scene
+    pos1, nrm1, _ = room_gbuffer(1920, 1080)
+    dp1, dn1 = torch.from_numpy(pos1).to(dev), torch.from_numpy(nrm1).to(dev)
+    o1 = torch.empty((1920 * 1080, 4), dtype=torch.float16, device=dev)
+    grid = ProbeGrid((50, 50, 50), ROOM_MIN, ROOM_MAX)
+    grid.bake(room_scene(0).blob(), rays=256, seed=0)
+    ms = _time_launches(lambda: grid.query(dp1, dn1, out=o1, image_width=1920), steps, warmup, flush, stream)
+    res["probes_1080p"] = {"probes": 125000, "mb": grid.nbytes / 1e6, "ms_per_frame": ms,
+                           "gqueries_per_s": 1920 * 1080 / (ms * 1e-3) / 1e9}
     return res
 
 

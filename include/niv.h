@@ -315,6 +315,17 @@ NIV_API int niv_query_host_noalloc(niv_handle h, const void* pos, const void* nr
                                    int32_t precision, niv_stream stream);
 
 /*
+ * The query with shading fused into its epilogue (Sec. 4.4 then Eq. 2 and the
+ * runtime direct light of Sec. 3 / Fig. 3): for each record the kernel evaluates E
+ * and writes rgba = (albedo * E / pi + direct, 1) straight to out_rgba, so E never
+ * reaches memory.  albedo, direct, out_rgba: device FP16 [n][4] records; pos, nrm as
+ * in niv_query.  Asynchronous.
+ */
+NIV_API int niv_query_shade(niv_handle h, const void* pos, const void* nrm, const void* albedo, const void* direct,
+                            int64_t n, int32_t dtype_in, const niv_query_params* params, void* out_rgba,
+                            int32_t precision, niv_stream stream);
+
+/*
  * Encoding only (Sec. 4.1), for inspection and parity checks: for each of the n
  * position records, out_enc (device float32 [n][levels*feat], nullable)
  * receives the interpolated level features in FP32 from the FP32 master grid,

@@ -74,6 +74,7 @@ _SIGNATURES = [
     ("niv_fit", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, ctypes.POINTER(QueryParams), ctypes.POINTER(FitParams), _VP, _VP]),
     ("niv_fp8_calibrate", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP]),
     ("niv_fp8_get_scales", ctypes.c_int, [_VP, _VP, _VP, _VP, _I32]),
+    ("niv_query_shade", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _VP]),
     ("niv_query_host_noalloc", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),
     ("niv_encode", ctypes.c_int, [_VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _VP, _VP]),
     ("niv_selftest_mma", ctypes.c_int, [_I32, _VP, _VP]),

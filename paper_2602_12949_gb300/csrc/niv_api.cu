@@ -585,6 +585,44 @@ int niv_compact_targets(const float* x4, const float* n4, const float* t, const 
     return NIV_OK;
 }
 
+int niv_query_shade(niv_handle h, const void* pos, const void* nrm, const void* albedo, const void* direct, int64_t n,
+                    int32_t dtype_in, const niv_query_params* params, void* out_rgba, int32_t precision,
+                    niv_stream stream) {
+    if (!h || !params) return niv_fail(NIV_ERR_ARG, "handle or params is NULL");
+    if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
+    if (n == 0) return NIV_OK;
+    if (!pos || !nrm || !albedo || !direct || !out_rgba) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if (!aligned16(pos) || !aligned16(nrm) || !aligned16(albedo) || !aligned16(direct) || !aligned16(out_rgba))
+        return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    if (dtype_in != NIV_F32 && dtype_in != NIV_F16) return niv_fail(NIV_ERR_ARG, "record dtype must be NIV_F32 or NIV_F16");
+    for (int k = 0; k < 3; ++k)
+        if (!(params->aabb_max[k] > params->aabb_min[k])) return niv_fail(NIV_ERR_ARG, "empty aabb");
+    if (params->image_width < 0) return niv_fail(NIV_ERR_ARG, "image_width < 0");
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (h->infer_dirty) {
+        rc = refresh_inference(h, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    GridArgs g = niv_grid_args(h, params);
+    IoArgs io;
+    io.pos = pos;
+    io.nrm = nrm;
+    io.out = out_rgba;
+    io.n = n;
+    io.image_width = params->image_width;
+    io.in_f16 = dtype_in == NIV_F16;
+    io.out_f16 = 1;
+    io.albedo = albedo;
+    io.direct = direct;
+    switch (precision) {
+        case NIV_FP32: return niv_launch_query_fp32(h, g, io, (cudaStream_t)stream);
+        case NIV_FP16: return niv_launch_query_tc(h, g, io, precision, (cudaStream_t)stream);
+        case NIV_FP8: return niv_launch_query_f8(h, g, io, (cudaStream_t)stream);
+        default: return niv_fail(NIV_ERR_UNSUPPORTED, "precision not supported");
+    }
+}
+
 int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out_rgba,
               niv_stream stream) {
     if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");

@@ -45,6 +45,10 @@ struct IoArgs {
     int32_t image_width;  // > 0: 2-D tile traversal of a row-major image
     int32_t in_f16;       // records are FP16 (else FP32)
     int32_t out_f16;
+    // Fused shading (Eq. 2 + direct light): when albedo is set, out receives FP16
+    // rgba = (albedo * E / pi + direct, 1) instead of E.  FP16 [n][4] records.
+    const void* albedo = nullptr;
+    const void* direct = nullptr;
 };
 
 struct niv_model {
@@ -353,6 +357,22 @@ __device__ __forceinline__ void niv_store_rec(void* base, int64_t i, float x, fl
         reinterpret_cast<uint2*>(base)[i] = r;
     } else {
         reinterpret_cast<float4*>(base)[i] = make_float4(x, y, z, 0.0f);
+    }
+}
+
+// Final store of a query: E, or the shaded rgba when the call fused shading.
+__device__ __forceinline__ void niv_store_result(const IoArgs& io, int64_t i, float e0, float e1, float e2) {
+    if (io.albedo) {
+        const float inv_pi = 0.318309886183790671538f;
+        const float4 a = niv_load_rec(io.albedo, i, true), d = niv_load_rec(io.direct, i, true);
+        __half2 rg = __floats2half2_rn(fmaf(a.x * e0, inv_pi, d.x), fmaf(a.y * e1, inv_pi, d.y));
+        __half2 ba = __floats2half2_rn(fmaf(a.z * e2, inv_pi, d.z), 1.0f);
+        uint2 r;
+        r.x = *reinterpret_cast<uint32_t*>(&rg);
+        r.y = *reinterpret_cast<uint32_t*>(&ba);
+        reinterpret_cast<uint2*>(io.out)[i] = r;
+    } else {
+        niv_store_rec(io.out, i, e0, e1, e2, io.out_f16);
     }
 }
 

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kT, 8) query_f8_kernel(GridArgs g, IoArgs io, 
             z1 = niv_softplus(z1);
             z2 = niv_softplus(z2);
         }
-        if (valid) niv_store_rec(io.out, r, z0, z1, z2, io.out_f16);
+        if (valid) niv_store_result(io, r, z0, z1, z2);
         tc::fence_before_sync();
         __syncthreads();
     }

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) query_fp32_kernel(GridArgs g, IoArgs
             z1 = niv_softplus(z1);
             z2 = niv_softplus(z2);
         }
-        if (valid) niv_store_rec(io.out, r, z0, z1, z2, io.out_f16);
+        if (valid) niv_store_result(io, r, z0, z1, z2);
     }
 }
 

@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             z1 = niv_softplus(z1);
             z2 = niv_softplus(z2);
         }
-        if (valid) niv_store_rec(io.out, r, z0, z1, z2, io.out_f16);
+        if (valid) niv_store_result(io, r, z0, z1, z2);
         tc::fence_before_sync();
         group_sync(wg);  // the next tile's encoder overwrites the activation tile
     }

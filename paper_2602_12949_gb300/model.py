@@ -124,6 +124,22 @@ class NIVModel:
                               _rec_dtype(out), PRECISIONS[precision], _stream(stream)))
         return out
 
+    def query_shade(self, pos, nrm, albedo, direct, out=None, precision="fp16", aabb_min=(0.0, 0.0, 0.0),
+                    aabb_max=(1.0, 1.0, 1.0), t=0.0, image_width=0, stream=None):
+        """Fused query + shading: FP16 rgba = (albedo * E / pi + direct, 1) for every record."""
+        for a, name in ((pos, "pos"), (nrm, "nrm"), (albedo, "albedo"), (direct, "direct")):
+            _check_records(a, name)
+        if albedo.dtype != torch.float16 or direct.dtype != torch.float16:
+            raise TypeError("albedo and direct must be float16 records")
+        if out is None:
+            out = torch.empty((pos.shape[0], 4), dtype=torch.float16, device=pos.device)
+        qp = self.query_params(aabb_min, aabb_max, t, image_width)
+        check(lib().niv_query_shade(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                                    ctypes.c_void_p(albedo.data_ptr()), ctypes.c_void_p(direct.data_ptr()),
+                                    pos.shape[0], _rec_dtype(pos), ctypes.byref(qp), ctypes.c_void_p(out.data_ptr()),
+                                    PRECISIONS[precision], _stream(stream)))
+        return out
+
     def query_host(self, pos, nrm, out=None, precision="fp16", aabb_min=(0.0, 0.0, 0.0),
                    aabb_max=(1.0, 1.0, 1.0), t=0.0, image_width=0, stream=None):
         """Same as query for host arrays (numpy or CPU tensors); copies in and out inside the call."""

@@ -37,3 +37,24 @@ def test_gbuffer_hits_everything_inside_the_closed_room():
     # normals face the camera
     d = pos - np.array(CAMERA_POS)
     assert np.all(np.einsum("ij,ij->i", d, nrm) < 0)
+
+
+def test_dynamic_objects_recipe():
+    from niv_inputs.meshes import torus, icosphere, twisted_box, dynamic_objects
+    assert len(torus()[1]) == 50000 and len(icosphere()[1]) == 81920 and len(twisted_box()[1]) == 49152
+    v, f = torus()
+    assert len(v) - (3 * len(f) // 2) + len(f) == 0      # Euler characteristic of a torus
+    v, f = icosphere()
+    assert len(v) - (3 * len(f) // 2) + len(f) == 2      # ... of a sphere
+    np.testing.assert_allclose(np.linalg.norm(v, axis=1), 0.6, rtol=1e-12)
+    verts, tris, ids, albedo = dynamic_objects(0)
+    assert tris.max() < len(verts) and set(np.unique(ids)) == {0, 1, 2}
+    assert np.all((albedo >= 0.1) & (albedo <= 0.9))
+
+
+def test_shading_frame_coverage(tmp_path):
+    from niv_inputs.meshes import shading_frame
+    pos, nrm, alb, direct, cov = shading_frame(960, 540, cache_dir=str(tmp_path))
+    assert 0.04 <= cov <= 0.12  # dynamic objects cover 5-10% of the frame (Sec. 5.2)
+    assert np.all(np.isfinite(pos.astype(np.float32)))
+    assert np.all((direct[:, :3] >= 0) & (direct[:, :3] <= 0.5))
