@@ -35,13 +35,13 @@
 namespace {
 
 #ifndef NIV_TC_WG
-#define NIV_TC_WG 1
+#define NIV_TC_WG 8
 #endif
 #ifndef NIV_TC_ILP
 #define NIV_TC_ILP 1
 #endif
 #ifndef NIV_TC_MINB
-#define NIV_TC_MINB 8
+#define NIV_TC_MINB 1
 #endif
 constexpr int kT = 128;          // rows per tile = threads per warpgroup
 constexpr int kWG = NIV_TC_WG;   // warpgroups (independent tile pipelines) per CTA
@@ -101,7 +101,7 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t act, uint32_
 // Encode levels [l0, l0 + G) of one record into one 16-byte chunk of FP16 features,
 // kILP levels' gathers in flight at a time.
 template <int DIMS, int F>
-__device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const __half* __restrict__ grid16, int l0,
+__device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const __half* __restrict__ grid16, int l0, int L,
                                               const float* u) {
     constexpr int NC = 1 << DIMS, G = 8 / F;
     using R = typename NivRaw<F, __half>::T;
@@ -109,7 +109,7 @@ __device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const __half* _
 #pragma unroll
     for (int q = 0; q < G; q += kILP) {
         const int la = l0 + q, lb = l0 + q + 1;
-        const bool has_a = la < g.levels, has_b = kILP == 2 && (q + 1 < G) && lb < g.levels;
+        const bool has_a = la < L, has_b = kILP == 2 && (q + 1 < G) && lb < L;
         uint32_t ea[NC], eb[NC];
         float wa[NC], wb[NC];
         R ra[NC], rb[NC];
@@ -141,7 +141,9 @@ __device__ __forceinline__ void group_sync(int wg) { asm volatile("bar.sync %0, 
 
 // kWG independent warpgroups per CTA; each owns a 128-row tile pipeline (activation tile,
 // mbarrier, named barrier, 64 TMEM columns) and all share the weights in shared memory.
-template <int DIMS, int F>
+// LV > 0: the level count is a compile-time constant, so the level loop unrolls fully and
+// every per-level constant (resolution, table offset, dense flag) is an immediate operand.
+template <int DIMS, int F, int LV>
 __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(GridArgs g, IoArgs io,
                                                                 const __half* __restrict__ grid16,
                                                                 const uint8_t* __restrict__ packed, TcLayout lay,
@@ -172,14 +174,15 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
     __syncthreads();
     tc::fence_after_sync();
 
-    const uint32_t tmem = *s_tmem + (uint32_t)wg * (tmem_cols / kWG);
+    const uint32_t wg_cols = lay.W <= 32 ? 32u : 64u;  // accumulator columns of one warpgroup
+    const uint32_t tmem = *s_tmem + (uint32_t)wg * wg_cols;
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     const uint32_t bar = tc::smem_u32(s_bar + wg);
     const uint32_t act_a = tc::smem_u32(s_act), net_a = tc::smem_u32(s_net);
     const float* s_bias = reinterpret_cast<const float*>(s_net + lay.bias);  // layers 1.. and b_out
     const float* s_wout = reinterpret_cast<const float*>(s_net + lay.wout);  // FP32 [3][W]
     const uint32_t idesc_h = tc::idesc_f16(128, W), idesc_o = tc::idesc_f16(128, kNO);
-    const int L = g.levels;
+    const int L = LV > 0 ? LV : g.levels;
     constexpr int G = 8 / F;
     uint32_t phase = 0;
     bool ok = true;
@@ -197,8 +200,14 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         u[3] = fminf(fmaxf(g.t, 0.0f), 1.0f);
 
         // ---- 1. encoding -> FP16 input row, one 16-byte chunk per G levels ----
-        for (int l0 = 0; l0 < L; l0 += G)
-            *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid16, l0, u);
+        if (LV > 0) {
+#pragma unroll
+            for (int l0 = 0; l0 < LV; l0 += G)
+                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid16, l0, LV, u);
+        } else {
+            for (int l0 = 0; l0 < L; l0 += G)
+                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid16, l0, L, u);
+        }
         {   // [n.x, n.y, n.z, (t), 1, 0, ...]: the 1 multiplies the first layer's bias column
             const bool has_t = g.n_in > L * F + 3;
             const uint32_t one = (uint32_t)__half_as_ushort(__float2half_rn(1.0f));
@@ -307,13 +316,12 @@ size_t tc_smem_bytes(const TcLayout& lay) {
     return (size_t)kHdr + ((lay.total + 127u) & ~127u) + (size_t)kWG * kT * kmax * 2;
 }
 
-template <int DIMS, int F>
+template <int DIMS, int F, int LV>
 int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s, int* status) {
     const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
-    auto kern = query_tc_f16_kernel<DIMS, F>;
+    auto kern = query_tc_f16_kernel<DIMS, F, LV>;
     const size_t smem = tc_smem_bytes(*lay);
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
     int dev = 0, sms = 0;
     NIV_CUDA(cudaGetDevice(&dev));
     NIV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -328,14 +336,23 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
     const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 1;
     const int by_regs = regs_per_sm / (kT * kWG * regs);
     int per_sm = by_smem < by_regs ? by_smem : by_regs;
-    const uint32_t cols = (lay->W <= 32 ? 32u : 64u) * kWG;
+    // TMEM is allocated in powers of two from 32 to 512 columns: round the CTA's need up.
+    uint32_t cols = 32u;
+    while (cols < (lay->W <= 32 ? 32u : 64u) * (uint32_t)kWG) cols <<= 1;
+    if (cols > 512u) return niv_fail(NIV_ERR_UNSUPPORTED, "too many warpgroups for tensor memory");
     const int forced = niv_env_int("NIV_TC_BLOCKS_PER_SM", 0);
     if (forced > 0) per_sm = forced;
     if (per_sm > (int)(512 / cols)) per_sm = (int)(512 / cols);  // never oversubscribe TMEM
     if (per_sm < 1) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core query kernel does not fit on an SM");
+    // Ask for just the shared memory the resident CTAs need: the rest of the SM's unified
+    // L1 / shared storage then serves as L1 cache for the feature gathers.
+    int carve = (int)((100 * (int64_t)per_sm * (int64_t)(smem + 1024) + smem_per_sm - 1) / smem_per_sm);
+    carve = niv_env_int("NIV_TC_CARVEOUT", carve);
+    if (carve > 100) carve = 100;
+    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
     if (niv_env_int("NIV_VERBOSE", 0))
-        fprintf(stderr, "niv: fp16 query: smem %zu B, regs %d, smem %d/SM, regs %d/SM, launching %d/SM\n", smem,
-                fa.numRegs, by_smem, by_regs, per_sm);
+        fprintf(stderr, "niv: fp16 query: smem %zu B, regs %d, smem %d/SM, regs %d/SM, launching %d/SM, carveout %d%%\n",
+                smem, fa.numRegs, by_smem, by_regs, per_sm, carve);
     if (!status) status = niv_status_word();
     if (!status) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
     const int64_t tiles = niv_tile_count_host(io.n, io.image_width);
@@ -349,10 +366,17 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
 
 template <int DIMS>
 int by_feat(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s, int* status) {
+    // fully unrolled encoders for the common level counts (16: configs 1, 3, 4; 8: config 0 and the
+    // paper's 8-level model), a runtime loop otherwise
     switch (m->d.feat) {
-        case 1: return launch<DIMS, 1>(m, g, io, s, status);
-        case 2: return launch<DIMS, 2>(m, g, io, s, status);
-        case 4: return launch<DIMS, 4>(m, g, io, s, status);
+        case 1: return launch<DIMS, 1, 0>(m, g, io, s, status);
+        case 2:
+            if (g.levels == 16) return launch<DIMS, 2, 16>(m, g, io, s, status);
+            if (g.levels == 8) return launch<DIMS, 2, 8>(m, g, io, s, status);
+            return launch<DIMS, 2, 0>(m, g, io, s, status);
+        case 4:
+            if (g.levels == 8) return launch<DIMS, 4, 8>(m, g, io, s, status);
+            return launch<DIMS, 4, 0>(m, g, io, s, status);
     }
     return niv_fail(NIV_ERR_UNSUPPORTED, "feat must be 1, 2 or 4");
 }
