@@ -130,6 +130,24 @@ def _profiled_traffic():
         return None
 
 
+def reduce_max(values, ws, device=None):
+    """Max over ranks of each entry of `values` (floats); the values themselves when ws == 1.
+    Every rank must call it with the same number of entries."""
+    if ws <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def weak_throughput(units_per_rank, ws, seconds):
+    """Whole-job rate (G units/s) of `ws` replicas that each processed `units_per_rank`
+    units, the slowest of them in `seconds`."""
+    return units_per_rank * ws / seconds / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,13 +345,6 @@ def main():
 
     with ClockSampler(torch.cuda.current_device() if ws == 1 else local) as clk:
         ms = timed(a.precision, out, a.steps, a.warmup)
-    ms_total = sum(ms)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / a.steps
-    value = npx * ws / (ms_step * 1e-3) / 1e9
 
     extra = {}
     if not a.no_compare:
@@ -354,7 +365,10 @@ def main():
         t0 = time.perf_counter()
         model.query_host(hp, hn, out=ho, precision=a.precision, **qkw)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_val = npx / statistics.mean(e2e_t) / 1e9
+    ms_total, e2e_total = reduce_max([sum(ms), sum(e2e_t)], ws, dev)
+    ms_step = ms_total / a.steps
+    value = weak_throughput(npx, ws, ms_step * 1e-3)
+    e2e_val = weak_throughput(npx, ws, e2e_total / len(e2e_t))
 
     if rank != 0:
         if ws > 1:
@@ -373,7 +387,7 @@ def main():
 
     cpu = None
     errs = {}
-    if not a.no_cpu_baseline:
+    if not a.no_cpu_baseline and ws == 1:
         import oracle
         om = oracle.Model(**MODEL_C1)
         sample = 1 << 17
@@ -406,7 +420,7 @@ def main():
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "Gqueries/s", "h2d_bytes_per_step": int(2 * hp.nbytes),
-                "d2h_bytes_per_step": int(ho.nbytes), "ms_per_frame": 1e3 * statistics.mean(e2e_t)},
+                "d2h_bytes_per_step": int(ho.nbytes), "ms_per_frame": 1e3 * e2e_total / len(e2e_t)},
         "clocks": clk.summary(),
         "gpu_launches": a.steps,
         "err_vs_fp64": errs,
