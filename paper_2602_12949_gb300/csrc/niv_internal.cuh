@@ -187,22 +187,27 @@ __device__ __forceinline__ void niv_level_corners(const GridArgs& g, int l, cons
         w0[d] = 1.0f - w1[d];
     }
     {
-        float wh[NC / 2];
-        wh[0] = w0[1] * w0[2];
-        wh[1] = w1[1] * w0[2];
-        wh[2] = w0[1] * w1[2];
-        wh[3] = w1[1] * w1[2];
+        // Products in pairs on the packed FP32 pipe: each lane is an ordinary FP32 product,
+        // so the weights are those of the scalar formulas.
+        const float2 wy = make_float2(w0[1], w1[1]), wx = make_float2(w0[0], w1[0]);
+        float2 wh[NC / 4];  // wh[q] = (w_y0 * w_rest_q, w_y1 * w_rest_q)
+        wh[0] = __fmul2_rn(wy, make_float2(w0[2], w0[2]));
+        wh[1] = __fmul2_rn(wy, make_float2(w1[2], w1[2]));
         if (DIMS == 4) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                wh[(q + 4) % (NC / 2)] = wh[q] * w1[DIMS - 1];
-                wh[q] = wh[q] * w0[DIMS - 1];
-            }
+            const float2 t0 = make_float2(w0[DIMS - 1], w0[DIMS - 1]), t1 = make_float2(w1[DIMS - 1], w1[DIMS - 1]);
+            wh[2 % (NC / 4)] = __fmul2_rn(wh[0], t1);
+            wh[3 % (NC / 4)] = __fmul2_rn(wh[1], t1);
+            wh[0] = __fmul2_rn(wh[0], t0);
+            wh[1] = __fmul2_rn(wh[1], t0);
         }
 #pragma unroll
-        for (int q = 0; q < NC / 2; ++q) {
-            wc[2 * q] = w0[0] * wh[q];
-            wc[2 * q + 1] = w1[0] * wh[q];
+        for (int q = 0; q < NC / 4; ++q) {
+            const float2 a = __fmul2_rn(wx, make_float2(wh[q].x, wh[q].x));
+            const float2 b = __fmul2_rn(wx, make_float2(wh[q].y, wh[q].y));
+            wc[4 * q] = a.x;
+            wc[4 * q + 1] = a.y;
+            wc[4 * q + 2] = b.x;
+            wc[4 * q + 3] = b.y;
         }
     }
     if ((g.dense_mask >> l) & 1u) {
@@ -324,6 +329,43 @@ __device__ __forceinline__ int64_t niv_record_of(int64_t tile, int k, int64_t n,
     if (px >= width) return n;  // outside the image: no record
     return py * width + px;
 }
+
+// Persistent walk over 128-record tiles with a fixed stride, in the record order of
+// niv_record_of: the image tile coordinates (tx, ty) advance by the stride's column and
+// row parts, so no tile costs a 64-bit division.
+struct NivTileWalk {
+    int64_t tile, stride, ty, sy;
+    int32_t tiles_x, tx, sx, ox, oy;
+
+    __device__ __forceinline__ void init(int64_t first, int64_t step, int k, int32_t width) {
+        tile = first;
+        stride = step;
+        const int w = k >> 5, lane = k & 31;
+        ox = (w & 1) * 8 + (lane & 7);
+        oy = (w >> 1) * 4 + (lane >> 3);
+        tiles_x = width > 0 ? (width + 15) / 16 : 1;
+        ty = first / tiles_x;
+        tx = (int32_t)(first - ty * tiles_x);
+        sy = step / tiles_x;
+        sx = (int32_t)(step - sy * tiles_x);
+    }
+    __device__ __forceinline__ void next() {
+        tile += stride;
+        tx += sx;
+        ty += sy;
+        if (tx >= tiles_x) {
+            tx -= tiles_x;
+            ++ty;
+        }
+    }
+    // Record of thread slot k (n: outside the image).
+    __device__ __forceinline__ int64_t record(int k, int64_t n, int32_t width) const {
+        if (width <= 0) return tile * 128 + k;
+        const int32_t px = tx * 16 + ox;
+        if (px >= width) return n;
+        return (ty * 8 + oy) * (int64_t)width + px;
+    }
+};
 
 __device__ __forceinline__ int64_t niv_tile_count(int64_t n, int32_t width) {
     if (width <= 0) return (n + 127) / 128;

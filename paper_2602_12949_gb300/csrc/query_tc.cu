@@ -43,6 +43,7 @@ namespace {
 #ifndef NIV_TC_MINB
 #define NIV_TC_MINB 1
 #endif
+
 constexpr int kT = 128;          // rows per tile = threads per warpgroup
 constexpr int kWG = NIV_TC_WG;   // warpgroups (independent tile pipelines) per CTA
 constexpr int kILP = NIV_TC_ILP; // levels whose gathers are in flight together (1 or 2)
@@ -71,9 +72,11 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-__device__ __forceinline__ uint32_t relu_half2(uint32_t x) {
-    __half2 h = __hmax2(*reinterpret_cast<__half2*>(&x), __float2half2_rn(0.0f));
-    return *reinterpret_cast<uint32_t*>(&h);
+// FP16 pair (lo, hi) of max(x, 0), rounded to nearest: one conversion with ReLU.
+__device__ __forceinline__ uint32_t relu_pack_half2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
@@ -100,11 +103,11 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t act, uint32_
 
 // Encode levels [l0, l0 + G) of one record into one 16-byte chunk of FP16 features,
 // kILP levels' gathers in flight at a time.
-template <int DIMS, int F>
-__device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const __half* __restrict__ grid16, int l0, int L,
+template <int DIMS, int F, typename TabT>
+__device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const TabT* __restrict__ grid, int l0, int L,
                                               const float* u) {
     constexpr int NC = 1 << DIMS, G = 8 / F;
-    using R = typename NivRaw<F, __half>::T;
+    using R = typename NivRaw<F, TabT>::T;
     uint32_t wd[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int q = 0; q < G; q += kILP) {
@@ -115,8 +118,8 @@ __device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const __half* _
         R ra[NC], rb[NC];
         if (has_a) niv_level_corners<DIMS>(g, la, u, ea, wa);
         if (has_b) niv_level_corners<DIMS>(g, lb, u, eb, wb);
-        if (has_a) niv_level_gather<NC, F, __half>(grid16 + (size_t)g.offset[la] * F, ea, ra);
-        if (has_b) niv_level_gather<NC, F, __half>(grid16 + (size_t)g.offset[lb] * F, eb, rb);
+        if (has_a) niv_level_gather<NC, F, TabT>(grid + (size_t)g.offset[la] * F, ea, ra);
+        if (has_b) niv_level_gather<NC, F, TabT>(grid + (size_t)g.offset[lb] * F, eb, rb);
         float acc[F];
 #pragma unroll
         for (int h = 0; h < kILP; ++h) {
@@ -143,9 +146,9 @@ __device__ __forceinline__ void group_sync(int wg) { asm volatile("bar.sync %0, 
 // mbarrier, named barrier, 64 TMEM columns) and all share the weights in shared memory.
 // LV > 0: the level count is a compile-time constant, so the level loop unrolls fully and
 // every per-level constant (resolution, table offset, dense flag) is an immediate operand.
-template <int DIMS, int F, int LV>
+template <int DIMS, int F, int LV, typename TabT>
 __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(GridArgs g, IoArgs io,
-                                                                const __half* __restrict__ grid16,
+                                                                const TabT* __restrict__ grid,
                                                                 const uint8_t* __restrict__ packed, TcLayout lay,
                                                                 int out_act, int64_t n_tiles, uint32_t tmem_cols,
                                                                 int* __restrict__ status) {
@@ -187,8 +190,10 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
     uint32_t phase = 0;
     bool ok = true;
 
-    for (int64_t tile = (int64_t)blockIdx.x * kWG + wg; tile < n_tiles && ok; tile += (int64_t)gridDim.x * kWG) {
-        const int64_t r = niv_record_of(tile, tid, io.n, io.image_width);
+    NivTileWalk walk;
+    walk.init((int64_t)blockIdx.x * kWG + wg, (int64_t)gridDim.x * kWG, tid, io.image_width);
+    for (; walk.tile < n_tiles && ok; walk.next()) {
+        const int64_t r = walk.record(tid, io.n, io.image_width);
         const bool valid = r < io.n;
         const int64_t rr = valid ? r : 0;
         const float4 p = niv_load_rec(io.pos, rr, io.in_f16);
@@ -203,10 +208,10 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         if (LV > 0) {
 #pragma unroll
             for (int l0 = 0; l0 < LV; l0 += G)
-                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid16, l0, LV, u);
+                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, LV, u);
         } else {
             for (int l0 = 0; l0 < L; l0 += G)
-                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid16, l0, L, u);
+                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, L, u);
         }
         {   // [n.x, n.y, n.z, (t), 1, 0, ...]: the 1 multiplies the first layer's bias column
             const bool has_t = g.n_in > L * F + 3;
@@ -248,7 +253,12 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                 tc::tmem_ld16(tmem_row + (uint32_t)(c * 16), v);
                 if (layer > 0) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] += bias[c * 16 + j];
+                    for (int j = 0; j < 8; ++j) {
+                        const float2 b = reinterpret_cast<const float2*>(bias + c * 16)[j];
+                        const float2 sum = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]), b);
+                        v[2 * j] = sum.x;
+                        v[2 * j + 1] = sum.y;
+                    }
                 }
                 if (kOutFma && last) {
 #pragma unroll
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                 } else {
                     uint32_t h[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = relu_half2(pack_half2(v[2 * j], v[2 * j + 1]));
+                    for (int j = 0; j < 8; ++j) h[j] = relu_pack_half2(v[2 * j], v[2 * j + 1]);
                     *reinterpret_cast<uint4*>(s_act + core_off(tid, c * 16, W)) = make_uint4(h[0], h[1], h[2], h[3]);
                     *reinterpret_cast<uint4*>(s_act + core_off(tid, c * 16 + 8, W)) = make_uint4(h[4], h[5], h[6], h[7]);
                 }
@@ -319,7 +329,8 @@ size_t tc_smem_bytes(const TcLayout& lay) {
 template <int DIMS, int F, int LV>
 int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s, int* status) {
     const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
-    auto kern = query_tc_f16_kernel<DIMS, F, LV>;
+    auto kern = query_tc_f16_kernel<DIMS, F, LV, __half>;
+    const __half* grid = m->grid_f16;
     const size_t smem = tc_smem_bytes(*lay);
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0;
@@ -358,7 +369,7 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
     const int64_t tiles = niv_tile_count_host(io.n, io.image_width);
     const int64_t need = (tiles + kWG - 1) / kWG;
     const int64_t blocks = need < (int64_t)sms * per_sm ? need : (int64_t)sms * per_sm;
-    kern<<<(unsigned)blocks, kT * kWG, smem, s>>>(g, io, m->grid_f16, m->mlp_tc, *lay, m->d.out_act, tiles, cols,
+    kern<<<(unsigned)blocks, kT * kWG, smem, s>>>(g, io, grid, m->mlp_tc, *lay, m->d.out_act, tiles, cols,
                                                  status);
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
