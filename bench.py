@@ -288,7 +288,54 @@ def _more_workloads(a, dev, flush, stream, steps=10, warmup=3):
     ms = _time_launches(lambda: grid.query(dp1, dn1, out=o1, image_width=1920), steps, warmup, flush, stream)
     res["probes_1080p"] = {"probes": 125000, "mb": grid.nbytes / 1e6, "ms_per_frame": ms,
                            "gqueries_per_s": 1920 * 1080 / (ms * 1e-3) / 1e9}
+    res.update(_table1_and_half(dev, flush, stream, dp1, dn1, steps, warmup))
     return res
+
+
+def _table1_and_half(dev, flush, stream, dpos, dnrm, steps, warmup):
+    """Every model of Table 1 (frequency-encoded widths 16 / 32 / 64; grids of 2 to 8 levels x F=4)
+    on the 1080p room frame in FP16: full resolution, and "half" (the pixels (2x, 2y) queried in
+    place), beside the paper's RTX 4090 numbers.  Then the whole half-resolution pipeline with
+    the config-1 model: quarter-pixel query + joint bilateral upsampling fused with shading."""
+    import torch
+    from paper_2602_12949_gb300 import NIVModel, upsample_shade
+    from niv_inputs import init_params
+    from niv_inputs.configs import TABLE1, MODEL_C1, ROOM_MIN, ROOM_MAX
+    from niv_inputs.meshes import shading_frame
+    W, H = 1920, 1080
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)
+    out = torch.empty((W * H, 4), dtype=torch.float16, device=dev)
+    low = torch.empty(((W // 2) * (H // 2), 4), dtype=torch.float16, device=dev)
+    rows = []
+    for spec, paper_full, paper_half, paper_mb in TABLE1:
+        m = NIVModel(**spec)
+        g, n_mlp = m.param_count()
+        m.set_params(init_params(g, m.layer_shapes(), seed=0))
+        full = _time_launches(lambda: m.query(dpos, dnrm, out=out, image_width=W, **kw), steps, warmup, flush, stream)
+        half = _time_launches(lambda: m.query_sub(dpos, dnrm, W, H, sub=2, out=low, **kw), steps, warmup, flush,
+                              stream)
+        rows.append({"width": spec["width"], "grid_levels": spec["levels"], "pe_bands": spec.get("pe_bands", 0),
+                     "mb_fp16": 2 * (g + n_mlp) / 1e6, "full_ms": full, "half_ms": half,
+                     "paper_rtx4090_full_ms": paper_full, "paper_rtx4090_half_ms": paper_half,
+                     "paper_mb": paper_mb})
+        m.close()
+    p4, n4, a4, d4, _ = shading_frame(W, H)
+    dp4, dn4, da4, dd4 = (torch.from_numpy(x).to(dev) for x in (p4, n4, a4, d4))
+    rgba = torch.empty((W * H, 4), dtype=torch.float16, device=dev)
+    m = NIVModel(**MODEL_C1)
+    g, _ = m.param_count()
+    m.set_params(init_params(g, m.layer_shapes(), seed=0))
+    ms_q = _time_launches(lambda: m.query_sub(dp4, dn4, W, H, sub=2, out=low, **kw), steps, warmup, flush, stream)
+    ms_u = _time_launches(lambda: upsample_shade(dp4, dn4, da4, dd4, W, H, low, sub=2, out=rgba), steps, warmup,
+                          flush, stream)
+    ms_f = _time_launches(lambda: m.query_shade(dp4, dn4, da4, dd4, out=rgba, image_width=W, **kw), steps, warmup,
+                          flush, stream)
+    m.close()
+    up_bytes = 40 * W * H + 8 * (W // 2) * (H // 2)  # 4 records in, rgba out, E at quarter resolution
+    half = {"query_ms": ms_q, "upsample_shade_ms": ms_u, "ms_per_frame": ms_q + ms_u,
+            "full_res_fused_ms": ms_f, "upsample_gb_per_s": up_bytes / (ms_u * 1e-3) / 1e9,
+            "upsample_bytes_per_frame": up_bytes}
+    return {"table1_1080p_fp16": rows, "half_1080p_config1": half}
 
 
 def main():

@@ -66,6 +66,14 @@ typedef struct niv_model* niv_handle;
  * ReLU layers of `width`, then `out_dim` outputs with softplus (out_act = 1) or
  * identity (0).  Its input is [level features (level-major), n.xyz, (t)], so
  * in_extra is 3, or 4 when a scene parameter t is appended (Sec. 6).
+ *
+ * pe_bands > 0 selects the smaller models of Sec. 4.1 / Table 1, which have no
+ * grid (levels = 0, dims = 3) and frequency-encode the position instead: for
+ * each coordinate u_k of the normalised position (k = 0, 1, 2) and each band
+ * b < pe_bands the pair (sin(2^b pi u_k), cos(2^b pi u_k)), in that order,
+ * coordinate-major; the network input is then [those 6 * pe_bands values,
+ * n.xyz].  Such models run in FP32 and FP16 (NIV_FP8 returns
+ * NIV_ERR_UNSUPPORTED).  pe_bands = 0 for grid models.
  */
 typedef struct niv_model_desc {
     int32_t dims;     /* 3, or 4 for a time-varying field (x, y, z, t) */
@@ -80,6 +88,7 @@ typedef struct niv_model_desc {
     int32_t out_dim;  /* 3 */
     int32_t out_act;  /* 0 identity, 1 softplus */
     uint32_t prime_t; /* odd hash constant of the 4th dimension */
+    int32_t pe_bands; /* 0: hash grid; 1..16: frequency encoding, no grid */
 } niv_model_desc;
 
 /*
@@ -327,8 +336,9 @@ NIV_API int niv_query_shade(niv_handle h, const void* pos, const void* nrm, cons
 
 /*
  * Encoding only (Sec. 4.1), for inspection and parity checks: for each of the n
- * position records, out_enc (device float32 [n][levels*feat], nullable)
- * receives the interpolated level features in FP32 from the FP32 master grid,
+ * position records, out_enc (device float32 [n][levels*feat + 6*pe_bands],
+ * nullable) receives the interpolated level features in FP32 from the FP32
+ * master grid, then the frequency-encoding values of a model without grid,
  * and out_idx (device uint32 [n][levels][2^dims], nullable) the table entry of
  * every cell corner, corner c having offset bit k set along dimension k.
  * Same normalisation and index arithmetic as niv_query.  Asynchronous.
@@ -343,6 +353,47 @@ NIV_API int niv_encode(niv_handle h, const void* pos, int64_t n, int32_t dtype_i
  */
 NIV_API int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out_rgba,
               niv_stream stream);
+
+/*
+ * Half-resolution rendering (Sec. 4.4 "Half-resolution Rendering"; Table 1, column
+ * "half": a quarter of the pixels queried, the full-size albedo buffer kept).
+ *
+ * niv_query_sub queries the pixels (sub x, sub y) of a full_width x full_height
+ * row-major G-buffer (pos, nrm as in niv_query) and writes E for them to out_E, a
+ * row-major [h][w][4] buffer, w = ceil(full_width / sub), h = ceil(full_height / sub).
+ * sub >= 1 (2 for half resolution).  Precisions and dtypes as in niv_query;
+ * params->image_width is ignored.  Asynchronous.
+ */
+NIV_API int niv_query_sub(niv_handle h, const void* pos, const void* nrm, int32_t full_width, int32_t full_height,
+                          int32_t sub, int32_t dtype_in, const niv_query_params* params, void* out_E,
+                          int32_t dtype_out, int32_t precision, niv_stream stream);
+
+/*
+ * Joint bilateral upsampling of the irradiance (the practice Sec. 4.4 points to:
+ * Kopf et al. 2007), fused with the shading of niv_shade.  The paper leaves the
+ * weights open; this library's reading: pixel p = (X, Y) blends the low-resolution
+ * samples q = (i, j), i in {i0, i1}, j in {j0, j1}, i0 = floor(X / sub),
+ * i1 = min(i0 + 1, w - 1) (likewise j), with the bilinear weights b_q of
+ * (X / sub - i0, Y / sub - j0) times a range term on the full-resolution G-buffer
+ * record of q's pixel (sub i, sub j):
+ *   g_q = max(0, n_p . n_q)^power * exp(-((n_p . (x_q - x_p)) / sigma)^2),
+ *   E_p = sum b_q (g_q + eps) E_q / sum b_q (g_q + eps),
+ *   rgba_p = (albedo_p E_p / pi + direct_p, 1),
+ * FP32 arithmetic, FP16 output.  pos, nrm: full-resolution [H][W][4] records of
+ * dtype_in; albedo, direct, out_rgba: FP16 [H][W][4]; E_low: [h][w][4] records of
+ * dtype_E as niv_query_sub writes them.  sigma (world units) and eps must be > 0.
+ * No counterpart of these exact weights in the paper.  Asynchronous.
+ */
+typedef struct niv_upsample_params {
+    float power; /* exponent of the normal agreement, e.g. 8 */
+    float sigma; /* plane-distance scale in world units, e.g. 0.05 */
+    float eps;   /* weight floor, e.g. 1e-4 */
+} niv_upsample_params;
+
+NIV_API int niv_upsample_shade(const void* pos, const void* nrm, const void* albedo, const void* direct,
+                               int32_t full_width, int32_t full_height, int32_t dtype_in, const void* E_low,
+                               int32_t dtype_E, int32_t sub, const niv_upsample_params* up, void* out_rgba,
+                               niv_stream stream);
 
 /*
  * Diagnostic (no counterpart in the paper): one 128 x 64 x K tensor-core product

@@ -50,6 +50,7 @@ class Desc(ctypes.Structure):
         ("log2_T", ctypes.c_int32), ("base", ctypes.c_double), ("growth", ctypes.c_double),
         ("n_hidden", ctypes.c_int32), ("width", ctypes.c_int32), ("in_extra", ctypes.c_int32),
         ("out_dim", ctypes.c_int32), ("out_act", ctypes.c_int32), ("prime_t", ctypes.c_uint32),
+        ("pe_bands", ctypes.c_int32),
     ]
 
 
@@ -68,14 +69,20 @@ class Model:
     out_dim: int = 3
     out_act: int = 1
     prime_t: int = 0x9E3779B1
+    pe_bands: int = 0  # > 0: frequency-encoded position (Table 1's models without grid levels)
 
     def cdesc(self):
         return Desc(self.dims, self.levels, self.feat, self.log2_T, self.base, self.growth,
-                    self.n_hidden, self.width, self.in_extra, self.out_dim, self.out_act, self.prime_t)
+                    self.n_hidden, self.width, self.in_extra, self.out_dim, self.out_act, self.prime_t,
+                    self.pe_bands)
+
+    @property
+    def enc_dim(self):
+        return self.levels * self.feat + 6 * self.pe_bands
 
     @property
     def n_in(self):
-        return self.levels * self.feat + self.in_extra
+        return self.enc_dim + self.in_extra
 
 
 def lib():
@@ -102,6 +109,13 @@ def lib():
         L.orc_shade.restype = None
         L.orc_e4m3.argtypes = [d]
         L.orc_e4m3.restype = d
+        L.orc_f16.argtypes = [d]
+        L.orc_f16.restype = d
+        L.orc_f16_array.argtypes = [vp, i64, vp]
+        L.orc_f16_array.restype = None
+        L.orc_query_f16.argtypes = [P(Desc), vp, vp, vp, i64, vp, vp, f, vp]
+        L.orc_upsample_shade.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, d, d, d, vp]
+        L.orc_upsample_shade.restype = None
         L.orc_e4m3_array.argtypes = [vp, i64, vp]
         L.orc_e4m3_array.restype = None
         L.orc_fp8_scale.argtypes = [d]
@@ -167,11 +181,12 @@ def layer_shapes(model):
 
 
 def encode(model, params, pos4, aabb_min=(0, 0, 0), aabb_max=(1, 1, 1), t=0.0, want_corners=False):
-    """Encoding of every query: enc[n][L*F] (and corner indices / weights if asked)."""
+    """Encoding of every query: enc[n][L*F + 6*B] (grid features, then frequency encoding),
+    and the grid corners' indices / weights if asked."""
     pos4 = _f32(pos4)
     n = len(pos4)
     nc = 1 << model.dims
-    enc = np.zeros((n, model.levels * model.feat))
+    enc = np.zeros((n, model.enc_dim))
     idx = np.zeros((n, model.levels, nc), np.uint32) if want_corners else None
     w = np.zeros((n, model.levels, nc)) if want_corners else None
     lib().orc_encode(ctypes.byref(model.cdesc()), _p(_f64(params)), _p(pos4), n, _p(_f32(aabb_min)),
@@ -195,6 +210,37 @@ def query(model, params, pos4, nrm4, aabb_min=(0, 0, 0), aabb_max=(1, 1, 1), t=0
     if rc:
         raise ValueError("orc_query failed")
     return E
+
+
+def f16(x):
+    """Nearest binary16 values (ties to even) of an array, as float64."""
+    x = _f64(x)
+    out = np.empty_like(x)
+    lib().orc_f16_array(_p(x), x.size, _p(out))
+    return out
+
+
+def query_f16(model, params16, pos4, nrm4, aabb_min=(0, 0, 0), aabb_max=(1, 1, 1), t=0.0):
+    """E(x, n) on the FP16 network path: params16 already rounded to binary16, network
+    input and hidden activations rounded to binary16, FP64 sums and softplus."""
+    pos4, nrm4 = _f32(pos4), _f32(nrm4)
+    E = np.zeros((len(pos4), model.out_dim))
+    rc = lib().orc_query_f16(ctypes.byref(model.cdesc()), _p(_f64(params16)), _p(pos4), _p(nrm4), len(pos4),
+                             _p(_f32(aabb_min)), _p(_f32(aabb_max)), float(t), _p(E))
+    if rc:
+        raise ValueError("orc_query_f16 failed")
+    return E
+
+
+def upsample_shade(pos4, nrm4, alb4, dir4, width, height, E_low, sub=2, power=8.0, sigma=0.05, eps=1e-4):
+    """Full-resolution shaded rgb [W*H][3] from the irradiance E_low [h*w][3] queried at every
+    sub-th pixel (joint bilateral upsampling guided by the full-resolution G-buffer)."""
+    n = width * height
+    out = np.zeros((n, 3))
+    E = _f64(np.asarray(E_low)[:, :3])
+    lib().orc_upsample_shade(_p(_f32(pos4)), _p(_f32(nrm4)), _p(_f32(alb4)), _p(_f32(dir4)), int(width),
+                             int(height), _p(E), int(sub), float(power), float(sigma), float(eps), _p(out))
+    return out
 
 
 def loss_grad(model, params, pos4, nrm4, target, aabb_min=(0, 0, 0), aabb_max=(1, 1, 1), t=None, eps=0.01):

@@ -11,6 +11,9 @@
  *    storage of the (N_l+1)^d vertices when that fits in T entries, otherwise the
  *    spatial hash  (XOR_k v_k * pi_k) mod T  with pi = (1, 2654435761, 805459861);
  *    multilinear interpolation of the F features stored at the 2^d cell corners.
+ *  - Sec. 4.1 / Table 1: the smaller models replace the grid by an eight-band
+ *    frequency (positional) encoding of the position (Mildenhall et al. 2020):
+ *    sin(2^k pi u_d) and cos(2^k pi u_d), k = 0..B-1, for each coordinate d;
  *  - Sec. 4.1: a fully connected network with ReLU on all but the final layer,
  *    mapping (encoded position, direction) to irradiance; the final activation is
  *    softplus (keeps E >= 0).
@@ -24,7 +27,10 @@
  *  - s = u * N_l (FP32 product), i = min(floor(s), N_l - 1), w = s - i, vertices
  *    at integer coordinates 0..N_l (no half-cell offset);
  *  - 4th (time) grid dimension hashed with a caller-chosen odd constant;
- *  - network input = [level 0 features, ..., level L-1 features, n.xyz, (t)].
+ *  - network input = [level 0 features, ..., level L-1 features, n.xyz, (t)];
+ *  - frequency encoding of the normalised coordinate u in [0, 1], no identity term,
+ *    ordered per coordinate, then per band, sin before cos; it follows the grid
+ *    features in the network input (a model has one or the other).
  *
  * Parity status: every function here is pinned by tests (closed forms, brute
  * force, library special cases, finite differences).
@@ -41,6 +47,8 @@
 #define ORC_MAX_DIMS 4
 #define ORC_MAX_LAYERS 8
 #define ORC_MAX_WIDTH 256
+#define ORC_MAX_BANDS 16
+#define ORC_MAX_ENC (ORC_MAX_LEVELS * 8 + 6 * ORC_MAX_BANDS) /* encoding values of one query */
 
 typedef struct {
     int32_t dims;      /* 3 (x,y,z) or 4 (x,y,z,t) */
@@ -55,6 +63,7 @@ typedef struct {
     int32_t out_dim;   /* 3 */
     int32_t out_act;   /* 0 identity, 1 softplus */
     uint32_t prime_t;  /* hash constant of the 4th dimension */
+    int32_t pe_bands;  /* > 0: frequency encoding of the position with that many bands (levels may be 0) */
 } orc_desc;
 
 typedef struct {
@@ -84,7 +93,8 @@ static float f32_mul(float a, float b) { return (float)((double)a * (double)b); 
 /* ---- level layout (Sec. 4.1) ---- */
 int64_t orc_layout(const orc_desc* d, int32_t* res, int32_t* dense, int64_t* offset, int64_t* entries)
 {
-    if (d->levels < 1 || d->levels > ORC_MAX_LEVELS || d->dims < 3 || d->dims > ORC_MAX_DIMS) return -1;
+    if (d->levels < 0 || d->levels > ORC_MAX_LEVELS || d->dims < 3 || d->dims > ORC_MAX_DIMS) return -1;
+    if (d->pe_bands < 0 || d->pe_bands > ORC_MAX_BANDS || (d->levels == 0 && d->pe_bands == 0)) return -1;
     const int64_t T = (int64_t)1 << d->log2_T;
     int64_t off = 0;
     for (int l = 0; l < d->levels; ++l) {
@@ -175,9 +185,20 @@ static void encode_point(const orc_desc* d, const orc_layout_t* L, const double*
             if (w_out) w_out[l * nc + c] = wc;
         }
     }
+    /* frequency encoding: sin / cos of 2^b * pi * u_k (the FP32 u taken exactly) */
+    double* pe = enc + d->levels * F;
+    for (int k = 0; k < 3; ++k)
+        for (int b = 0; b < d->pe_bands; ++b) {
+            double a = M_PI * ldexp((double)u[k], b);
+            pe[(k * d->pe_bands + b) * 2 + 0] = sin(a);
+            pe[(k * d->pe_bands + b) * 2 + 1] = cos(a);
+        }
 }
 
-int orc_net_inputs(const orc_desc* d) { return d->levels * d->feat + d->in_extra; }
+/* encoding values of one query: grid features, then frequency-encoding values */
+int orc_enc_dim(const orc_desc* d) { return d->levels * d->feat + 6 * d->pe_bands; }
+
+int orc_net_inputs(const orc_desc* d) { return orc_enc_dim(d) + d->in_extra; }
 
 /* number of network parameters (all layers, weights and biases) */
 int64_t orc_mlp_param_count(const orc_desc* d)
@@ -230,7 +251,7 @@ static void mlp_forward(const orc_desc* d, const double* mlp, const double* x, d
 /* assemble the network input of one query: [encoding, n.xyz, (t)] */
 static void net_input(const orc_desc* d, const double* enc, const float* nrm, float t, double* x)
 {
-    int ne = d->levels * d->feat;
+    int ne = orc_enc_dim(d);
     for (int i = 0; i < ne; ++i) x[i] = enc[i];
     x[ne + 0] = nrm[0];
     x[ne + 1] = nrm[1];
@@ -240,7 +261,7 @@ static void net_input(const orc_desc* d, const double* enc, const float* nrm, fl
 }
 
 /*
- * Encoding only: enc[n][L*F].  Optionally the corner indices idx[n][L][2^d]
+ * Encoding only: enc[n][L*F + 6*B] (grid features, then frequency encoding).  Optionally the corner indices idx[n][L][2^d]
  * (uint32) and corner weights w[n][L][2^d].
  */
 int orc_encode(const orc_desc* d, const double* grid, const float* pos4, int64_t n, const float* aabb_min,
@@ -248,14 +269,14 @@ int orc_encode(const orc_desc* d, const double* grid, const float* pos4, int64_t
 {
     orc_layout_t L;
     if (fill_layout(d, &L)) return -1;
-    const int nc = 1 << d->dims, LF = d->levels * d->feat;
+    const int nc = 1 << d->dims, ne = orc_enc_dim(d);
 #pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) {
         float u[ORC_MAX_DIMS];
         int64_t ix[ORC_MAX_LEVELS * 16];
         double wc[ORC_MAX_LEVELS * 16];
         normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
-        encode_point(d, &L, grid, u, enc + q * LF, ix, wc);
+        encode_point(d, &L, grid, u, enc + q * ne, ix, wc);
         for (int e = 0; e < d->levels * nc; ++e) {
             if (idx) idx[q * d->levels * nc + e] = (uint32_t)ix[e];
             if (wts) wts[q * d->levels * nc + e] = wc[e];
@@ -289,7 +310,7 @@ int orc_query(const orc_desc* d, const double* params, const float* pos4, const 
 #pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) {
         float u[ORC_MAX_DIMS];
-        double enc[ORC_MAX_LEVELS * 8], x[ORC_MAX_LEVELS * 8 + 8];
+        double enc[ORC_MAX_ENC], x[ORC_MAX_ENC + 8];
         normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
         encode_point(d, &L, params, u, enc, NULL, NULL);
         net_input(d, enc, nrm4 + 4 * q, t, x);
@@ -324,7 +345,7 @@ int orc_loss_grad(const orc_desc* d, const double* params, const float* pos4, co
     double* a_all = (double*)malloc(sizeof(double) * ORC_MAX_LAYERS * ORC_MAX_WIDTH);
     for (int64_t q = 0; q < n; ++q) {
         float u[ORC_MAX_DIMS];
-        double enc[ORC_MAX_LEVELS * 8], x[ORC_MAX_LEVELS * 8 + 8], E[8];
+        double enc[ORC_MAX_ENC], x[ORC_MAX_ENC + 8], E[8];
         int64_t ix[ORC_MAX_LEVELS * 16];
         double wc[ORC_MAX_LEVELS * 16];
         float tq = t_per_sample ? t_per_sample[q] : 0.0f;
@@ -333,7 +354,7 @@ int orc_loss_grad(const orc_desc* d, const double* params, const float* pos4, co
         net_input(d, enc, nrm4 + 4 * q, tq, x);
         mlp_forward(d, mlp, x, z_all, a_all, E);
         /* dLoss/dE with the denominator held constant */
-        double g_out[ORC_MAX_WIDTH], g_in[ORC_MAX_WIDTH + ORC_MAX_LEVELS * 8];
+        double g_out[ORC_MAX_WIDTH], g_in[ORC_MAX_WIDTH + ORC_MAX_ENC];
         for (int c = 0; c < C; ++c) {
             double y = target[q * C + c];
             double den = E[c] * E[c] + eps;
@@ -402,6 +423,59 @@ void orc_shade(const double* albedo3, const double* E3, const double* direct3, i
 }
 
 /*
+ * Half-resolution rendering (Sec. 4.4): irradiance queried at every s-th pixel of
+ * every s-th row, brought back to full resolution by joint bilateral upsampling
+ * (Kopf et al. 2007, the practice the paper points to) guided by the full-
+ * resolution G-buffer, then shaded with the full-resolution albedo.  Reading:
+ *   low-resolution sample q = (i, j), i < w = ceil(W / s), j < h = ceil(H / s),
+ *   holds E queried at full-resolution pixel (s i, s j);
+ *   pixel p = (X, Y): i0 = floor(X / s), fx = X / s - i0, i1 = min(i0 + 1, w - 1),
+ *   likewise j0, fy, j1; the four samples carry bilinear weights b_q;
+ *   range term g_q = max(0, n_p . n_q)^P * exp(-((n_p . (x_q - x_p)) / sigma)^2)
+ *   (normal agreement, distance of the sample from p's tangent plane);
+ *   w_q = b_q (g_q + eps): eps keeps the sum positive and makes the result a
+ *   continuous function of the inputs (plain bilinear where every g_q vanishes);
+ *   E_p = sum w_q E_q / sum w_q; out_p = albedo_p E_p / pi + direct_p.
+ * pos4 / nrm4 / alb4 / dir4: full-resolution [W*H][4] records (row-major);
+ * E_low3: [h*w][3]; out3: [W*H][3].
+ */
+void orc_upsample_shade(const float* pos4, const float* nrm4, const float* alb4, const float* dir4, int W, int H,
+                        const double* E_low3, int s, double P, double sigma, double eps, double* out3)
+{
+    const int w = (W + s - 1) / s, h = (H + s - 1) / s;
+#pragma omp parallel for schedule(static)
+    for (int Y = 0; Y < H; ++Y)
+        for (int X = 0; X < W; ++X) {
+            const int64_t p = (int64_t)Y * W + X;
+            const int i0 = X / s, j0 = Y / s;
+            const int i1 = i0 + 1 < w ? i0 + 1 : w - 1, j1 = j0 + 1 < h ? j0 + 1 : h - 1;
+            const double fx = (double)(X - s * i0) / s, fy = (double)(Y - s * j0) / s;
+            const int qi[4] = {i0, i1, i0, i1}, qj[4] = {j0, j0, j1, j1};
+            const double b[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+            const float* xp = pos4 + 4 * p;
+            const float* np_ = nrm4 + 4 * p;
+            double sw = 0.0, se[3] = {0.0, 0.0, 0.0};
+            for (int c = 0; c < 4; ++c) {
+                const int64_t src = (int64_t)(s * qj[c]) * W + s * qi[c];
+                const float* xq = pos4 + 4 * src;
+                const float* nq = nrm4 + 4 * src;
+                double dot = 0.0, dpl = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    dot += (double)np_[k] * nq[k];
+                    dpl += (double)np_[k] * ((double)xq[k] - xp[k]);
+                }
+                const double g = pow(dot > 0.0 ? dot : 0.0, P) * exp(-(dpl / sigma) * (dpl / sigma));
+                const double wq = b[c] * (g + eps);
+                const int64_t q = (int64_t)qj[c] * w + qi[c];
+                sw += wq;
+                for (int k = 0; k < 3; ++k) se[k] += wq * E_low3[3 * q + k];
+            }
+            for (int k = 0; k < 3; ++k)
+                out3[3 * p + k] = (double)alb4[4 * p + k] * (se[k] / sw) / M_PI + dir4[4 * p + k];
+        }
+}
+
+/*
  * Round to the nearest FP8 E4M3 value (1 sign, 4 exponent bits with bias 7,
  * 3 mantissa bits, subnormal step 2^-9, largest finite 448, no infinities),
  * ties to even, saturating to +-448.  Written from the format's definition.
@@ -427,6 +501,85 @@ double orc_e4m3(double x)
 void orc_e4m3_array(const double* x, int64_t n, double* out)
 {
     for (int64_t i = 0; i < n; ++i) out[i] = orc_e4m3(x[i]);
+}
+
+/*
+ * Nearest IEEE binary16 value of x (round to nearest, ties to even), written from
+ * the format's definition: 11 significant bits for normal values (>= 2^-14),
+ * spacing 2^-24 below; |x| >= 65520 (the midpoint between 65504 and 2^16) rounds
+ * to infinity.
+ */
+double orc_f16(double x)
+{
+    if (isnan(x) || isinf(x)) return x;
+    double a = fabs(x);
+    if (a >= 65520.0) return copysign(INFINITY, x);
+    int e2;
+    frexp(a, &e2); /* a = m * 2^e2, m in [0.5, 1) */
+    int ulp = e2 - 11;
+    if (ulp < -24) ulp = -24;
+    double q = ldexp(nearbyint(ldexp(a, -ulp)), ulp); /* default rounding mode: ties to even */
+    return copysign(q, x);
+}
+
+void orc_f16_array(const double* x, int64_t n, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_f16(x[i]);
+}
+
+/*
+ * The FP16 network path as defined by Table 1's "all parameters in half
+ * precision" with FP16 activations: the caller passes parameters already
+ * rounded to binary16; every network input value and every hidden activation
+ * (after ReLU) is rounded to binary16; sums are exact-ish in FP64; the output
+ * layer's sum and softplus stay in FP64.
+ */
+static void mlp_forward_f16(const orc_desc* d, const double* mlp, const double* x_in, double* E)
+{
+    double buf_a[ORC_MAX_ENC + 8], buf_b[ORC_MAX_WIDTH];
+    int k_in = orc_net_inputs(d);
+    for (int i = 0; i < k_in; ++i) buf_a[i] = orc_f16(x_in[i]);
+    const double* in = buf_a;
+    const double* p = mlp;
+    int layers = d->n_hidden + 1;
+    double tmp[ORC_MAX_WIDTH];
+    for (int layer = 0; layer < layers; ++layer) {
+        int last = layer == layers - 1;
+        int n_out = last ? d->out_dim : d->width;
+        const double* W = p;
+        const double* b = p + (int64_t)n_out * k_in;
+        for (int o = 0; o < n_out; ++o) {
+            double z = b[o];
+            for (int i = 0; i < k_in; ++i) z += W[(int64_t)o * k_in + i] * in[i];
+            if (last) E[o] = d->out_act == 1 ? softplus(z) : z;
+            else tmp[o] = orc_f16(z > 0.0 ? z : 0.0);
+        }
+        if (!last) {
+            for (int o = 0; o < n_out; ++o) buf_b[o] = tmp[o];
+            in = buf_b;
+        }
+        p = b + n_out;
+        k_in = n_out;
+    }
+}
+
+/* Full query on the FP16 network path (see mlp_forward_f16); grid values as given. */
+int orc_query_f16(const orc_desc* d, const double* params, const float* pos4, const float* nrm4, int64_t n,
+                  const float* aabb_min, const float* aabb_max, float t, double* E)
+{
+    orc_layout_t L;
+    if (fill_layout(d, &L)) return -1;
+    const double* mlp = params + L.total * d->feat;
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) {
+        float u[ORC_MAX_DIMS];
+        double enc[ORC_MAX_ENC], x[ORC_MAX_ENC + 8];
+        normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
+        encode_point(d, &L, params, u, enc, NULL, NULL);
+        net_input(d, enc, nrm4 + 4 * q, t, x);
+        mlp_forward_f16(d, mlp, x, E + q * d->out_dim);
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------------
@@ -466,7 +619,7 @@ int orc_fp8_act_amax(const orc_desc* d, const double* params, const float* pos4,
     double* a_all = (double*)malloc(sizeof(double) * ORC_MAX_LAYERS * ORC_MAX_WIDTH);
     for (int64_t q = 0; q < n; ++q) {
         float u[ORC_MAX_DIMS];
-        double enc[ORC_MAX_LEVELS * 8], x[ORC_MAX_LEVELS * 8 + 8], E[8];
+        double enc[ORC_MAX_ENC], x[ORC_MAX_ENC + 8], E[8];
         normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
         encode_point(d, &L, params, u, enc, NULL, NULL);
         net_input(d, enc, nrm4 + 4 * q, t, x);
@@ -510,7 +663,7 @@ int orc_query_fp8(const orc_desc* d, const double* params, const double* s_act, 
 #pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) {
         float u[ORC_MAX_DIMS];
-        double enc[ORC_MAX_LEVELS * 8], a[ORC_MAX_WIDTH + ORC_MAX_LEVELS * 8], z[ORC_MAX_WIDTH];
+        double enc[ORC_MAX_ENC], a[ORC_MAX_WIDTH + ORC_MAX_ENC], z[ORC_MAX_WIDTH];
         normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
         encode_point(d, &L, params, u, enc, NULL, NULL);
         net_input(d, enc, nrm4 + 4 * q, t, a);

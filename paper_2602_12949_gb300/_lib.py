@@ -34,12 +34,17 @@ class ModelDesc(ctypes.Structure):
         ("log2_T", ctypes.c_int32), ("base", ctypes.c_double), ("growth", ctypes.c_double),
         ("n_hidden", ctypes.c_int32), ("width", ctypes.c_int32), ("in_extra", ctypes.c_int32),
         ("out_dim", ctypes.c_int32), ("out_act", ctypes.c_int32), ("prime_t", ctypes.c_uint32),
+        ("pe_bands", ctypes.c_int32),
     ]
 
 
 class QueryParams(ctypes.Structure):
     _fields_ = [("aabb_min", ctypes.c_float * 3), ("aabb_max", ctypes.c_float * 3), ("t", ctypes.c_float),
                 ("image_width", ctypes.c_int32)]
+
+
+class UpsampleParams(ctypes.Structure):
+    _fields_ = [("power", ctypes.c_float), ("sigma", ctypes.c_float), ("eps", ctypes.c_float)]
 
 
 class FitParams(ctypes.Structure):
@@ -79,6 +84,10 @@ _SIGNATURES = [
     ("niv_encode", ctypes.c_int, [_VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _VP, _VP]),
     ("niv_selftest_mma", ctypes.c_int, [_I32, _VP, _VP]),
     ("niv_shade", ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
+    ("niv_query_sub", ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _I32, _I32, ctypes.POINTER(QueryParams), _VP, _I32,
+                                     _I32, _VP]),
+    ("niv_upsample_shade", ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _I32, _I32, _VP, _I32, _I32,
+                                          ctypes.POINTER(UpsampleParams), _VP, _VP]),
 ]
 
 

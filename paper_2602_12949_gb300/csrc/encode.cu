@@ -1,6 +1,7 @@
-// Encoding only (Sec. 4.1): per query the L*F interpolated features and, on
-// request, the 2^d corner entry indices of every level.  Used to check the
-// integer index pipeline bit for bit and the FP32 interpolation on its own.
+// Encoding only (Sec. 4.1): per query the L*F interpolated features, then the
+// 6 * pe_bands frequency-encoding values of a model without grid, and on request
+// the 2^d corner entry indices of every level.  Used to check the integer index
+// pipeline bit for bit and the FP32 interpolation on its own.
 #include "niv_internal.cuh"
 
 namespace {
@@ -17,6 +18,14 @@ __global__ void __launch_bounds__(128) encode_kernel(GridArgs g, IoArgs io, cons
     u[2] = niv_unit(p.z, g.aabb_min[2], g.inv_ext[2]);
     u[3] = fminf(fmaxf(g.t, 0.0f), 1.0f);
     constexpr int NC = 1 << DIMS;
+    const int LG = g.levels * F, ne = LG + 6 * g.pe_bands;
+    for (int d = 0; d < 3 && g.pe_bands > 0 && enc; ++d)
+        for (int b = 0; b < g.pe_bands; ++b) {
+            float sv, cv;
+            niv_pe_pair(u[d], b, sv, cv);
+            enc[q * ne + LG + 2 * (d * g.pe_bands + b)] = sv;
+            enc[q * ne + LG + 2 * (d * g.pe_bands + b) + 1] = cv;
+        }
     for (int l = 0; l < g.levels; ++l) {
         const int32_t N = g.res[l];
         const bool dense = (g.dense_mask >> l) & 1u;
@@ -45,7 +54,7 @@ __global__ void __launch_bounds__(128) encode_kernel(GridArgs g, IoArgs io, cons
         }
         if (enc)
 #pragma unroll
-            for (int j = 0; j < F; ++j) enc[q * g.levels * F + l * F + j] = acc[j];
+            for (int j = 0; j < F; ++j) enc[q * ne + l * F + j] = acc[j];
     }
 }
 

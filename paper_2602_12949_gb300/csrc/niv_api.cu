@@ -33,7 +33,13 @@ __global__ void f32_to_f16_kernel(const float* __restrict__ src, __half* __restr
 int validate_desc(const niv_model_desc* d) {
     if (!d) return niv_fail(NIV_ERR_ARG, "desc is NULL");
     if (d->dims != 3 && d->dims != 4) return niv_fail(NIV_ERR_ARG, "dims must be 3 or 4");
-    if (d->levels < 1 || d->levels > NIV_MAX_LEVELS) return niv_fail(NIV_ERR_ARG, "levels must be in 1..32");
+    if (d->pe_bands < 0 || d->pe_bands > 16) return niv_fail(NIV_ERR_ARG, "pe_bands must be in 0..16");
+    if (d->pe_bands > 0) {
+        if (d->levels != 0) return niv_fail(NIV_ERR_UNSUPPORTED, "a frequency-encoded model has no grid levels");
+        if (d->dims != 3) return niv_fail(NIV_ERR_UNSUPPORTED, "frequency encoding is 3-D");
+    } else if (d->levels < 1 || d->levels > NIV_MAX_LEVELS) {
+        return niv_fail(NIV_ERR_ARG, "levels must be in 1..32");
+    }
     if (d->feat != 1 && d->feat != 2 && d->feat != 4) return niv_fail(NIV_ERR_UNSUPPORTED, "feat must be 1, 2 or 4");
     if (d->log2_T < 4 || d->log2_T > 24) return niv_fail(NIV_ERR_ARG, "log2_T must be in 4..24");
     if (!(d->base >= 1.0) || !(d->growth >= 1.0)) return niv_fail(NIV_ERR_ARG, "base and growth must be >= 1");
@@ -43,7 +49,8 @@ int validate_desc(const niv_model_desc* d) {
     if (d->in_extra != 3 && d->in_extra != 4) return niv_fail(NIV_ERR_ARG, "in_extra must be 3 or 4");
     if (d->out_dim != 3) return niv_fail(NIV_ERR_UNSUPPORTED, "out_dim must be 3");
     if (d->out_act != 0 && d->out_act != 1) return niv_fail(NIV_ERR_ARG, "out_act must be 0 or 1");
-    if (d->levels * d->feat + d->in_extra > NIV_MAX_IN) return niv_fail(NIV_ERR_UNSUPPORTED, "network input too wide");
+    if (d->levels * d->feat + 6 * d->pe_bands + d->in_extra > NIV_MAX_IN)
+        return niv_fail(NIV_ERR_UNSUPPORTED, "network input too wide");
     if (d->dims == 4 && (d->prime_t & 1u) == 0) return niv_fail(NIV_ERR_ARG, "prime_t must be odd");
     return NIV_OK;
 }
@@ -57,6 +64,7 @@ int check_device(const niv_model* m) {
 
 int convert_grid_f16(niv_model* m, cudaStream_t s) {
     int64_t n = m->n_grid;
+    if (n == 0) return NIV_OK;  // frequency-encoded model: no grid
     int64_t blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     f32_to_f16_kernel<<<(unsigned)blocks, 256, 0, s>>>(m->params, m->grid_f16, n);
@@ -147,6 +155,7 @@ GridArgs niv_grid_args(const niv_model* m, const niv_query_params* p) {
     memset(&g, 0, sizeof g);
     g.dims = m->d.dims;
     g.levels = m->d.levels;
+    g.pe_bands = m->d.pe_bands;
     g.feat = m->d.feat;
     g.n_in = m->n_in;
     g.hash_mask = (uint32_t)((1ull << m->d.log2_T) - 1ull);
@@ -183,7 +192,7 @@ int niv_pack_plain(niv_model* m, const float* src, cudaStream_t s) {
 
 extern "C" {
 
-const char* niv_version(void) { return "niv 0.1 (sm_103a)"; }
+const char* niv_version(void) { return "niv 0.2 (sm_103a)"; }
 
 const char* niv_last_error(void) { return t_err.c_str(); }
 
@@ -228,7 +237,7 @@ int niv_create(const niv_model_desc* desc, niv_handle* out) {
         off += m->entries[l];
     }
     m->total_entries = off;
-    m->n_in = desc->levels * desc->feat + desc->in_extra;
+    m->n_in = desc->levels * desc->feat + 6 * desc->pe_bands + desc->in_extra;
     m->n_grid = off * desc->feat;
     int64_t n = 0, k = m->n_in;
     for (int h = 0; h < desc->n_hidden; ++h) {
@@ -240,10 +249,10 @@ int niv_create(const niv_model_desc* desc, niv_handle* out) {
     m->mlp_plain_len = n;
     cudaError_t e = cudaGetDevice(&m->device);
     if (e == cudaSuccess) e = cudaMalloc(&m->params, sizeof(float) * (m->n_grid + m->n_mlp));
-    if (e == cudaSuccess) e = cudaMalloc(&m->grid_f16, sizeof(__half) * m->n_grid);
+    if (e == cudaSuccess) e = cudaMalloc(&m->grid_f16, sizeof(__half) * (m->n_grid > 0 ? m->n_grid : 1));
     if (e == cudaSuccess) e = cudaMalloc(&m->mlp_plain, sizeof(float) * m->mlp_plain_len);
     if (e == cudaSuccess) e = cudaMemset(m->params, 0, sizeof(float) * (m->n_grid + m->n_mlp));
-    if (e == cudaSuccess) e = cudaMemset(m->grid_f16, 0, sizeof(__half) * m->n_grid);
+    if (e == cudaSuccess) e = cudaMemset(m->grid_f16, 0, sizeof(__half) * (m->n_grid > 0 ? m->n_grid : 1));
     if (e == cudaSuccess) e = cudaMemset(m->mlp_plain, 0, sizeof(float) * m->mlp_plain_len);
     if (e != cudaSuccess) {
         free_model(m);
@@ -621,6 +630,67 @@ int niv_query_shade(niv_handle h, const void* pos, const void* nrm, const void* 
         case NIV_FP8: return niv_launch_query_f8(h, g, io, (cudaStream_t)stream);
         default: return niv_fail(NIV_ERR_UNSUPPORTED, "precision not supported");
     }
+}
+
+int niv_query_sub(niv_handle h, const void* pos, const void* nrm, int32_t full_width, int32_t full_height,
+                  int32_t sub, int32_t dtype_in, const niv_query_params* params, void* out_E, int32_t dtype_out,
+                  int32_t precision, niv_stream stream) {
+    if (!h || !params) return niv_fail(NIV_ERR_ARG, "handle or params is NULL");
+    if (full_width < 0 || full_height < 0) return niv_fail(NIV_ERR_ARG, "negative image size");
+    if (sub < 1) return niv_fail(NIV_ERR_ARG, "sub must be >= 1");
+    if (full_width == 0 || full_height == 0) return NIV_OK;
+    if ((int64_t)full_width * sub > INT32_MAX) return niv_fail(NIV_ERR_UNSUPPORTED, "image too wide");
+    if (!pos || !nrm || !out_E) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if (!aligned16(pos) || !aligned16(nrm) || !aligned16(out_E))
+        return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    if ((dtype_in != NIV_F32 && dtype_in != NIV_F16) || (dtype_out != NIV_F32 && dtype_out != NIV_F16))
+        return niv_fail(NIV_ERR_ARG, "record dtype must be NIV_F32 or NIV_F16");
+    for (int k = 0; k < 3; ++k)
+        if (!(params->aabb_max[k] > params->aabb_min[k])) return niv_fail(NIV_ERR_ARG, "empty aabb");
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (h->infer_dirty) {
+        rc = refresh_inference(h, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    const int32_t w = (full_width + sub - 1) / sub, hh = (full_height + sub - 1) / sub;
+    GridArgs g = niv_grid_args(h, params);
+    IoArgs io;
+    io.pos = pos;
+    io.nrm = nrm;
+    io.out = out_E;
+    io.n = (int64_t)w * hh;
+    io.image_width = w;
+    io.in_f16 = dtype_in == NIV_F16;
+    io.out_f16 = dtype_out == NIV_F16;
+    io.sub = sub;
+    io.src_width = full_width;
+    switch (precision) {
+        case NIV_FP32: return niv_launch_query_fp32(h, g, io, (cudaStream_t)stream);
+        case NIV_FP16: return niv_launch_query_tc(h, g, io, precision, (cudaStream_t)stream);
+        case NIV_FP8: return niv_launch_query_f8(h, g, io, (cudaStream_t)stream);
+        default: return niv_fail(NIV_ERR_UNSUPPORTED, "precision not supported");
+    }
+}
+
+int niv_upsample_shade(const void* pos, const void* nrm, const void* albedo, const void* direct, int32_t full_width,
+                       int32_t full_height, int32_t dtype_in, const void* E_low, int32_t dtype_E, int32_t sub,
+                       const niv_upsample_params* up, void* out_rgba, niv_stream stream) {
+    if (!up) return niv_fail(NIV_ERR_ARG, "upsample params are NULL");
+    if (full_width < 0 || full_height < 0) return niv_fail(NIV_ERR_ARG, "negative image size");
+    if (sub < 1) return niv_fail(NIV_ERR_ARG, "sub must be >= 1");
+    if (full_width == 0 || full_height == 0) return NIV_OK;
+    if (!(up->sigma > 0.0f) || !(up->eps > 0.0f) || !(up->power >= 0.0f))
+        return niv_fail(NIV_ERR_ARG, "sigma and eps must be > 0, power >= 0");
+    if (!pos || !nrm || !albedo || !direct || !E_low || !out_rgba) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if (!aligned16(pos) || !aligned16(nrm) || !aligned16(albedo) || !aligned16(direct) || !aligned16(E_low) ||
+        !aligned16(out_rgba))
+        return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    if ((dtype_in != NIV_F32 && dtype_in != NIV_F16) || (dtype_E != NIV_F32 && dtype_E != NIV_F16))
+        return niv_fail(NIV_ERR_ARG, "record dtype must be NIV_F32 or NIV_F16");
+    return niv_launch_upsample_shade(pos, nrm, albedo, direct, full_width, full_height, dtype_in == NIV_F16, E_low,
+                                     dtype_E == NIV_F16, sub, up->power, up->sigma, up->eps, out_rgba,
+                                     (cudaStream_t)stream);
 }
 
 int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out_rgba,

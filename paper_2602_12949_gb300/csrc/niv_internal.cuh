@@ -29,6 +29,7 @@ struct GridArgs {
     uint32_t hash_mask;  // T - 1
     uint32_t prime_t;
     uint32_t dense_mask;  // bit l set: level l is dense
+    int32_t pe_bands;     // > 0: frequency encoding of the position (no grid levels)
     float aabb_min[3];
     float inv_ext[3];
     float t;
@@ -49,7 +50,19 @@ struct IoArgs {
     // rgba = (albedo * E / pi + direct, 1) instead of E.  FP16 [n][4] records.
     const void* albedo = nullptr;
     const void* direct = nullptr;
+    // Half-resolution rendering (Sec. 4.4): sub > 1 makes record r of the image_width-wide
+    // output the pixel (sub x, sub y) of a src_width-wide full-resolution G-buffer, where
+    // (x, y) is r's position in the output image.
+    int32_t sub = 1;
+    int32_t src_width = 0;
 };
+
+// G-buffer record read for output record r (see IoArgs::sub).
+__device__ __forceinline__ int64_t niv_source_of(const IoArgs& io, int64_t r) {
+    if (io.sub <= 1) return r;
+    const int64_t y = r / io.image_width, x = r - y * io.image_width;
+    return y * io.sub * io.src_width + x * io.sub;
+}
 
 struct niv_model {
     niv_model_desc d;
@@ -129,6 +142,9 @@ int niv_launch_compact(const float* x4, const float* n4, const float* t, const d
                        float* ox4, float* on4, float* ot, float* otarget, int64_t* count_dev, int* scratch,
                        cudaStream_t s);
 int niv_launch_shade(const void* albedo, const void* direct, const void* E, int64_t n, void* out, cudaStream_t s);
+int niv_launch_upsample_shade(const void* pos, const void* nrm, const void* albedo, const void* direct, int32_t width,
+                              int32_t height, int32_t in_f16, const void* E_low, int32_t e_f16, int32_t sub, float power,
+                              float sigma, float eps, void* out, cudaStream_t s);
 int niv_pack_plain(niv_model* m, const float* mlp_host, cudaStream_t s);
 int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s);
 // status: device word for kernel-side failures (nullptr = this device's library status word).
@@ -149,6 +165,12 @@ __device__ __forceinline__ void niv_cell(float u, int32_t N, uint32_t& i, float&
     int ii = min((int)floorf(s), N - 1);
     i = (uint32_t)ii;
     w = __fsub_rn(s, (float)ii);
+}
+
+// Frequency encoding (the models of Table 1 without grid levels): for a coordinate u of
+// the normalised position and band b, (sin(2^b pi u), cos(2^b pi u)); 2^b u is exact in FP32.
+__device__ __forceinline__ void niv_pe_pair(float u, int b, float& s, float& c) {
+    sincospif(__fmul_rn(u, (float)(1 << b)), &s, &c);
 }
 
 // Entry index of vertex v at a level: dense row-major (x fastest) or spatial hash.
@@ -364,6 +386,11 @@ struct NivTileWalk {
         const int32_t px = tx * 16 + ox;
         if (px >= width) return n;
         return (ty * 8 + oy) * (int64_t)width + px;
+    }
+    // G-buffer record of this thread's output record r (see IoArgs::sub).
+    __device__ __forceinline__ int64_t source(int64_t r, const IoArgs& io) const {
+        if (io.sub <= 1) return r;
+        return (ty * 8 + oy) * io.sub * (int64_t)io.src_width + (int64_t)(tx * 16 + ox) * io.sub;
     }
 };
 

@@ -25,11 +25,11 @@ __global__ void __launch_bounds__(kThreads) query_fp32_kernel(GridArgs g, IoArgs
     __syncthreads();
 
     const int k = threadIdx.x;
-    const int LF = g.levels * F;
+    const int LG = g.levels * F, LF = LG + 6 * g.pe_bands;  // grid values, all encoding values
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t r = niv_record_of(tile, k, io.n, io.image_width);
         const bool valid = r < io.n;
-        const int64_t rr = valid ? r : 0;
+        const int64_t rr = valid ? niv_source_of(io, r) : 0;
         const float4 p = niv_load_rec(io.pos, rr, io.in_f16);
         const float4 nv = niv_load_rec(io.nrm, rr, io.in_f16);
         float u[4];
@@ -45,6 +45,13 @@ __global__ void __launch_bounds__(kThreads) query_fp32_kernel(GridArgs g, IoArgs
 #pragma unroll
             for (int j = 0; j < F; ++j) s_x[(l * F + j) * kThreads + k] = acc[j];
         }
+        for (int d = 0; d < 3 && g.pe_bands > 0; ++d)
+            for (int b = 0; b < g.pe_bands; ++b) {
+                float sv, cv;
+                niv_pe_pair(u[d], b, sv, cv);
+                s_x[(LG + 2 * (d * g.pe_bands + b)) * kThreads + k] = sv;
+                s_x[(LG + 2 * (d * g.pe_bands + b) + 1) * kThreads + k] = cv;
+            }
         s_x[(LF + 0) * kThreads + k] = nv.x;
         s_x[(LF + 1) * kThreads + k] = nv.y;
         s_x[(LF + 2) * kThreads + k] = nv.z;

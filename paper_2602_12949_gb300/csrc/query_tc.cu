@@ -4,7 +4,8 @@
 // pixel block for images) and walks tiles persistently.  Per tile:
 //   1. every thread encodes its own record (Sec. 4.1: per level the cell, the
 //      2^d corner entries -- dense or hashed --, FP16 feature gathers served from
-//      L2, multilinear weights in FP32) and writes its row of the network input
+//      L2, multilinear weights in FP32; or, for the models of Table 1 without
+//      grid, the sin / cos pairs of the frequency encoding) and writes its row of the network input
 //      [features | n, (t), 1 | 0-pad] as FP16, in 16-byte chunks, into a shared-memory
 //      tile laid out in the tensor core's canonical K-major format (the constant 1
 //      multiplies the first layer's bias, stored as an extra weight column);
@@ -101,6 +102,40 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t act, uint32_
     tc::mma_commit(bar);
 }
 
+// Frequency encoding of one record (PE bands, PE > 0 fixed at compile time, PE < 0 taken
+// from g): the pairs (sin, cos)(2^b pi u_d) in FP16, d-major then b, columns [0, 6B); the
+// columns up to the next multiple of 8 are zero.
+template <int PE>
+__device__ __forceinline__ void encode_pe(const GridArgs& g, const float* u, uint8_t* s_act, int tid, int K1) {
+    if (PE > 0 && PE % 4 == 0) {  // whole 16-byte chunks of 4 pairs
+#pragma unroll 1
+        for (int q = 0; q < 3 * PE / 4; ++q) {
+            const int d = q / (PE / 4), b0 = (q % (PE / 4)) * 4;
+            const float ud = d == 0 ? u[0] : (d == 1 ? u[1] : u[2]);
+            uint32_t wd[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float sv, cv;
+                niv_pe_pair(ud, b0 + j, sv, cv);
+                wd[j] = pack_half2(sv, cv);
+            }
+            *reinterpret_cast<uint4*>(s_act + core_off(tid, 8 * q, K1)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        }
+    } else {
+        const int B = g.pe_bands, pairs = 3 * B;
+        for (int p = 0; p < ((pairs + 3) & ~3); ++p) {
+            uint32_t v = 0u;
+            if (p < pairs) {
+                const int d = p / B;
+                float sv, cv;
+                niv_pe_pair(d == 0 ? u[0] : (d == 1 ? u[1] : u[2]), p - d * B, sv, cv);
+                v = pack_half2(sv, cv);
+            }
+            *reinterpret_cast<uint32_t*>(s_act + core_off(tid, 2 * p, K1)) = v;
+        }
+    }
+}
+
 // Encode levels [l0, l0 + G) of one record into one 16-byte chunk of FP16 features,
 // kILP levels' gathers in flight at a time.
 template <int DIMS, int F, typename TabT>
@@ -146,7 +181,8 @@ __device__ __forceinline__ void group_sync(int wg) { asm volatile("bar.sync %0, 
 // mbarrier, named barrier, 64 TMEM columns) and all share the weights in shared memory.
 // LV > 0: the level count is a compile-time constant, so the level loop unrolls fully and
 // every per-level constant (resolution, table offset, dense flag) is an immediate operand.
-template <int DIMS, int F, int LV, typename TabT>
+// PE != 0: frequency-encoded model without grid (PE > 0: that many bands, fixed at compile time).
+template <int DIMS, int F, int LV, int PE, typename TabT>
 __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(GridArgs g, IoArgs io,
                                                                 const TabT* __restrict__ grid,
                                                                 const uint8_t* __restrict__ packed, TcLayout lay,
@@ -195,7 +231,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
     for (; walk.tile < n_tiles && ok; walk.next()) {
         const int64_t r = walk.record(tid, io.n, io.image_width);
         const bool valid = r < io.n;
-        const int64_t rr = valid ? r : 0;
+        const int64_t rr = valid ? walk.source(r, io) : 0;
         const float4 p = niv_load_rec(io.pos, rr, io.in_f16);
         const float4 nv = niv_load_rec(io.nrm, rr, io.in_f16);
         float u[4];
@@ -205,7 +241,9 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         u[3] = fminf(fmaxf(g.t, 0.0f), 1.0f);
 
         // ---- 1. encoding -> FP16 input row, one 16-byte chunk per G levels ----
-        if (LV > 0) {
+        if (PE != 0) {
+            encode_pe<PE>(g, u, s_act, tid, K1);
+        } else if (LV > 0) {
 #pragma unroll
             for (int l0 = 0; l0 < LV; l0 += G)
                 *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, LV, u);
@@ -214,7 +252,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                 *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, L, u);
         }
         {   // [n.x, n.y, n.z, (t), 1, 0, ...]: the 1 multiplies the first layer's bias column
-            const bool has_t = g.n_in > L * F + 3;
+            const bool has_t = g.n_in > (PE != 0 ? 0 : L * F) + 6 * g.pe_bands + 3;
             const uint32_t one = (uint32_t)__half_as_ushort(__float2half_rn(1.0f));
             uint4 c = make_uint4(pack_half2(nv.x, nv.y), has_t ? pack_half2(nv.z, u[3]) : (pack_half2(nv.z, 0.0f) & 0xFFFFu) | (one << 16), 0u, 0u);
             if (has_t) c.z = one;
@@ -326,10 +364,10 @@ size_t tc_smem_bytes(const TcLayout& lay) {
     return (size_t)kHdr + ((lay.total + 127u) & ~127u) + (size_t)kWG * kT * kmax * 2;
 }
 
-template <int DIMS, int F, int LV>
+template <int DIMS, int F, int LV, int PE = 0>
 int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s, int* status) {
     const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
-    auto kern = query_tc_f16_kernel<DIMS, F, LV, __half>;
+    auto kern = query_tc_f16_kernel<DIMS, F, LV, PE, __half>;
     const __half* grid = m->grid_f16;
     const size_t smem = tc_smem_bytes(*lay);
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -379,6 +417,13 @@ template <int DIMS>
 int by_feat(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s, int* status) {
     // fully unrolled encoders for the common level counts (16: configs 1, 3, 4; 8: config 0 and the
     // paper's 8-level model), a runtime loop otherwise
+    if (m->d.pe_bands > 0) {  // no grid: the frequency encoding (8 bands in Table 1)
+        if constexpr (DIMS == 3) {
+            if (m->d.pe_bands == 8) return launch<DIMS, 2, 0, 8>(m, g, io, s, status);
+            return launch<DIMS, 2, 0, -1>(m, g, io, s, status);
+        }
+        return niv_fail(NIV_ERR_UNSUPPORTED, "frequency encoding is 3-D");
+    }
     switch (m->d.feat) {
         case 1: return launch<DIMS, 1, 0>(m, g, io, s, status);
         case 2:
@@ -401,7 +446,8 @@ int by_feat(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_
 // round_up(L*F, 8); the first layer's bias sits in column col_one, which the kernel
 // fills with 1 in every input row.
 int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s) {
-    const int W = m->d.width, nh = m->d.n_hidden, n_in = m->n_in, LF = m->d.levels * m->d.feat;
+    const int W = m->d.width, nh = m->d.n_hidden, n_in = m->n_in;
+    const int LF = m->d.levels * m->d.feat + 6 * m->d.pe_bands;  // encoding values
     TcLayout lay;
     memset(&lay, 0, sizeof lay);
     lay.col_extra = (LF + 7) & ~7;

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kT) fwd_bwd_kernel(GridArgs g, const float4* _
                                                      float eps, float inv_count, float* __restrict__ grad,
                                                      float* __restrict__ stash, double* __restrict__ loss_sum) {
     extern __shared__ float smem[];
-    const int n_in = g.n_in, LF = g.levels * F;
+    const int n_in = g.n_in, LG = g.levels * F, LF = LG + 6 * g.pe_bands;  // grid values, all encoding values
     // weights of every layer, row-major as stored: [W1 | b1 | W2 | b2 | ... | Wo | bo]
     const int n_mlp = W * n_in + W + (nh - 1) * (W * W + W) + 3 * W + 3;
     float* s_w = smem;
@@ -60,6 +60,13 @@ __global__ void __launch_bounds__(kT) fwd_bwd_kernel(GridArgs g, const float4* _
 #pragma unroll
         for (int j = 0; j < F; ++j) s_a[(l * F + j) * kT + tid] = acc[j];
     }
+    for (int d = 0; d < 3 && g.pe_bands > 0; ++d)
+        for (int b = 0; b < g.pe_bands; ++b) {
+            float sv, cv;
+            niv_pe_pair(u[d], b, sv, cv);
+            s_a[(LG + 2 * (d * g.pe_bands + b)) * kT + tid] = sv;
+            s_a[(LG + 2 * (d * g.pe_bands + b) + 1) * kT + tid] = cv;
+        }
     s_a[(LF + 0) * kT + tid] = nv.x;
     s_a[(LF + 1) * kT + tid] = nv.y;
     s_a[(LF + 2) * kT + tid] = nv.z;

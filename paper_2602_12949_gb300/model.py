@@ -9,7 +9,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import check, lib, ModelDesc, QueryParams, FitParams
+from ._lib import check, lib, ModelDesc, QueryParams, FitParams, UpsampleParams
 
 PRECISIONS = {"fp32": _lib.NIV_FP32, "fp16": _lib.NIV_FP16, "fp8": _lib.NIV_FP8}
 
@@ -38,11 +38,11 @@ class NIVModel:
     """One Neural Irradiance Volume on the current CUDA device."""
 
     def __init__(self, dims=3, levels=16, feat=2, log2_T=17, base=16.0, growth=1.38, n_hidden=2, width=64,
-                 in_extra=None, out_dim=3, out_act=1, prime_t=0x9E3779B1):
+                 in_extra=None, out_dim=3, out_act=1, prime_t=0x9E3779B1, pe_bands=0):
         if in_extra is None:
             in_extra = 4 if dims == 4 else 3
         self.desc = ModelDesc(dims, levels, feat, log2_T, float(base), float(growth), n_hidden, width, in_extra,
-                              out_dim, out_act, prime_t)
+                              out_dim, out_act, prime_t, pe_bands)
         h = ctypes.c_void_p()
         check(lib().niv_create(ctypes.byref(self.desc), ctypes.byref(h)))
         self._h = h
@@ -64,7 +64,7 @@ class NIVModel:
 
     @property
     def n_in(self):
-        return self.desc.levels * self.desc.feat + self.desc.in_extra
+        return self.desc.levels * self.desc.feat + 6 * self.desc.pe_bands + self.desc.in_extra
 
     def param_count(self):
         g, m = ctypes.c_int64(), ctypes.c_int64()
@@ -122,6 +122,27 @@ class NIVModel:
         check(lib().niv_query(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
                               pos.shape[0], _rec_dtype(pos), ctypes.byref(qp), ctypes.c_void_p(out.data_ptr()),
                               _rec_dtype(out), PRECISIONS[precision], _stream(stream)))
+        return out
+
+    def query_sub(self, pos, nrm, width, height, sub=2, out=None, precision="fp16", aabb_min=(0.0, 0.0, 0.0),
+                  aabb_max=(1.0, 1.0, 1.0), t=0.0, out_dtype=None, stream=None):
+        """E at the pixels (sub x, sub y) of a width x height G-buffer (device [H*W][4] records);
+        returns out ([h*w][4], h = ceil(height / sub), w = ceil(width / sub))."""
+        _check_records(pos, "pos")
+        _check_records(nrm, "nrm")
+        if pos.shape != nrm.shape or pos.dtype != nrm.dtype or pos.shape[0] != width * height:
+            raise ValueError("pos and nrm must both hold width * height records of one dtype")
+        n_low = ((width + sub - 1) // sub) * ((height + sub - 1) // sub)
+        if out is None:
+            out = torch.empty((n_low, 4), dtype=out_dtype or pos.dtype, device=pos.device)
+        _check_records(out, "out")
+        if out.shape[0] != n_low:
+            raise ValueError("out must hold ceil(width / sub) * ceil(height / sub) records")
+        qp = self.query_params(aabb_min, aabb_max, t, 0)
+        check(lib().niv_query_sub(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                                  int(width), int(height), int(sub), _rec_dtype(pos), ctypes.byref(qp),
+                                  ctypes.c_void_p(out.data_ptr()), _rec_dtype(out), PRECISIONS[precision],
+                                  _stream(stream)))
         return out
 
     def query_shade(self, pos, nrm, albedo, direct, out=None, precision="fp16", aabb_min=(0.0, 0.0, 0.0),
@@ -223,17 +244,37 @@ class NIVModel:
         return sa, sw, am
 
     def encode(self, pos, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), t=0.0, want_idx=True, stream=None):
-        """(features [n][L*F] float32, corner indices [n][L][2^dims] int32 or None) for device records."""
+        """(encoding [n][L*F + 6*pe_bands] float32, corner indices [n][L][2^dims] int32 or None)
+        for device records."""
         _check_records(pos, "pos")
         n = pos.shape[0]
         L, F, nc = self.desc.levels, self.desc.feat, 1 << self.desc.dims
-        enc = torch.empty((n, L * F), dtype=torch.float32, device=pos.device)
+        enc = torch.empty((n, L * F + 6 * self.desc.pe_bands), dtype=torch.float32, device=pos.device)
         idx = torch.empty((n, L, nc), dtype=torch.int32, device=pos.device) if want_idx else None
         qp = self.query_params(aabb_min, aabb_max, t, 0)
         check(lib().niv_encode(self._h, ctypes.c_void_p(pos.data_ptr()), n, _rec_dtype(pos), ctypes.byref(qp),
                                ctypes.c_void_p(enc.data_ptr()),
                                ctypes.c_void_p(idx.data_ptr() if idx is not None else 0), _stream(stream)))
         return enc, idx
+
+
+def upsample_shade(pos, nrm, albedo, direct, width, height, E_low, sub=2, power=8.0, sigma=0.05, eps=1e-4,
+                   out=None, stream=None):
+    """Full-resolution FP16 rgba from irradiance E_low queried at every sub-th pixel (joint
+    bilateral upsampling guided by the G-buffer, then albedo * E / pi + direct)."""
+    for t, name in ((pos, "pos"), (nrm, "nrm"), (albedo, "albedo"), (direct, "direct"), (E_low, "E_low")):
+        _check_records(t, name)
+    if albedo.dtype != torch.float16 or direct.dtype != torch.float16:
+        raise TypeError("albedo and direct must be float16 records")
+    if out is None:
+        out = torch.empty((width * height, 4), dtype=torch.float16, device=pos.device)
+    up = UpsampleParams(float(power), float(sigma), float(eps))
+    check(lib().niv_upsample_shade(ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                                   ctypes.c_void_p(albedo.data_ptr()), ctypes.c_void_p(direct.data_ptr()),
+                                   int(width), int(height), _rec_dtype(pos), ctypes.c_void_p(E_low.data_ptr()),
+                                   _rec_dtype(E_low), int(sub), ctypes.byref(up), ctypes.c_void_p(out.data_ptr()),
+                                   _stream(stream)))
+    return out
 
 
 def shade(albedo, direct, E, out=None, stream=None):

@@ -1,0 +1,152 @@
+"""GPU parity of the frequency-encoded models (Table 1's rows without grid levels).
+
+Sec. 4.1: the smaller models replace the hash grid by an eight-band positional
+encoding of the position.  The oracle's encoding is pinned in
+tests/test_oracle_pe.py; here the FP32 plain kernel, the fused FP16 tensor-core
+kernel, the encoding entry point and the training gradient must reproduce it,
+through the C ABI.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from niv_inputs import init_params, uniform_queries
+from niv_inputs.configs import MODEL_PE16, MODEL_PE32, MODEL_PE64, ROOM_MIN, ROOM_MAX, room_gbuffer
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+FP32_BOUND = 1e-5
+FP16_BOUND = 2e-3
+# Against the oracle's FP16 path (binary16 inputs and activations, pinned in
+# tests/test_oracle_pe.py) only FP32-vs-FP64 arithmetic remains, and it decides a binary16
+# rounding of an encoding value or activation differently where the value lies within an
+# FP32 rounding error of a rounding point.  Such a flip moves one value by one binary16 step
+# (2^-11 of its size).  Bar: every sample within 2^-10 of the frame's max E (two binary16
+# steps at the frame's scale), and >= 98% of samples agree to 1e-5 of it (measured: at most
+# 5.1e-4 and 98.6-100%; an FP32 emulation of the kernel on the CPU gives 2-3e-4, 98.6-99.7%).
+FP16_PATH_NORM_BOUND = 2.0 ** -10
+FP16_PATH_AGREE = 0.98
+GRAD_BOUND = 1e-4
+
+
+@pytest.fixture(scope="module")
+def niv():
+    from paper_2602_12949_gb300.build import build
+    build()
+    import paper_2602_12949_gb300 as P
+    return P
+
+
+def rel_err(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    return float(np.max(np.abs(got - ref) / den))
+
+
+def path_parity(got, ref):
+    """(max |got - ref| / max |ref|, fraction of samples with every channel within 1e-5 of max |ref|)."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    nab = np.abs(got - ref) / np.abs(ref).max()
+    return float(nab.max()), float(np.mean(np.all(nab <= 1e-5, axis=1)))
+
+
+def make(P, spec, seed=0, bias_std=0.1):
+    m = P.NIVModel(**spec)
+    g, _ = m.param_count()
+    assert g == 0
+    params = init_params(g, m.layer_shapes(), seed=seed, bias_std=bias_std)
+    m.set_params(params)
+    return m, params, oracle.Model(**spec)
+
+
+@pytest.mark.parametrize("spec", [MODEL_PE16, MODEL_PE32, MODEL_PE64, dict(MODEL_PE32, pe_bands=5),
+                                  dict(MODEL_PE64, n_hidden=1)])
+@pytest.mark.parametrize("n", [1, 1000, 65536 + 77])
+def test_fp32_and_fp16_match_oracle(niv, spec, n):
+    """FP32 within 1e-5 of the FP64 oracle.  FP16 at the FP16-path bar above; against the
+    unquantised network it keeps the 2e-3 bound unless the FP16 format itself
+    departs further on these queries (48 encoding values of size O(1) are rounded to
+    binary16, against O(1e-2) grid features), then within 1.5x the format's own error."""
+    m, params, om = make(niv, spec)
+    pos, nrm = uniform_queries(n, seed=n)
+    p16 = params.astype(np.float16).astype(np.float64)
+    ref = oracle.query(om, params, pos, nrm)
+    ref16 = oracle.query(om, p16, pos, nrm)
+    ref16_path = oracle.query_f16(om, p16, pos, nrm)
+    dp, dn = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+    e32 = m.query(dp, dn, precision="fp32", out_dtype=torch.float32)[:, :3].cpu().numpy()
+    e16 = m.query(dp, dn, precision="fp16", out_dtype=torch.float32)[:, :3].cpu().numpy()
+    fmt = rel_err(ref16_path, ref16)
+    worst, agree = path_parity(e16, ref16_path)
+    print("fp32 %.2e  fp16 vs path: max %.2e agree %.4f  fp16 vs network %.2e  format %.2e"
+          % (rel_err(e32, ref), worst, agree, rel_err(e16, ref16), fmt))
+    assert rel_err(e32, ref) <= FP32_BOUND
+    assert worst <= FP16_PATH_NORM_BOUND and agree >= FP16_PATH_AGREE
+    assert rel_err(e16, ref16) <= max(FP16_BOUND, 1.5 * fmt)
+    m.close()
+
+
+def test_room_frame_image_traversal(niv):
+    pos, nrm, _ = room_gbuffer(480, 270)
+    m, params, om = make(niv, MODEL_PE64)
+    ref16 = oracle.query_f16(om, params.astype(np.float16).astype(np.float64), pos.astype(np.float32),
+                             nrm.astype(np.float32), ROOM_MIN, ROOM_MAX)
+    dp, dn = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)
+    e_img = m.query(dp, dn, precision="fp16", image_width=480, out_dtype=torch.float32, **kw)
+    e_lin = m.query(dp, dn, precision="fp16", out_dtype=torch.float32, **kw)
+    assert torch.equal(e_img, e_lin)
+    worst, agree = path_parity(e_img[:, :3].cpu().numpy(), ref16)
+    assert worst <= FP16_PATH_NORM_BOUND and agree >= FP16_PATH_AGREE
+    m.close()
+
+
+def test_encoding_entry_matches_oracle(niv):
+    m, params, om = make(niv, dict(MODEL_PE16, pe_bands=7))
+    pos, _ = uniform_queries(5000, seed=9)
+    enc, idx = m.encode(torch.from_numpy(pos).cuda(), want_idx=False)
+    ref = oracle.encode(om, params, pos)
+    assert enc.shape == (5000, 42)
+    assert float(np.max(np.abs(enc.cpu().numpy() - ref))) <= 2e-6
+    m.close()
+
+
+@pytest.mark.parametrize("spec", [MODEL_PE32, dict(MODEL_PE16, n_hidden=2, pe_bands=6)])
+def test_gradient_matches_oracle(niv, spec):
+    m, params, om = make(niv, spec, seed=3, bias_std=0.2)
+    n = 3000
+    pos, nrm = uniform_queries(n, seed=4)
+    target = np.zeros((n, 4), np.float32)
+    target[:, :3] = np.random.default_rng(5).uniform(0.1, 2.0, (n, 3))
+    dev = lambda a: torch.from_numpy(a).cuda()
+    loss = m.grad(dev(pos), dev(nrm), dev(target))
+    got = m.get_grads().astype(np.float64)
+    ref_loss, ref = oracle.loss_grad(om, params, pos, nrm, target[:, :3])
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    off = 0
+    for (o, i) in oracle.layer_shapes(om):
+        for a, b in ((off, off + o * i), (off + o * i, off + o * i + o)):
+            scale = np.abs(ref[a:b]).max()
+            assert np.max(np.abs(got[a:b] - ref[a:b])) <= GRAD_BOUND * scale
+        off += o * i + o
+    m.close()
+
+
+def test_fp8_refused_for_frequency_models(niv):
+    m, _, _ = make(niv, MODEL_PE64)
+    pos, nrm = uniform_queries(256, seed=1)
+    with pytest.raises(niv.NivError):
+        m.fp8_calibrate(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda())
+    m.close()
+
+
+def test_descriptor_rules(niv):
+    with pytest.raises(niv.NivError):
+        niv.NIVModel(**dict(MODEL_PE16, levels=4))       # grid and frequency encoding together
+    with pytest.raises(niv.NivError):
+        niv.NIVModel(**dict(MODEL_PE16, dims=4, in_extra=4))
+    with pytest.raises(niv.NivError):
+        niv.NIVModel(**dict(MODEL_PE16, pe_bands=17))
