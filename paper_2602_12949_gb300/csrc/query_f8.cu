@@ -1,8 +1,9 @@
 // FP8 (E4M3) fused query on the tensor cores, its calibration and its weight packing.
 //
-// Same tile pipeline as the FP16 path (query_tc.cu): a warpgroup encodes 128 records
-// (FP16 grid features, FP32 interpolation), writes the network input as E4M3 bytes
-// into a K-major shared-memory tile, and every layer runs as tcgen05.mma of
+// Same tile pipeline as the FP16 path (query_tc.cu): persistent CTAs of 8 warpgroups that
+// share one copy of the weights; a warpgroup encodes 128 records (FP16 grid features, FP32
+// interpolation), writes the network input as E4M3 bytes into its K-major shared-memory
+// tile, and every layer runs as tcgen05.mma of
 // kind::f8f6f4 (E4M3 x E4M3, K = 32 per instruction) into an FP32 TMEM accumulator.
 // Per-layer power-of-two scales (the FP8 reading of the design notes): weights
 // e4m3(W / s_w), inputs e4m3(a / s_a), and the epilogue forms
@@ -70,25 +71,72 @@ __device__ __forceinline__ void issue_layer8(uint32_t tmem, uint32_t act, uint32
     tc::mma_commit(bar);
 }
 
+// One E4M3 byte pair (a, b), rounded to nearest with saturation, in the low 16 bits.
+__device__ __forceinline__ uint32_t e4m3x2(float a, float b) {
+    return __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3) & 0xFFFFu;
+}
+
+// Encode levels [l0, l0 + 16/F) of one record into one 16-byte chunk of E4M3 inputs (value
+// times q0, the inverse input scale), each level converted as soon as it is blended.
 template <int DIMS, int F>
-__global__ void __launch_bounds__(kT, 8) query_f8_kernel(GridArgs g, IoArgs io, const __half* __restrict__ grid16,
-                                                         const uint8_t* __restrict__ packed, F8Layout lay, int out_act,
-                                                         int64_t n_tiles, uint32_t tmem_cols, int* __restrict__ status) {
+__device__ __forceinline__ uint4 encode_chunk8(const GridArgs& g, const __half* __restrict__ grid16, int l0, int L,
+                                               const float* u, float q0) {
+    constexpr int NC = 1 << DIMS, G = 16 / F;
+    using R = typename NivRaw<F, __half>::T;
+    uint32_t wd[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        if (l0 + q >= L) continue;
+        uint32_t e[NC];
+        float wc[NC];
+        R raw[NC];
+        niv_level_corners<DIMS>(g, l0 + q, u, e, wc);
+        niv_level_gather<NC, F, __half>(grid16 + (size_t)g.offset[l0 + q] * F, e, raw);
+        float acc[F];
+        niv_level_blend<NC, F>(raw, wc, acc);
+        if (F == 1) {
+            wd[q >> 2] |= (e4m3x2(acc[0] * q0, 0.0f) & 0xFFu) << (8 * (q & 3));
+        } else if (F == 2) {
+            const uint32_t h = e4m3x2(acc[0] * q0, acc[1 % F] * q0);
+            wd[(q >> 1) & 3] |= (q & 1) ? (h << 16) : h;
+        } else {
+            wd[q & 3] = e4m3x2(acc[0] * q0, acc[1 % F] * q0) | (e4m3x2(acc[2 % F] * q0, acc[3 % F] * q0) << 16);
+        }
+    }
+    return make_uint4(wd[0], wd[1], wd[2], wd[3]);
+}
+
+#ifndef NIV_F8_WG
+#define NIV_F8_WG 8
+#endif
+constexpr int kWG = NIV_F8_WG;  // warpgroups (independent tile pipelines) per CTA sharing the weights
+
+__device__ __forceinline__ void group_sync8(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory"); }
+
+// kWG warpgroups per CTA, persistent over 128-record tiles; each warpgroup owns an activation
+// tile, an mbarrier, a named barrier and its TMEM columns.  LV > 0: level count fixed at
+// compile time (the level loop unrolls).
+template <int DIMS, int F, int LV>
+__global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArgs io, const __half* __restrict__ grid16,
+                                                                const uint8_t* __restrict__ packed, F8Layout lay,
+                                                                int out_act, int64_t n_tiles, uint32_t tmem_cols,
+                                                                int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);  // one per warpgroup
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + 64);
     uint8_t* s_net = smem + kHdr;
-    uint8_t* s_act = s_net + ((lay.total + 127u) & ~127u);
-    const int tid = threadIdx.x, warp = tid >> 5;
     const int K1 = lay.K1, W = lay.W, nh = lay.n_hidden;
+    const uint32_t act_bytes = (uint32_t)kT * (uint32_t)(K1 > W ? K1 : W);
+    const int wg = threadIdx.x / kT, tid = threadIdx.x % kT, warp = tid >> 5;
+    uint8_t* s_act = s_net + ((lay.total + 127u) & ~127u) + wg * act_bytes;
 
-    for (uint32_t i = tid; i < lay.total / 16; i += kT)
+    for (uint32_t i = threadIdx.x; i < lay.total / 16; i += kT * kWG)
         reinterpret_cast<uint4*>(s_net)[i] = __ldg(reinterpret_cast<const uint4*>(packed) + i);
-    if (tid == 0) {
-        tc::mbar_init(s_bar, 1);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kWG; ++i) tc::mbar_init(s_bar + i, 1);
         tc::fence_mbar_init();
     }
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
         tc::tmem_alloc(tc::smem_u32(s_tmem), tmem_cols);
         tc::tmem_relinquish();
     }
@@ -97,23 +145,26 @@ __global__ void __launch_bounds__(kT, 8) query_f8_kernel(GridArgs g, IoArgs io, 
     __syncthreads();
     tc::fence_after_sync();
 
-    const uint32_t tmem = *s_tmem;
+    const uint32_t wg_cols = W <= 32 ? 32u : 64u;
+    const uint32_t tmem = *s_tmem + (uint32_t)wg * wg_cols;
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint32_t bar = tc::smem_u32(s_bar);
+    const uint32_t bar = tc::smem_u32(s_bar + wg);
     const uint32_t act_a = tc::smem_u32(s_act), net_a = tc::smem_u32(s_net);
     const uint32_t idesc_h = tc::idesc_e4m3(128, W), idesc_o = tc::idesc_e4m3(128, kNO);
     const float* s_c = reinterpret_cast<const float*>(s_net + lay.scal);  // acc -> z multipliers
     const float* s_q = s_c + (nh + 1);                                   // 1 / s_a per matrix input
     const float* s_b = s_q + (nh + 1);                                   // biases
-    const int L = g.levels, LF = L * F;
+    const int L = LV > 0 ? LV : g.levels, LF = L * F;
     constexpr int G = 16 / F;  // levels per 16-byte chunk of E4M3 inputs
     uint32_t phase = 0;
     bool ok = true;
 
-    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int64_t r = niv_record_of(tile, tid, io.n, io.image_width);
+    NivTileWalk walk;
+    walk.init((int64_t)blockIdx.x * kWG + wg, (int64_t)gridDim.x * kWG, tid, io.image_width);
+    for (; walk.tile < n_tiles && ok; walk.next()) {
+        const int64_t r = walk.record(tid, io.n, io.image_width);
         const bool valid = r < io.n;
-        const int64_t rr = valid ? niv_source_of(io, r) : 0;
+        const int64_t rr = valid ? walk.source(r, io) : 0;
         const float4 p = niv_load_rec(io.pos, rr, io.in_f16);
         const float4 nv = niv_load_rec(io.nrm, rr, io.in_f16);
         float u[4];
@@ -124,36 +175,24 @@ __global__ void __launch_bounds__(kT, 8) query_f8_kernel(GridArgs g, IoArgs io, 
 
         // ---- encoding -> E4M3 input row ----
         const float q0 = s_q[0];
-        for (int l0 = 0; l0 < L; l0 += G) {
-            float v[16];
+        if (LV > 0) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.0f;
-#pragma unroll
-            for (int q = 0; q < G; ++q) {
-                if (l0 + q < L) {
-                    float acc[F];
-                    niv_encode_level<DIMS, F, __half>(g, grid16, l0 + q, u, acc);
-#pragma unroll
-                    for (int j = 0; j < F; ++j) v[q * F + j] = acc[j];
-                }
-            }
-            *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K1)) = e4m3x16(v, q0);
+            for (int l0 = 0; l0 < LV; l0 += G)
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K1)) = encode_chunk8<DIMS, F>(g, grid16, l0, LV, u, q0);
+        } else {
+            for (int l0 = 0; l0 < L; l0 += G)
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K1)) = encode_chunk8<DIMS, F>(g, grid16, l0, L, u, q0);
         }
         {
-            float v[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.0f;
-            v[0] = nv.x;
-            v[1] = nv.y;
-            v[2] = nv.z;
-            if (g.n_in > LF + 3) v[3] = u[3];
-            *reinterpret_cast<uint4*>(s_act + core_off8(tid, lay.col_extra, K1)) = e4m3x16(v, q0);
+            const float tv = g.n_in > LF + 3 ? u[3] : 0.0f;
+            *reinterpret_cast<uint4*>(s_act + core_off8(tid, lay.col_extra, K1)) =
+                make_uint4(e4m3x2(nv.x * q0, nv.y * q0) | (e4m3x2(nv.z * q0, tv * q0) << 16), 0u, 0u, 0u);
         }
         for (int k = lay.col_extra + 16; k < K1; k += 16)
             *reinterpret_cast<uint4*>(s_act + core_off8(tid, k, K1)) = make_uint4(0u, 0u, 0u, 0u);
         tc::fence_async_smem();
         tc::fence_before_sync();
-        __syncthreads();
+        group_sync8(wg);
 
         // ---- hidden layers ----
         uint32_t K = (uint32_t)K1, w_off = lay.w1;
@@ -180,7 +219,7 @@ __global__ void __launch_bounds__(kT, 8) query_f8_kernel(GridArgs g, IoArgs io, 
             }
             tc::fence_async_smem();
             tc::fence_before_sync();
-            __syncthreads();
+            group_sync8(wg);
             w_off = layer == 0 ? lay.wh : w_off + (uint32_t)(W * W);
             K = (uint32_t)W;
         }
@@ -210,21 +249,20 @@ __global__ void __launch_bounds__(kT, 8) query_f8_kernel(GridArgs g, IoArgs io, 
         }
         if (valid) niv_store_result(io, r, z0, z1, z2);
         tc::fence_before_sync();
-        __syncthreads();
+        group_sync8(wg);  // the next tile's encoder overwrites the activation tile
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+    if (threadIdx.x < 32) tc::tmem_dealloc(*s_tmem, tmem_cols);
 }
 
-template <int DIMS, int F>
+template <int DIMS, int F, int LV>
 int launch8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
     const F8Layout* lay = reinterpret_cast<const F8Layout*>(m->f8_layout);
-    auto kern = query_f8_kernel<DIMS, F>;
+    auto kern = query_f8_kernel<DIMS, F, LV>;
     const int kmax = lay->K1 > lay->W ? lay->K1 : lay->W;
-    const size_t smem = (size_t)kHdr + ((lay->total + 127u) & ~127u) + (size_t)kT * kmax;
+    const size_t smem = (size_t)kHdr + ((lay->total + 127u) & ~127u) + (size_t)kWG * kT * kmax;
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
     int dev = 0, sms = 0, smem_per_sm = 0, regs_per_sm = 0;
     NIV_CUDA(cudaGetDevice(&dev));
     NIV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -232,18 +270,27 @@ int launch8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_
     NIV_CUDA(cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
     cudaFuncAttributes fa;
     NIV_CUDA(cudaFuncGetAttributes(&fa, kern));
-    // residency from the register and shared-memory budgets (see query_tc.cu)
+    // residency from the register and shared-memory budgets (the occupancy API reports a
+    // single CTA per SM for kernels that allocate tensor memory)
     const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 1;
     int per_sm = smem_per_sm / (int)(smem + 1024);
-    if (regs_per_sm / (kT * regs) < per_sm) per_sm = regs_per_sm / (kT * regs);
-    const uint32_t cols = lay->W <= 32 ? 32u : 64u;
+    if (regs_per_sm / (kT * kWG * regs) < per_sm) per_sm = regs_per_sm / (kT * kWG * regs);
+    uint32_t cols = 32u;  // TMEM is allocated in powers of two from 32 to 512 columns
+    while (cols < (lay->W <= 32 ? 32u : 64u) * (uint32_t)kWG) cols <<= 1;
+    if (cols > 512u) return niv_fail(NIV_ERR_UNSUPPORTED, "too many warpgroups for tensor memory");
     if (per_sm > (int)(512 / cols)) per_sm = (int)(512 / cols);
     if (per_sm < 1) return niv_fail(NIV_ERR_UNSUPPORTED, "FP8 query kernel does not fit on an SM");
+    // shared memory for the resident CTAs only; the rest of the SM's storage is L1 for the gathers
+    int carve = (int)((100 * (int64_t)per_sm * (int64_t)(smem + 1024) + smem_per_sm - 1) / smem_per_sm);
+    if (carve > 100) carve = 100;
+    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
     int* status = niv_status_word();
     if (!status) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
     const int64_t tiles = niv_tile_count_host(io.n, io.image_width);
-    const int64_t blocks = tiles < (int64_t)sms * per_sm ? tiles : (int64_t)sms * per_sm;
-    kern<<<(unsigned)blocks, kT, smem, s>>>(g, io, m->grid_f16, m->mlp_f8, *lay, m->d.out_act, tiles, cols, status);
+    const int64_t need = (tiles + kWG - 1) / kWG;
+    const int64_t blocks = need < (int64_t)sms * per_sm ? need : (int64_t)sms * per_sm;
+    kern<<<(unsigned)blocks, kT * kWG, smem, s>>>(g, io, m->grid_f16, m->mlp_f8, *lay, m->d.out_act, tiles, cols,
+                                                  status);
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }
@@ -420,16 +467,20 @@ int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io,
     if (!m->fp8_ready) return niv_fail(NIV_ERR_ARG, "FP8 path needs niv_fp8_calibrate after the last niv_set_params");
     const F8Layout* lay = reinterpret_cast<const F8Layout*>(m->f8_layout);
     if (lay->K1 > 128) return niv_fail(NIV_ERR_UNSUPPORTED, "FP8 path needs a network input of <= 112 values");
+    // fully unrolled encoders for 16 levels of 2 features (configs 1, 3, 4), a runtime loop otherwise
+    const bool l16 = g.levels == 16 && m->d.feat == 2;
     if (m->d.dims == 4) {
+        if (l16) return launch8<4, 2, 16>(m, g, io, s);
         switch (m->d.feat) {
-            case 1: return launch8<4, 1>(m, g, io, s);
-            case 2: return launch8<4, 2>(m, g, io, s);
-            default: return launch8<4, 4>(m, g, io, s);
+            case 1: return launch8<4, 1, 0>(m, g, io, s);
+            case 2: return launch8<4, 2, 0>(m, g, io, s);
+            default: return launch8<4, 4, 0>(m, g, io, s);
         }
     }
+    if (l16) return launch8<3, 2, 16>(m, g, io, s);
     switch (m->d.feat) {
-        case 1: return launch8<3, 1>(m, g, io, s);
-        case 2: return launch8<3, 2>(m, g, io, s);
-        default: return launch8<3, 4>(m, g, io, s);
+        case 1: return launch8<3, 1, 0>(m, g, io, s);
+        case 2: return launch8<3, 2, 0>(m, g, io, s);
+        default: return launch8<3, 4, 0>(m, g, io, s);
     }
 }
