@@ -46,6 +46,9 @@ def _args():
     ap.add_argument("--res", default="1080p", choices=["1080p", "4k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison and error checks")
+    ap.add_argument("--workload", default="config1", choices=["config1", "config3", "half"],
+                    help="config1: the headline (config-1 model on the room frame); config3: the 4-D model at "
+                         "--res with t from the seed; half: quarter-pixel query + upsampling and shading")
     return ap.parse_args()
 
 
@@ -338,10 +341,91 @@ def _table1_and_half(dev, flush, stream, dpos, dnrm, steps, warmup):
     return {"table1_1080p_fp16": rows, "half_1080p_config1": half}
 
 
+def run_workload(a):
+    """One side workload on one GPU, timed like the headline: K steps after W warm-up steps,
+    L2 flushed (256 MB write) before each step, CUDA events on the launching stream."""
+    import torch
+    from paper_2602_12949_gb300 import NIVModel, upsample_shade
+    from niv_inputs import init_params
+    from niv_inputs.configs import MODEL_C1, MODEL_C3, ROOM_MIN, ROOM_MAX, RESOLUTIONS, room_gbuffer
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    W, H = RESOLUTIONS[a.res]
+    npx = W * H
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    peaks = _peaks()
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)
+    if a.workload == "config3":
+        pos, nrm, _ = room_gbuffer(W, H)
+        dp, dn = torch.from_numpy(pos).to(dev), torch.from_numpy(nrm).to(dev)
+        t = float(np.random.default_rng(0).random())  # per-frame scene parameter from the seed
+        m = NIVModel(**MODEL_C3)
+        g, _ = m.param_count()
+        m.set_params(init_params(g, m.layer_shapes(), seed=0))
+        if a.precision == "fp8":
+            m.fp8_calibrate(dp[::31].contiguous(), dn[::31].contiguous(), t=t, **kw)
+        out = torch.empty((npx, 4), dtype=torch.float32 if a.precision == "fp32" else torch.float16, device=dev)
+        step = lambda: m.query(dp, dn, out=out, precision=a.precision, t=t, image_width=W, **kw)
+        flop = 2 * (36 * 64 + 2 * 64 * 64 + 64 * 3)  # 21,376 per query
+        tensor_peak = peaks["tensor"] * (2.0 if a.precision == "fp8" else 1.0)  # FP8 dense rate = 2x BF16
+        config = {"workload": "config3-%s: 4-D model (16 levels x 2 features, T=2^19, 36-64-64-64-3) on the "
+                              "%dx%d room frame, t=%.4f" % (a.res, W, H, t), "pixels": npx, "precision": a.precision}
+        unit_per_step = npx
+    else:
+        from niv_inputs.meshes import shading_frame
+        p4, n4, a4, d4, _ = shading_frame(W, H)
+        dp, dn, da, dd = (torch.from_numpy(x).to(dev) for x in (p4, n4, a4, d4))
+        m = NIVModel(**MODEL_C1)
+        g, _ = m.param_count()
+        m.set_params(init_params(g, m.layer_shapes(), seed=0))
+        w, h = (W + 1) // 2, (H + 1) // 2
+        low = torch.empty((w * h, 4), dtype=torch.float16, device=dev)
+        rgba = torch.empty((npx, 4), dtype=torch.float16, device=dev)
+
+        def step():
+            m.query_sub(dp, dn, W, H, sub=2, out=low, precision=a.precision, **kw)
+            upsample_shade(dp, dn, da, dd, W, H, low, sub=2, out=rgba)
+        flop = 2 * (35 * 64 + 64 * 64 + 64 * 3) / 4.0  # per full-resolution pixel: a quarter of the queries
+        tensor_peak = peaks["tensor"]
+        config = {"workload": "half-%s: config-1 model queried at the pixels (2x, 2y) of the %dx%d frame with "
+                              "three inserted meshes, joint bilateral upsampling + shading to FP16 rgba"
+                              % (a.res, W, H), "pixels": npx, "precision": a.precision}
+        unit_per_step = npx
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    with ClockSampler(0) as clk:
+        for s0, e0 in evs:
+            flush.zero_()
+            s0.record(stream)
+            step()
+            e0.record(stream)
+        torch.cuda.synchronize()
+    ms = statistics.mean(s0.elapsed_time(e0) for s0, e0 in evs)
+    achieved = flop * unit_per_step / (ms * 1e-3) / 1e12
+    line = {"metric": "ms/frame and Gpixels/s, %s" % a.workload, "value": unit_per_step / (ms * 1e-3) / 1e9,
+            "unit": "Gpixels/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "ms_per_frame": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp16": "f16", "fp8": "e4m3"}[a.precision], "data": "synthetic",
+            "config": dict(config, l2="flushed between steps (256 MB write)", parallelism="single"),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": tensor_peak, "unit": "TFLOP/s",
+                         "frac": achieved / tensor_peak, "traffic": None,
+                         "peak_source": "%s bf16 burst%s" % (peaks["src"], " x 2 (FP8 dense rate)"
+                                                            if a.precision == "fp8" else "")},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    m.close()
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.workload != "config1":
+        run_workload(a)
         return
     import torch
     import torch.distributed as dist
