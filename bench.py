@@ -289,8 +289,12 @@ def _more_workloads(a, dev, flush, stream, steps=10, warmup=3):
     grid = ProbeGrid((50, 50, 50), ROOM_MIN, ROOM_MAX)
     grid.bake(room_scene(0).blob(), rays=256, seed=0)
     ms = _time_launches(lambda: grid.query(dp1, dn1, out=o1, image_width=1920), steps, warmup, flush, stream)
+    blob = room_scene(0).blob()
+    ms_rt = _time_launches(lambda: grid.query(dp1, dn1, out=o1, image_width=1920, scene_blob=blob), steps, warmup,
+                           flush, stream)
     res["probes_1080p"] = {"probes": 125000, "mb": grid.nbytes / 1e6, "ms_per_frame": ms,
-                           "gqueries_per_s": 1920 * 1080 / (ms * 1e-3) / 1e9}
+                           "gqueries_per_s": 1920 * 1080 / (ms * 1e-3) / 1e9,
+                           "rt_visibility_ms_per_frame": ms_rt}
     res.update(_table1_and_half(dev, flush, stream, dp1, dn1, steps, warmup))
     return res
 

@@ -295,6 +295,20 @@ NIV_API int niv_probe_query(const void* coef16, const int32_t* P, const float* l
                             int32_t image_width, niv_stream stream);
 
 /*
+ * The probe query with ray-traced visibility ("+ RT", Sec. 5.1 and App. A: visibility-
+ * based probe rejection replaces the cosine fall-off).  Reading: a shadow ray leaves
+ * x + 0.01 n (world units, n normalised) toward each of the 8 probes; a probe whose ray
+ * hits scene geometry more than 0.01 before reaching it gets weight 0 before the 1e-6
+ * clamp and the renormalisation.  scene, scene_len: the host scene description of
+ * niv_mc_irradiance, at scene parameter t.  Other arguments as niv_probe_query.
+ * Asynchronous.
+ */
+NIV_API int niv_probe_query_rt(const void* coef16, const int32_t* P, const float* lo, const float* hi,
+                               const float* scene, int64_t scene_len, float t, const void* pos, const void* nrm,
+                               int64_t n, int32_t dtype_in, void* out_E, int32_t dtype_out, int32_t image_width,
+                               niv_stream stream);
+
+/*
  * Largest n accepted by niv_query_host_noalloc: the number of records its fixed
  * staging area holds.
  */

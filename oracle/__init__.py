@@ -134,6 +134,9 @@ def lib():
         L.orc_sh_project.restype = None
         L.orc_probe_bake.argtypes = [vp, vp, vp, vp, ctypes.c_int, u64, u64, vp]
         L.orc_probe_query.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
+        L.orc_probe_query_rt.argtypes = [vp, vp, vp, vp, vp, d, vp, vp, i64, vp, vp]
+        L.orc_visible.argtypes = [vp, d, d, vp, vp, d]
+        L.orc_visible.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -364,3 +367,21 @@ def probe_query(coef, P, lo, hi, x4, n4):
     E = np.zeros((len(x4), 3))
     lib().orc_probe_query(_p(_f64(coef)), _p(P), _p(_f32(lo)), _p(_f32(hi)), _p(x4), _p(n4), len(x4), _p(E))
     return E
+
+
+def probe_query_rt(coef, P, lo, hi, scene_blob, x4, n4, t=0.0):
+    """Probe irradiance with ray-traced visibility ("+ RT"): (E [m][3], ambiguous [m] bool), the
+    second flagging records whose visibility decisions flip under +-1e-5 of geometry."""
+    P = np.ascontiguousarray(P, np.int32)
+    x4, n4 = _f32(x4), _f32(n4)
+    E = np.zeros((len(x4), 3))
+    amb = np.zeros(len(x4), np.uint8)
+    lib().orc_probe_query_rt(_p(_f64(coef)), _p(P), _p(_f32(lo)), _p(_f32(hi)), _p(_f32(scene_blob)), float(t),
+                             _p(x4), _p(n4), len(x4), _p(E), _p(amb))
+    return E, amb.astype(bool)
+
+
+def visible(scene_blob, o, p, t=0.0, grow=0.0, end_tol=0.01):
+    """1 when the segment o -> p is free of scene geometry (up to end_tol before p)."""
+    return int(lib().orc_visible(_p(_f32(scene_blob)), float(t), float(grow), _p(_f64(o)), _p(_f64(p)),
+                                 float(end_tol)))

@@ -79,6 +79,7 @@ typedef struct {
     const float* box;
     int ns, nb, room;
     double sph_c[64][3]; /* sphere centres after the time rotation */
+    double grow;         /* every solid thickened by this much (0 except for visibility margins) */
 } scene_t;
 
 static void scene_init(scene_t* s, const float* blob, double t)
@@ -89,6 +90,7 @@ static void scene_init(scene_t* s, const float* blob, double t)
     s->room = blob[2] != 0.0f;
     s->sph = blob + HDR;
     s->box = blob + HDR + SPH * s->ns;
+    s->grow = 0.0;
     int rot = (int)blob[3];
     for (int i = 0; i < s->ns && i < 64; ++i) {
         const float* c = s->sph + SPH * i;
@@ -120,7 +122,7 @@ static int intersect(const scene_t* s, const double* o, const double* d, hit_t* 
     h->t = INFINITY;
     for (int i = 0; i < s->ns; ++i) {
         const double* c = s->sph_c[i];
-        double r = s->sph[SPH * i + 3];
+        double r = s->sph[SPH * i + 3] + s->grow;
         double oc[3] = {o[0] - c[0], o[1] - c[1], o[2] - c[2]};
         double b = dot3(oc, d), cc = dot3(oc, oc) - r * r, disc = b * b - cc;
         if (disc < 0.0) continue;
@@ -133,7 +135,7 @@ static int intersect(const scene_t* s, const double* o, const double* d, hit_t* 
         double tn = -INFINITY, tf = INFINITY;
         int an = 0, af = 0;
         for (int k = 0; k < 3; ++k) {
-            double t1 = (bx[k] - o[k]) / d[k], t2 = (bx[3 + k] - o[k]) / d[k];
+            double t1 = ((double)bx[k] - s->grow - o[k]) / d[k], t2 = ((double)bx[3 + k] + s->grow - o[k]) / d[k];
             double lo = t1 < t2 ? t1 : t2, hi = t1 < t2 ? t2 : t1;
             if (lo > tn) { tn = lo; an = k; }
             if (hi < tf) { tf = hi; af = k; }
@@ -151,15 +153,17 @@ static int intersect(const scene_t* s, const double* o, const double* d, hit_t* 
         int wall = -1;
         for (int k = 0; k < 3; ++k) {
             double t;
-            if (d[k] > 0) t = (hi[k] - o[k]) / d[k];
-            else if (d[k] < 0) t = (lo[k] - o[k]) / d[k];
+            if (d[k] > 0) t = ((double)hi[k] - s->grow - o[k]) / d[k];
+            else if (d[k] < 0) t = ((double)lo[k] + s->grow - o[k]) / d[k];
             else continue;
             if (t < tw) { tw = t; wall = 2 * k + (d[k] > 0); }
         }
         if (wall >= 0 && tw < h->t) {
             double px = o[0] + tw * d[0], pz = o[2] + tw * d[2];
             const float* sk = s->h + 13;
-            int open = wall == 3 && sk[0] < sk[1] && px >= sk[0] && px <= sk[1] && pz >= sk[2] && pz <= sk[3];
+            const double g = s->grow;
+            int open = wall == 3 && sk[0] < sk[1] && px >= sk[0] + g && px <= sk[1] - g && pz >= sk[2] + g &&
+                       pz <= sk[3] - g;
             if (!open) { h->t = tw; h->kind = HIT_WALL; h->id = wall; }
         }
     }
@@ -363,4 +367,22 @@ int orc_mc_radiance(const float* blob, const float* x4, const float* d4, int64_t
         for (int k = 0; k < 3; ++k) out_L[3 * i + k] = acc[k] / (double)spp;
     }
     return 0;
+}
+
+/*
+ * Visibility of point p from point o through the scene at parameter t, with every solid
+ * thickened by `grow` (the room's walls and the skylight's rim moved inward): 0 when the
+ * ray o -> p hits geometry at a distance below |p - o| - end_tol, else 1.
+ */
+int orc_visible(const float* blob, double t, double grow, const double* o, const double* p, double end_tol)
+{
+    scene_t s;
+    scene_init(&s, blob, t);
+    s.grow = grow;
+    double d[3] = {p[0] - o[0], p[1] - o[1], p[2] - o[2]};
+    double dist = sqrt(dot3(d, d));
+    if (!(dist > 0.0)) return 1;
+    for (int k = 0; k < 3; ++k) d[k] /= dist;
+    hit_t h;
+    return !(intersect(&s, o, d, &h) && h.t < dist - end_tol);
 }

@@ -16,6 +16,12 @@
  *    keeps factor 1), clamped below at 1e-6, then renormalised (App. A).
  *  - Probes sit at the vertices of a regular P_x x P_y x P_z lattice spanning
  *    the box [lo, hi] (P_k >= 2).
+ *  - "+ RT" (Sec. 5.1, App. A): visibility-based rejection replaces the fall-off.
+ *    Reading: a ray from x + 0.01 n toward each probe; a probe whose ray hits the
+ *    scene more than 0.01 before reaching it gets weight 0, then the 1e-6 clamp and
+ *    the renormalisation.  The same test with every solid thickened and thinned by
+ *    1e-5 (ten times the FP32 error of these intersections in a 10 m room) flags the
+ *    records whose decision depends on rounding (rays grazing an object).
  */
 #include <math.h>
 #include <stdint.h>
@@ -23,6 +29,7 @@
 void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]);
 int orc_mc_radiance(const float* blob, const float* x4, const float* d4, int64_t m, int spp, uint64_t seed,
                     uint64_t index_base, int mode, double* out_L);
+int orc_visible(const float* blob, double t, double grow, const double* o, const double* p, double end_tol);
 
 /* real SH basis, bands 0..2, from the normalised associated Legendre definitions */
 void orc_sh9(const double* w, double* Y)
@@ -172,6 +179,63 @@ int orc_probe_query(const double* coef, const int* P, const float* lo, const flo
             wsum += w;
         }
         for (int k = 0; k < 3; ++k) E[3 * q + k] = acc[k] / wsum;
+    }
+    return 0;
+}
+
+/*
+ * Query with ray-traced visibility ("+ RT"): as orc_probe_query with the fall-off
+ * replaced by the visibility of each probe from x + 0.01 n in scene `blob` at
+ * parameter t.  ambiguous[q] (nullable) = 1 when some probe's visibility differs
+ * between the scene thickened and thinned by 1e-5.
+ */
+int orc_probe_query_rt(const double* coef, const int* P, const float* lo, const float* hi, const float* blob,
+                       double t, const float* x4, const float* n4, int64_t m, double* E, uint8_t* ambiguous)
+{
+    const double bias = 0.01, end_tol = 0.01, margin = 1e-5;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < m; ++q) {
+        const float* xq = x4 + 4 * q;
+        double nq[3] = {n4[4 * q], n4[4 * q + 1], n4[4 * q + 2]};
+        double nl = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2]);
+        for (int a = 0; a < 3; ++a) nq[a] /= nl;
+        const double o[3] = {xq[0] + bias * nq[0], xq[1] + bias * nq[1], xq[2] + bias * nq[2]};
+        int64_t base[3];
+        double f[3];
+        for (int a = 0; a < 3; ++a) {
+            double g = ((double)xq[a] - lo[a]) / ((double)hi[a] - lo[a]) * (double)(P[a] - 1);
+            if (g < 0.0) g = 0.0;
+            if (g > P[a] - 1) g = P[a] - 1;
+            int64_t i = (int64_t)floor(g);
+            if (i > P[a] - 2) i = P[a] - 2;
+            base[a] = i;
+            f[a] = g - (double)i;
+        }
+        double acc[3] = {0.0, 0.0, 0.0}, wsum = 0.0;
+        int amb = 0;
+        for (int c = 0; c < 8; ++c) {
+            int64_t ijk[3];
+            double w = 1.0;
+            for (int a = 0; a < 3; ++a) {
+                int bit = (c >> a) & 1;
+                ijk[a] = base[a] + bit;
+                w *= bit ? f[a] : 1.0 - f[a];
+            }
+            int64_t p = ijk[0] + (int64_t)P[0] * (ijk[1] + (int64_t)P[1] * ijk[2]);
+            double pp[3];
+            probe_pos(P, lo, hi, p, pp);
+            int vis = orc_visible(blob, t, 0.0, o, pp, end_tol);
+            if (ambiguous && orc_visible(blob, t, margin, o, pp, end_tol) != orc_visible(blob, t, -margin, o, pp, end_tol))
+                amb = 1;
+            if (!vis) w = 0.0;
+            if (w < 1e-6) w = 1e-6;
+            double Ep[3];
+            orc_sh_irradiance(coef + p * 27, nq, Ep);
+            for (int k = 0; k < 3; ++k) acc[k] += w * Ep[k];
+            wsum += w;
+        }
+        for (int k = 0; k < 3; ++k) E[3 * q + k] = acc[k] / wsum;
+        if (ambiguous) ambiguous[q] = (uint8_t)amb;
     }
     return 0;
 }

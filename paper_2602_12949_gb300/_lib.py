@@ -84,6 +84,8 @@ _SIGNATURES = [
     ("niv_encode", ctypes.c_int, [_VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _VP, _VP]),
     ("niv_selftest_mma", ctypes.c_int, [_I32, _VP, _VP]),
     ("niv_shade", ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
+    ("niv_probe_query_rt", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, _F, _VP, _VP, _I64, _I32, _VP, _I32, _I32,
+                                          _VP]),
     ("niv_query_sub", ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _I32, _I32, ctypes.POINTER(QueryParams), _VP, _I32,
                                      _I32, _VP]),
     ("niv_upsample_shade", ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _I32, _I32, _VP, _I32, _I32,

@@ -533,9 +533,10 @@ int niv_probe_bake(const float* scene, int64_t scene_len, const int32_t* P, cons
                                  (cudaStream_t)stream);
 }
 
-int niv_probe_query(const void* coef16, const int32_t* P, const float* lo, const float* hi, const void* pos,
-                    const void* nrm, int64_t n, int32_t dtype_in, void* out_E, int32_t dtype_out, int32_t image_width,
-                    niv_stream stream) {
+namespace {
+int probe_query_common(const void* coef16, const int32_t* P, const float* lo, const float* hi, const float* scene,
+                       int64_t scene_len, float t, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+                       void* out_E, int32_t dtype_out, int32_t image_width, niv_stream stream) {
     if (!coef16 || !P || !lo || !hi) return niv_fail(NIV_ERR_ARG, "NULL argument");
     if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
     if (n == 0) return NIV_OK;
@@ -557,7 +558,23 @@ int niv_probe_query(const void* coef16, const int32_t* P, const float* lo, const
     io.image_width = image_width;
     io.in_f16 = dtype_in == NIV_F16;
     io.out_f16 = dtype_out == NIV_F16;
-    return niv_launch_probe_query(coef16, P, lo, hi, io, (cudaStream_t)stream);
+    return niv_launch_probe_query(coef16, P, lo, hi, io, scene, scene_len, t, (cudaStream_t)stream);
+}
+}  // namespace
+
+int niv_probe_query(const void* coef16, const int32_t* P, const float* lo, const float* hi, const void* pos,
+                    const void* nrm, int64_t n, int32_t dtype_in, void* out_E, int32_t dtype_out, int32_t image_width,
+                    niv_stream stream) {
+    return probe_query_common(coef16, P, lo, hi, nullptr, 0, 0.0f, pos, nrm, n, dtype_in, out_E, dtype_out,
+                              image_width, stream);
+}
+
+int niv_probe_query_rt(const void* coef16, const int32_t* P, const float* lo, const float* hi, const float* scene,
+                       int64_t scene_len, float t, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+                       void* out_E, int32_t dtype_out, int32_t image_width, niv_stream stream) {
+    if (!scene) return niv_fail(NIV_ERR_ARG, "scene is NULL");
+    return probe_query_common(coef16, P, lo, hi, scene, scene_len, t, pos, nrm, n, dtype_in, out_E, dtype_out,
+                              image_width, stream);
 }
 
 int niv_compact_targets(const float* x4, const float* n4, const float* t, const double* E, const uint8_t* keep,

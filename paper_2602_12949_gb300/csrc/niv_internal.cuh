@@ -136,8 +136,9 @@ int niv_launch_mc(const float* blob, int64_t blob_len, const float* x4, const fl
                   int spp, uint64_t seed, uint64_t index_base, int mode, double* outE, uint8_t* keep, cudaStream_t s);
 int niv_launch_probe_bake(const float* blob, int64_t blob_len, const int* P, const float* lo, const float* hi, int rays,
                           uint64_t seed, uint64_t index_base, double* out64, __half* out16, cudaStream_t s);
+// scene (host, nullable): "+RT" visibility rays against it at scene parameter t.
 int niv_launch_probe_query(const void* coef16, const int* P, const float* lo, const float* hi, const IoArgs& io,
-                           cudaStream_t s);
+                           const float* scene, int64_t scene_len, float t, cudaStream_t s);
 int niv_launch_compact(const float* x4, const float* n4, const float* t, const double* E, const uint8_t* keep, int64_t m,
                        float* ox4, float* on4, float* ot, float* otarget, int64_t* count_dev, int* scratch,
                        cudaStream_t s);

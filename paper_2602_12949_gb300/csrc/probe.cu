@@ -6,7 +6,14 @@
 // irradiance E(n) = sum_l A_l sum_m L_lm Y_lm(n) with A = (pi, 2 pi / 3, pi / 4)
 // (Ramamoorthi & Hanrahan 2001).  Coefficients are FP16, 27 per probe padded to 28
 // (56 bytes, so a probe is seven 8-byte loads); arithmetic is FP32.
+//
+// "+RT" (Sec. 5.1, App. A): visibility-based probe rejection by ray tracing replaces the
+// cosine fall-off.  Reading: a shadow ray from x + 0.01 n (world units) toward each probe;
+// the probe is rejected (weight 0, then the 1e-6 clamp) when the ray hits scene geometry
+// more than 0.01 short of the probe.  The scene is the analytic one of the training
+// targets (scene.cuh), at scene parameter t.
 #include "niv_internal.cuh"
+#include "scene.cuh"
 
 namespace {
 
@@ -29,8 +36,20 @@ __device__ __forceinline__ float sh_irr(const float* c, float3 n, int ch) {
                  c20 * c[18 + ch] * (3.0f * z * z - 1.0f) + c22 * c[24 + ch] * (x * x - y * y));
 }
 
+constexpr float kRayBias = 0.01f;  // shadow-ray origin offset along n
+constexpr float kRayEnd = 0.01f;   // hits this close to the probe do not reject it
+
+template <bool VIS>
 __global__ void __launch_bounds__(128) probe_query_kernel(const uint2* __restrict__ coef, ProbeArgs pa, IoArgs io,
-                                                          int64_t n_tiles) {
+                                                          int64_t n_tiles, SceneArg scene, float t) {
+    __shared__ float s_scene[VIS ? kHdr + kSph * kMaxObjects : 1];
+    SceneView S;
+    if (VIS) {
+        const int len = kHdr + kSph * ((int)scene.v[0] + (int)scene.v[1]);
+        for (int k = threadIdx.x; k < len; k += blockDim.x) s_scene[k] = scene.v[k];
+        __syncthreads();
+        S.init(s_scene, t);
+    }
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t r = niv_record_of(tile, threadIdx.x, io.n, io.image_width);
         if (r >= io.n) continue;
@@ -63,9 +82,23 @@ __global__ void __launch_bounds__(128) probe_query_kernel(const uint2* __restric
             const float dx = pa.lo[0] + pa.cell[0] * ijk[0] - xs[0];
             const float dy = pa.lo[1] + pa.cell[1] * ijk[1] - xs[1];
             const float dz = pa.lo[2] + pa.cell[2] * ijk[2] - xs[2];
-            const float dl = sqrtf(dx * dx + dy * dy + dz * dz);
-            const float fall = dl > 0.0f ? fmaxf((dx * n.x + dy * n.y + dz * n.z) / dl, 0.0f) : 1.0f;
-            w = fmaxf(w * fall, 1e-6f);
+            if (VIS) {
+                const float3 o = make_float3(xs[0] + kRayBias * n.x, xs[1] + kRayBias * n.y, xs[2] + kRayBias * n.z);
+                const float3 dv = make_float3(pa.lo[0] + pa.cell[0] * ijk[0] - o.x, pa.lo[1] + pa.cell[1] * ijk[1] - o.y,
+                                              pa.lo[2] + pa.cell[2] * ijk[2] - o.z);
+                const float dist = sqrtf(dot3(dv, dv));
+                bool visible = true;
+                if (dist > 0.0f) {
+                    Hit h;
+                    const float3 d = make_float3(dv.x / dist, dv.y / dist, dv.z / dist);
+                    visible = !(S.intersect(o, d, h) && h.t < dist - kRayEnd);
+                }
+                w = fmaxf(visible ? w : 0.0f, 1e-6f);
+            } else {
+                const float dl = sqrtf(dx * dx + dy * dy + dz * dz);
+                const float fall = dl > 0.0f ? fmaxf((dx * n.x + dy * n.y + dz * n.z) / dl, 0.0f) : 1.0f;
+                w = fmaxf(w * fall, 1e-6f);
+            }
             float cf[28];
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
@@ -89,7 +122,10 @@ __global__ void __launch_bounds__(128) probe_query_kernel(const uint2* __restric
 }  // namespace
 
 int niv_launch_probe_query(const void* coef16, const int* P, const float* lo, const float* hi, const IoArgs& io,
-                           cudaStream_t s) {
+                           const float* scene, int64_t scene_len, float t, cudaStream_t s) {
+    SceneArg arg;
+    if (scene && !niv_scene_arg(scene, scene_len, arg))
+        return niv_fail(NIV_ERR_ARG, "scene description invalid (at most 56 objects, length as its header says)");
     ProbeArgs pa;
     for (int a = 0; a < 3; ++a) {
         pa.P[a] = P[a];
@@ -104,7 +140,10 @@ int niv_launch_probe_query(const void* coef16, const int* P, const float* lo, co
     const int64_t tiles = niv_tile_count_host(io.n, io.image_width);
     const int64_t cap = (int64_t)sms * 16;
     const int64_t blocks = tiles < cap ? tiles : cap;
-    probe_query_kernel<<<(unsigned)blocks, 128, 0, s>>>((const uint2*)coef16, pa, io, tiles);
+    if (scene)
+        probe_query_kernel<true><<<(unsigned)blocks, 128, 0, s>>>((const uint2*)coef16, pa, io, tiles, arg, t);
+    else
+        probe_query_kernel<false><<<(unsigned)blocks, 128, 0, s>>>((const uint2*)coef16, pa, io, tiles, arg, t);
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }

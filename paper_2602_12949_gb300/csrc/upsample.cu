@@ -116,7 +116,10 @@ __device__ __forceinline__ float4 h4(uint2 r) {
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
-__global__ void __launch_bounds__(kQW * kQH) upsample2_staged_kernel(UpArgs a) {
+#ifndef NIV_UP_MINB
+#define NIV_UP_MINB 4
+#endif
+__global__ void __launch_bounds__(kQW * kQH, NIV_UP_MINB) upsample2_staged_kernel(UpArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     StagedTile& t = *reinterpret_cast<StagedTile*>(smem_raw);
     const int tid = threadIdx.x;
@@ -126,18 +129,24 @@ __global__ void __launch_bounds__(kQW * kQH) upsample2_staged_kernel(UpArgs a) {
     const uint2* galb = reinterpret_cast<const uint2*>(a.alb);
     const uint2* gdir = reinterpret_cast<const uint2*>(a.dir);
     const uint2* gE = reinterpret_cast<const uint2*>(a.E);
-    // rows 0..16 of pos / nrm and rows 0..15 of albedo / direct, in 16-byte chunks (2 pixels)
-    for (int c = tid; c < (kTH + 1) * (kTW / 2) * 4; c += kQW * kQH) {
-        const int buf = c / ((kTH + 1) * (kTW / 2)), rc = c % ((kTH + 1) * (kTW / 2));
-        const int row = rc / (kTW / 2), col = 2 * (rc % (kTW / 2));
-        if (buf >= 2 && row == kTH) continue;
-        const int X = X0 + col, Y = Y0 + row;
-        const bool ok = X < a.W && Y < a.H;  // W is even: both pixels of the chunk are inside
-        const int64_t g = ok ? (int64_t)Y * a.W + X : 0;
-        const uint2* src = buf == 0 ? gpos : buf == 1 ? gnrm : buf == 2 ? galb : gdir;
-        uint2* dst = buf == 0 ? &t.pos[row][col] : buf == 1 ? &t.nrm[row][col] : buf == 2 ? &t.alb[row][col]
-                                                                                         : &t.dir[row][col];
-        cp_async16(dst, src + g, ok);
+    // rows 0..16 of pos / nrm and rows 0..15 of albedo / direct in 16-byte chunks (2 pixels):
+    // thread (column pair tid % 32, row tid / 32) copies rows r, r + 8 (and 16 for r = 0)
+    {
+        const int cc = 2 * (tid % kQW), r0 = tid / kQW, X = X0 + cc;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int row = r0 + kQH * k;
+            if (row > kTH) break;
+            const int Y = Y0 + row;
+            const bool ok = X < a.W && Y < a.H;  // W is even: both pixels of the chunk are inside
+            const int64_t g = ok ? (int64_t)Y * a.W + X : 0;
+            cp_async16(&t.pos[row][cc], gpos + g, ok);
+            cp_async16(&t.nrm[row][cc], gnrm + g, ok);
+            if (row < kTH) {
+                cp_async16(&t.alb[row][cc], galb + g, ok);
+                cp_async16(&t.dir[row][cc], gdir + g, ok);
+            }
+        }
     }
     // pixel column 64 of pos / nrm (rows 0..16)
     if (tid < 2 * (kTH + 1)) {

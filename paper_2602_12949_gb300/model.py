@@ -352,16 +352,22 @@ class ProbeGrid:
                                    ctypes.c_void_p(self.coef16.data_ptr()), _stream(stream)))
         return c64
 
-    def query(self, pos, nrm, out=None, image_width=0, out_dtype=None, stream=None):
+    def query(self, pos, nrm, out=None, image_width=0, out_dtype=None, scene_blob=None, t=0.0, stream=None):
+        """Probe irradiance at device records; with scene_blob, probes are rejected by
+        ray-traced visibility ("+ RT") instead of the cosine fall-off."""
         _check_records(pos, "pos")
         _check_records(nrm, "nrm")
         if out is None:
             out = torch.empty(pos.shape, dtype=out_dtype or pos.dtype, device=pos.device)
-        check(lib().niv_probe_query(ctypes.c_void_p(self.coef16.data_ptr()), ctypes.c_void_p(self.P.ctypes.data),
-                                    ctypes.c_void_p(self.lo.ctypes.data), ctypes.c_void_p(self.hi.ctypes.data),
-                                    ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()), pos.shape[0],
-                                    _rec_dtype(pos), ctypes.c_void_p(out.data_ptr()), _rec_dtype(out), int(image_width),
-                                    _stream(stream)))
+        grid = (ctypes.c_void_p(self.coef16.data_ptr()), ctypes.c_void_p(self.P.ctypes.data),
+                ctypes.c_void_p(self.lo.ctypes.data), ctypes.c_void_p(self.hi.ctypes.data))
+        recs = (ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()), pos.shape[0], _rec_dtype(pos),
+                ctypes.c_void_p(out.data_ptr()), _rec_dtype(out), int(image_width), _stream(stream))
+        if scene_blob is None:
+            check(lib().niv_probe_query(*grid, *recs))
+        else:
+            blob = np.ascontiguousarray(scene_blob, dtype=np.float32)
+            check(lib().niv_probe_query_rt(*grid, ctypes.c_void_p(blob.ctypes.data), blob.size, float(t), *recs))
         return out
 
 

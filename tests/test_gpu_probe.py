@@ -58,6 +58,41 @@ def test_probe_query_matches_oracle(niv):
     assert err <= 1e-5
 
 
+@pytest.mark.parametrize("t", [0.0, 0.37])
+def test_probe_query_rt_matches_oracle(niv, t):
+    """+ RT: visibility rays against the room (FP32 on the GPU, FP64 in the oracle).  Records
+    whose visibility decisions flip under +-1e-5 of geometry (grazing rays) may differ; all
+    others agree to 1e-5 of the frame's max E, and the flagged ones stay rare."""
+    rng = np.random.default_rng(1)
+    P = np.array([11, 9, 12], np.int32)
+    lo, hi = np.array(ROOM_MIN, np.float32), np.array(ROOM_MAX, np.float32)
+    g = niv.ProbeGrid(P, lo, hi)
+    coef = rng.normal(0.0, 0.3, (int(np.prod(P)), 28))
+    coef[:, 0] += 3.0
+    coef[:, 27] = 0.0
+    g.coef16.copy_(torch.from_numpy(coef).half())
+    from niv_inputs.configs import room_gbuffer
+    gp, gn, _ = room_gbuffer(320, 180)
+    vp, vn = uniform_queries(20000 + 9, seed=3, lo=ROOM_MIN, hi=ROOM_MAX)
+    pos = np.concatenate([gp.astype(np.float32), vp])
+    nrm = np.concatenate([gn.astype(np.float32), vn])
+    scene = room_scene(0)
+    scene.rot_sphere, scene.rot_axis_point = 0, (0.0, 0.0, 0.0)  # exercise the time rotation too
+    blob = scene.blob()
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    got = g.query(d(pos), d(nrm), out_dtype=torch.float32, scene_blob=blob, t=t)[:, :3].cpu().numpy()
+    plain = g.query(d(pos), d(nrm), out_dtype=torch.float32)[:, :3].cpu().numpy()
+    c16 = coef.astype(np.float16).astype(np.float64)[:, :27].reshape(-1, 9, 3)
+    ref, amb = oracle.probe_query_rt(c16, P, lo, hi, blob, pos, nrm, t=t)
+    err = np.abs(got - ref).max(axis=1) / np.abs(ref).max()
+    print("+RT: %d of %d ambiguous; max err normalised %.3g (clear records), %.3g (all); differs from "
+          "fall-off on %.1f%%" % (amb.sum(), len(pos), err[~amb].max(), err.max(),
+                                  100 * np.mean(np.abs(got - plain).max(axis=1) > 1e-3 * np.abs(ref).max())))
+    assert err[~amb].max() <= 1e-5
+    assert amb.mean() <= 0.005
+    assert np.mean(np.abs(got - plain).max(axis=1) > 1e-3 * np.abs(ref).max()) > 0.05  # visibility is applied
+
+
 def test_probe_furnace(niv):
     """Furnace (walls emit 1, albedo 0.5): indirect radiance is 1 everywhere, so every probe gives E = pi."""
     g = niv.ProbeGrid((4, 4, 4), (-4.0, -4.0, -4.0), (4.0, 4.0, 4.0))
