@@ -46,9 +46,10 @@ def _args():
     ap.add_argument("--res", default="1080p", choices=["1080p", "4k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison and error checks")
-    ap.add_argument("--workload", default="config1", choices=["config1", "config3", "half"],
+    ap.add_argument("--workload", default="config1", choices=["config1", "config3", "half", "sweep"],
                     help="config1: the headline (config-1 model on the room frame); config3: the 4-D model at "
-                         "--res with t from the seed; half: quarter-pixel query + upsampling and shading")
+                         "--res with t from the seed; half: quarter-pixel query + upsampling and shading; "
+                         "sweep: memory-error trade-off (hash table sizes against probes of equal memory)")
     return ap.parse_args()
 
 
@@ -345,10 +346,35 @@ def _table1_and_half(dev, flush, stream, dpos, dnrm, steps, warmup):
     return {"table1_1080p_fp16": rows, "half_1080p_config1": half}
 
 
+def run_sweep(a):
+    """Memory-error trade-off on the seeded room: NIV (config-1 shape) trained at hash table
+    sizes 2^13 .. 2^19 against the SH probe grid of the same memory, with and without
+    ray-traced visibility; MSE on 2^14 held-out samples with 4096-spp references."""
+    import torch
+    from paper_2602_12949_gb300 import fitting
+    from niv_inputs import room_scene
+    from niv_inputs.configs import MODEL_C1
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    rows = fitting.memory_error_sweep(room_scene(0), [13, 15, 17, 19], MODEL_C1, steps=2000)
+    ref = next(r for r in rows if r["log2_T"] == 17)
+    line = {"metric": "held-out MSE, NIV vs SH probes of equal memory (hash table size sweep)",
+            "value": ref["probe_mse"] / ref["niv_mse"], "unit": "x (probe MSE / NIV MSE at T=2^17)",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "f16",
+            "config": {"workload": "room scene seed 0; NIV 16 levels x 2 features, base 16, growth 1.38, "
+                                   "35-64-64-3; 2000 Adam steps, batch 2^16, 128-spp targets; probes baked "
+                                   "with 1024 rays"},
+            "rows": rows, "seconds": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def run_workload(a):
     """One side workload on one GPU, timed like the headline: K steps after W warm-up steps,
     L2 flushed (256 MB write) before each step, CUDA events on the launching stream."""
     import torch
+    if a.workload == "sweep":
+        run_sweep(a)
+        return
     from paper_2602_12949_gb300 import NIVModel, upsample_shade
     from niv_inputs import init_params
     from niv_inputs.configs import MODEL_C1, MODEL_C3, ROOM_MIN, ROOM_MAX, RESOLUTIONS, room_gbuffer

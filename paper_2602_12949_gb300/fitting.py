@@ -77,3 +77,42 @@ def errors(pred, ref):
     mse = torch.mean((p - r) ** 2).item()
     rel = torch.mean((p - r) ** 2 / (r * r + 0.01)).item()
     return mse, rel
+
+
+def memory_error_sweep(scene, log2_Ts, shape, steps=2000, batch=1 << 16, pool=1 << 18, spp=128, reuse=2,
+                       held=(1 << 14, 4096), probe_rays=1024, seed=1, aabb_min=(-5.0, -5.0, -5.0),
+                       aabb_max=(5.0, 5.0, 5.0), device="cuda"):
+    """Memory-error trade-off (Sec. 4.1's hash-table-size study and Sec. 5.1's comparison with
+    probes): for every hash table size 2^log2_T, NIV of the given shape is trained on `scene`,
+    and the SH probe grid with the largest cubic lattice that fits the same memory is baked;
+    the probes are queried with the cosine fall-off and with ray-traced visibility ("+ RT").
+    Returns one row per size with the FP16 memory and the (MSE, relative MSE) of each on the
+    same held-out samples (Monte Carlo references at held[1] spp)."""
+    import torch
+    from niv_inputs import init_params
+    from .model import NIVModel, ProbeGrid
+    hx, hn, hE, _ = held_out(scene, held[0], held[1], seed=99, device=device)
+    rows = []
+    for lt in log2_Ts:
+        m = NIVModel(**dict(shape, log2_T=int(lt)))
+        g, nm = m.param_count()
+        nbytes = 2 * (g + nm)  # FP16 parameters
+        m.set_params(init_params(g, m.layer_shapes(), seed=0))
+        train(m, scene, steps=steps, batch=batch, pool=pool, spp=spp, reuse=reuse, seed=seed, aabb_min=aabb_min,
+              aabb_max=aabb_max, device=device)
+        niv = errors(m.query(hx, hn, precision="fp16", out_dtype=torch.float32, aabb_min=aabb_min,
+                             aabb_max=aabb_max), hE)
+        m.close()
+        P = int((nbytes / 54.0) ** (1.0 / 3.0))
+        while (P + 1) ** 3 * 54 <= nbytes:
+            P += 1
+        while P ** 3 * 54 > nbytes:
+            P -= 1
+        grid = ProbeGrid((P,) * 3, aabb_min, aabb_max, device=device)
+        grid.bake(scene.blob(), rays=probe_rays, seed=3)
+        probe = errors(grid.query(hx, hn, out_dtype=torch.float32), hE)
+        probe_rt = errors(grid.query(hx, hn, out_dtype=torch.float32, scene_blob=scene.blob()), hE)
+        rows.append({"log2_T": int(lt), "mb": nbytes / 1e6, "niv_mse": niv[0], "niv_rel": niv[1],
+                     "probes_per_axis": P, "probe_mb": grid.nbytes / 1e6, "probe_mse": probe[0],
+                     "probe_rel": probe[1], "probe_rt_mse": probe_rt[0], "probe_rt_rel": probe_rt[1]})
+    return rows
