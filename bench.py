@@ -279,6 +279,20 @@ def _more_workloads(a, dev, flush, stream, steps=10, warmup=3):
     ms_s = _time_launches(lambda: shade(da4, dd4, out16, out=rgba), steps, warmup, flush, stream)
     r["fp16_query_then_shade"] = {"ms_per_frame": ms_q + ms_s, "shade_ms": ms_s,
                                   "shade_gb_per_s": 32 * npx / (ms_s * 1e-3) / 1e9}
+    # dynamic ambient occlusion against the three meshes (Sec. 4.4), scaling E in place
+    from paper_2602_12949_gb300 import DynamicGeometry
+    from niv_inputs.meshes import dynamic_objects
+    verts, tris, _, _ = dynamic_objects(0)
+    tri9 = verts[tris].reshape(-1, 9).astype(np.float32)
+    t0 = time.perf_counter()
+    dyn = DynamicGeometry(tri9)
+    build_ms = 1e3 * (time.perf_counter() - t0)
+    ao = torch.empty(npx, dtype=torch.float32, device=dev)
+    ms_ao = _time_launches(lambda: dyn.ao(dp4, dn4, rays=8, radius=0.5, out=ao, E=out16), steps, warmup, flush,
+                           stream)
+    r["dynamic_ao"] = {"triangles": int(len(tri9)), "nodes": dyn.node_count, "rays": 8, "radius": 0.5,
+                       "ms_per_frame": ms_ao, "host_build_and_upload_ms": build_ms}
+    dyn.close()
     res["config4_4k"] = r
     m4.close()
     # the non-neural path beside it: SH probe grid with the config-1 model's memory, 1080p frame

@@ -369,6 +369,32 @@ NIV_API int niv_shade(const void* albedo, const void* direct, const void* E, int
               niv_stream stream);
 
 /*
+ * Dynamic ambient occlusion (Sec. 4.4 "Dynamic Ambient Occlusion": the hemisphere
+ * obstruction at the shading point by the dynamic geometry only, which the cached
+ * irradiance does not know; it darkens the dynamic objects themselves and the static
+ * surfaces near them).  The paper gives no formula; this library's reading:
+ *   from o = x + 0.01 n (world units, n normalised), `rays` cosine-distributed
+ *   directions about n, direction j drawn from Philox4x32-10 (as niv_mc_irradiance) on
+ *   counter (record lo, record hi, j, 0xA0) with key (seed lo, seed hi); a ray is
+ *   blocked when it meets a dynamic triangle at 0 < t <= radius;
+ *   AO = 1 - blocked / rays, and the irradiance is scaled E <- AO E before shading.
+ *
+ * niv_dyn_create takes the frame's dynamic triangles (host float32 [n_tris][9]: three
+ * world-space vertices each), builds a bounding-volume hierarchy over them on the host
+ * and uploads it to the current device; niv_dyn_destroy frees it.  niv_dyn_ao runs the
+ * pass for n records (pos, nrm: device [n][4] of dtype_in): out_ao (device float32 [n],
+ * nullable) receives AO, and E_inout (device [n][4] of dtype_E, nullable, e.g. the
+ * output of niv_query) is scaled in place.  rays in 1..1024, radius > 0.  Asynchronous.
+ */
+typedef struct niv_dyn* niv_dyn_handle;
+NIV_API int niv_dyn_create(const float* tris, int64_t n_tris, niv_dyn_handle* out);
+NIV_API int niv_dyn_destroy(niv_dyn_handle d);
+/* Number of hierarchy nodes (diagnostics). */
+NIV_API int64_t niv_dyn_node_count(niv_dyn_handle d);
+NIV_API int niv_dyn_ao(niv_dyn_handle d, const void* pos, const void* nrm, int64_t n, int32_t dtype_in, int32_t rays,
+                       float radius, uint64_t seed, float* out_ao, void* E_inout, int32_t dtype_E, niv_stream stream);
+
+/*
  * Half-resolution rendering (Sec. 4.4 "Half-resolution Rendering"; Table 1, column
  * "half": a quarter of the pixels queried, the full-size albedo buffer kept).
  *

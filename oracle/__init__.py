@@ -17,7 +17,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["niv_oracle.c", "oracle_mc.c", "oracle_sh.c"]
+_SOURCES = ["niv_oracle.c", "oracle_mc.c", "oracle_sh.c", "oracle_ao.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -137,6 +137,7 @@ def lib():
         L.orc_probe_query_rt.argtypes = [vp, vp, vp, vp, vp, d, vp, vp, i64, vp, vp]
         L.orc_visible.argtypes = [vp, d, d, vp, vp, d]
         L.orc_visible.restype = ctypes.c_int
+        L.orc_dyn_ao.argtypes = [vp, i64, vp, vp, i64, ctypes.c_int, d, u64, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -385,3 +386,17 @@ def visible(scene_blob, o, p, t=0.0, grow=0.0, end_tol=0.01):
     """1 when the segment o -> p is free of scene geometry (up to end_tol before p)."""
     return int(lib().orc_visible(_p(_f32(scene_blob)), float(t), float(grow), _p(_f64(o)), _p(_f64(p)),
                                  float(end_tol)))
+
+
+def dyn_ao(tri9, x4, n4, rays, radius, seed=0):
+    """Dynamic ambient occlusion: (AO [m], blocked ray counts [m], ambiguous [m] bool) for
+    records x4, n4 against triangles tri9 ([T][9] world-space vertices)."""
+    tri9 = _f32(np.asarray(tri9).reshape(-1, 9))
+    x4, n4 = _f32(x4), _f32(n4)
+    m = len(x4)
+    ao = np.zeros(m)
+    blocked = np.zeros(m, np.int32)
+    amb = np.zeros(m, np.uint8)
+    lib().orc_dyn_ao(_p(tri9), len(tri9), _p(x4), _p(n4), m, int(rays), float(radius), int(seed), _p(ao),
+                     _p(blocked), _p(amb))
+    return ao, blocked, amb.astype(bool)

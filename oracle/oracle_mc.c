@@ -386,3 +386,6 @@ int orc_visible(const float* blob, double t, double grow, const double* o, const
     hit_t h;
     return !(intersect(&s, o, d, &h) && h.t < dist - end_tol);
 }
+
+/* Cosine-distributed direction about unit n from two uniform numbers (for the other oracle files). */
+void orc_cosine_dir(const double* n, double u1, double u2, double* w) { cosine_dir(n, u1, u2, w); }

@@ -4,7 +4,9 @@
 all the work; this package marshals torch tensors into it.
 """
 from ._lib import lib, NivError, LIB_PATH
-from .model import NIVModel, ProbeGrid, shade, upsample_shade, sync_status, mc_irradiance, compact_targets, PRECISIONS
+from .model import (NIVModel, ProbeGrid, DynamicGeometry, shade, upsample_shade, sync_status, mc_irradiance,
+                    compact_targets, PRECISIONS)
 
-__all__ = ["lib", "NivError", "LIB_PATH", "NIVModel", "ProbeGrid", "shade", "upsample_shade", "sync_status",
+__all__ = ["lib", "NivError", "LIB_PATH", "NIVModel", "ProbeGrid", "DynamicGeometry", "shade", "upsample_shade",
+           "sync_status",
            "mc_irradiance", "compact_targets", "PRECISIONS"]

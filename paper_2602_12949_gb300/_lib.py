@@ -84,6 +84,10 @@ _SIGNATURES = [
     ("niv_encode", ctypes.c_int, [_VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _VP, _VP]),
     ("niv_selftest_mma", ctypes.c_int, [_I32, _VP, _VP]),
     ("niv_shade", ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
+    ("niv_dyn_create", ctypes.c_int, [_VP, _I64, ctypes.POINTER(_VP)]),
+    ("niv_dyn_destroy", ctypes.c_int, [_VP]),
+    ("niv_dyn_node_count", _I64, [_VP]),
+    ("niv_dyn_ao", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, _I32, _F, _U64, _VP, _VP, _I32, _VP]),
     ("niv_probe_query_rt", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, _F, _VP, _VP, _I64, _I32, _VP, _I32, _I32,
                                           _VP]),
     ("niv_query_sub", ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _I32, _I32, ctypes.POINTER(QueryParams), _VP, _I32,

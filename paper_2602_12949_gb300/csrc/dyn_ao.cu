@@ -1,0 +1,283 @@
+// Dynamic ambient occlusion (Sec. 4.4): the hemisphere obstruction at the shading point by
+// the dynamic (inserted) geometry only, which NIV does not know about; it darkens the
+// dynamic objects themselves (self-occlusion) and the static surfaces next to them.
+//
+// Reading (the paper gives no formula): from o = x + 0.01 n (world units, n normalised)
+// K cosine-distributed directions about n, drawn from Philox4x32-10 on counter
+// (record lo, record hi, ray j, 0xA0) with key (seed lo, seed hi); a ray is blocked when
+// it hits a dynamic triangle at 0 < t <= R (Moeller-Trumbore).  AO = 1 - blocked / K, and
+// the irradiance is scaled, E <- AO E, before shading.
+//
+// The triangles (world space, as posed for the frame) are put into a bounding-volume
+// hierarchy on the host: median split of the centroids along the widest axis, at most 4
+// triangles per leaf, nodes in depth-first order (left child next to its parent), bounds
+// padded by 1e-5 of the scene's extent.  One thread per record traverses it with a stack
+// (any hit ends the ray); records whose ray origin lies farther than R from the geometry's
+// bounds skip the rays (AO = 1).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "niv_internal.cuh"
+#include "sampling.cuh"
+
+struct niv_dyn {
+    int device;
+    int64_t n_tris, n_nodes;
+    float4* nodes;  // per node: (lo.xyz, a), (hi.xyz, b); leaf: a = first triangle, b = count; inner: a = right child, b = 0
+    float4* tris;   // per triangle: v0, e1 = v1 - v0, e2 = v2 - v0
+    float lo[3], hi[3];
+};
+
+namespace {
+
+struct HostNode {
+    float lo[3], hi[3];
+    int32_t a, b;
+};
+
+struct Builder {
+    const float* tri;  // [T][9]
+    std::vector<float> cen;
+    std::vector<int32_t> order;
+    std::vector<HostNode> nodes;
+    float pad;
+
+    int32_t build(int32_t b, int32_t e, int depth) {
+        const int32_t me = (int32_t)nodes.size();
+        nodes.push_back(HostNode());
+        HostNode nd;
+        float clo[3], chi[3];
+        for (int k = 0; k < 3; ++k) {
+            nd.lo[k] = clo[k] = INFINITY;
+            nd.hi[k] = chi[k] = -INFINITY;
+        }
+        for (int32_t i = b; i < e; ++i) {
+            const float* t = tri + 9 * (int64_t)order[i];
+            for (int v = 0; v < 3; ++v)
+                for (int k = 0; k < 3; ++k) {
+                    nd.lo[k] = std::min(nd.lo[k], t[3 * v + k]);
+                    nd.hi[k] = std::max(nd.hi[k], t[3 * v + k]);
+                }
+            for (int k = 0; k < 3; ++k) {
+                clo[k] = std::min(clo[k], cen[3 * (int64_t)order[i] + k]);
+                chi[k] = std::max(chi[k], cen[3 * (int64_t)order[i] + k]);
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            nd.lo[k] -= pad;
+            nd.hi[k] += pad;
+        }
+        int axis = 0;
+        for (int k = 1; k < 3; ++k)
+            if (chi[k] - clo[k] > chi[axis] - clo[axis]) axis = k;
+        if (e - b <= 4 || !(chi[axis] > clo[axis]) || depth >= 60) {
+            nd.a = b;
+            nd.b = e - b;
+            nodes[me] = nd;
+            return me;
+        }
+        const int32_t mid = b + (e - b) / 2;
+        std::nth_element(order.begin() + b, order.begin() + mid, order.begin() + e, [&](int32_t x, int32_t y) {
+            return cen[3 * (int64_t)x + axis] < cen[3 * (int64_t)y + axis];
+        });
+        build(b, mid, depth + 1);
+        nd.a = build(mid, e, depth + 1);
+        nd.b = 0;
+        nodes[me] = nd;
+        return me;
+    }
+};
+
+constexpr int kStack = 64;
+constexpr float kRayBias = 0.01f;
+
+// Slab test of the ray o + t d, t in [0, tmax], against a node box (inv: finite reciprocals of d).
+__device__ __forceinline__ bool box_hit(const float4& lo, const float4& hi, float3 o, float3 inv, float tmax) {
+    const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
+    const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
+    const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    return tn <= tf;
+}
+
+// Moeller-Trumbore: hit at 0 < t <= tmax inside the triangle (v0, e1, e2).
+__device__ __forceinline__ bool tri_hit(const float4& v0, const float4& e1, const float4& e2, float3 o, float3 d,
+                                        float tmax) {
+    const float px = d.y * e2.z - d.z * e2.y, py = d.z * e2.x - d.x * e2.z, pz = d.x * e2.y - d.y * e2.x;
+    const float det = e1.x * px + e1.y * py + e1.z * pz;
+    if (det == 0.0f) return false;
+    const float inv = 1.0f / det;
+    const float sx = o.x - v0.x, sy = o.y - v0.y, sz = o.z - v0.z;
+    const float u = (sx * px + sy * py + sz * pz) * inv;
+    if (u < 0.0f || u > 1.0f) return false;
+    const float qx = sy * e1.z - sz * e1.y, qy = sz * e1.x - sx * e1.z, qz = sx * e1.y - sy * e1.x;
+    const float v = (d.x * qx + d.y * qy + d.z * qz) * inv;
+    if (v < 0.0f || u + v > 1.0f) return false;
+    const float t = (e2.x * qx + e2.y * qy + e2.z * qz) * inv;
+    return t > 0.0f && t <= tmax;
+}
+
+__device__ bool any_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, float3 o, float3 d,
+                        float tmax) {
+    const float3 inv = make_float3(1.0f / (fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x)),
+                                   1.0f / (fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y)),
+                                   1.0f / (fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z)));
+    int stack[kStack];
+    int sp = 0, node = 0;
+    while (true) {
+        const float4 lo = __ldg(nodes + 2 * node), hi = __ldg(nodes + 2 * node + 1);
+        if (box_hit(lo, hi, o, inv, tmax)) {
+            const int a = __float_as_int(lo.w), b = __float_as_int(hi.w);
+            if (b > 0) {
+                for (int i = a; i < a + b; ++i)
+                    if (tri_hit(__ldg(tris + 3 * i), __ldg(tris + 3 * i + 1), __ldg(tris + 3 * i + 2), o, d, tmax))
+                        return true;
+            } else {
+                if (sp < kStack) stack[sp++] = a;  // right child later; the builder caps the depth at 60
+                node = node + 1;
+                continue;
+            }
+        }
+        if (sp == 0) return false;
+        node = stack[--sp];
+    }
+}
+
+struct AoArgs {
+    const float4* nodes;
+    const float4* tris;
+    const void* pos;
+    const void* nrm;
+    int64_t n;
+    int32_t in_f16, rays, e_f16;
+    float radius;
+    uint32_t k0, k1;
+    float lo[3], hi[3];
+    float* ao;
+    void* E;
+};
+
+__global__ void __launch_bounds__(128) ao_kernel(AoArgs a) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= a.n) return;
+    const float4 p = niv_load_rec(a.pos, r, a.in_f16), nv = niv_load_rec(a.nrm, r, a.in_f16);
+    const float nl = sqrtf(nv.x * nv.x + nv.y * nv.y + nv.z * nv.z);
+    const float3 n = make_float3(nv.x / nl, nv.y / nl, nv.z / nl);
+    const float3 o = make_float3(p.x + kRayBias * n.x, p.y + kRayBias * n.y, p.z + kRayBias * n.z);
+    const float gx = fmaxf(fmaxf(a.lo[0] - o.x, o.x - a.hi[0]), 0.0f);
+    const float gy = fmaxf(fmaxf(a.lo[1] - o.y, o.y - a.hi[1]), 0.0f);
+    const float gz = fmaxf(fmaxf(a.lo[2] - o.z, o.z - a.hi[2]), 0.0f);
+    int blocked = 0;
+    if (gx * gx + gy * gy + gz * gz <= a.radius * a.radius) {
+        for (int j = 0; j < a.rays; ++j) {
+            const uint4 u = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)(r >> 32), (uint32_t)j, 0xA0u), a.k0, a.k1);
+            const float3 d = cosine_dir(n, u01(u.x), u01(u.y));
+            blocked += any_hit(a.nodes, a.tris, o, d, a.radius);
+        }
+    }
+    const float ao = 1.0f - (float)blocked / (float)a.rays;
+    if (a.ao) a.ao[r] = ao;
+    if (a.E) {
+        const float4 e = niv_load_rec(a.E, r, a.e_f16);
+        niv_store_rec(a.E, r, e.x * ao, e.y * ao, e.z * ao, a.e_f16);
+    }
+}
+
+}  // namespace
+
+int niv_dyn_build(const float* tri9, int64_t n_tris, niv_dyn** out) {
+    if (n_tris < 1 || n_tris > (int64_t)1 << 30) return niv_fail(NIV_ERR_ARG, "triangle count must be in 1..2^30");
+    Builder B;
+    B.tri = tri9;
+    B.cen.resize(3 * (size_t)n_tris);
+    B.order.resize((size_t)n_tris);
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < n_tris; ++i) {
+        B.order[(size_t)i] = (int32_t)i;
+        for (int k = 0; k < 3; ++k) {
+            const float a = tri9[9 * i + k], b = tri9[9 * i + 3 + k], c = tri9[9 * i + 6 + k];
+            if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c))
+                return niv_fail(NIV_ERR_ARG, "non-finite triangle vertex");
+            B.cen[3 * (size_t)i + k] = (a + b + c) * (1.0f / 3.0f);
+            lo[k] = std::min(lo[k], std::min(a, std::min(b, c)));
+            hi[k] = std::max(hi[k], std::max(a, std::max(b, c)));
+        }
+    }
+    float ext = 0.0f;
+    for (int k = 0; k < 3; ++k) ext = std::max(ext, hi[k] - lo[k]);
+    B.pad = 1e-5f * std::max(ext, 1e-3f);
+    B.build(0, (int32_t)n_tris, 0);
+    std::vector<float4> nodes(2 * B.nodes.size()), tris(3 * (size_t)n_tris);
+    for (size_t i = 0; i < B.nodes.size(); ++i) {
+        const HostNode& h = B.nodes[i];
+        float a, b;
+        memcpy(&a, &h.a, 4);
+        memcpy(&b, &h.b, 4);
+        nodes[2 * i] = make_float4(h.lo[0], h.lo[1], h.lo[2], a);
+        nodes[2 * i + 1] = make_float4(h.hi[0], h.hi[1], h.hi[2], b);
+    }
+    for (int64_t i = 0; i < n_tris; ++i) {
+        const float* t = tri9 + 9 * (int64_t)B.order[(size_t)i];
+        tris[3 * i] = make_float4(t[0], t[1], t[2], 0.0f);
+        tris[3 * i + 1] = make_float4(t[3] - t[0], t[4] - t[1], t[5] - t[2], 0.0f);
+        tris[3 * i + 2] = make_float4(t[6] - t[0], t[7] - t[1], t[8] - t[2], 0.0f);
+    }
+    niv_dyn* d = new niv_dyn();
+    d->n_tris = n_tris;
+    d->n_nodes = (int64_t)B.nodes.size();
+    for (int k = 0; k < 3; ++k) {
+        d->lo[k] = lo[k] - B.pad;
+        d->hi[k] = hi[k] + B.pad;
+    }
+    cudaError_t e = cudaGetDevice(&d->device);
+    d->nodes = nullptr;
+    d->tris = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d->nodes, sizeof(float4) * nodes.size());
+    if (e == cudaSuccess) e = cudaMalloc(&d->tris, sizeof(float4) * tris.size());
+    if (e == cudaSuccess) e = cudaMemcpy(d->nodes, nodes.data(), sizeof(float4) * nodes.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d->tris, tris.data(), sizeof(float4) * tris.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d->nodes);
+        cudaFree(d->tris);
+        delete d;
+        return niv_cuda_fail(e, "dynamic geometry upload");
+    }
+    *out = d;
+    return NIV_OK;
+}
+
+void niv_dyn_free(niv_dyn* d) {
+    if (!d) return;
+    cudaFree(d->nodes);
+    cudaFree(d->tris);
+    delete d;
+}
+
+int64_t niv_dyn_node_count(const niv_dyn* d) { return d->n_nodes; }
+
+int niv_launch_ao(const niv_dyn* d, const void* pos, const void* nrm, int64_t n, int32_t in_f16, int32_t rays,
+                  float radius, uint64_t seed, float* ao, void* E, int32_t e_f16, cudaStream_t s) {
+    AoArgs a;
+    a.nodes = d->nodes;
+    a.tris = d->tris;
+    a.pos = pos;
+    a.nrm = nrm;
+    a.n = n;
+    a.in_f16 = in_f16;
+    a.rays = rays;
+    a.e_f16 = e_f16;
+    a.radius = radius;
+    a.k0 = (uint32_t)seed;
+    a.k1 = (uint32_t)(seed >> 32);
+    for (int k = 0; k < 3; ++k) {
+        a.lo[k] = d->lo[k];
+        a.hi[k] = d->hi[k];
+    }
+    a.ao = ao;
+    a.E = E;
+    ao_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
+    NIV_CUDA(cudaGetLastError());
+    return NIV_OK;
+}

@@ -1,6 +1,8 @@
 // Host side of the C ABI: model objects, parameter management, argument checks
 // and dispatch of the query / shading kernels.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -647,6 +649,39 @@ int niv_query_shade(niv_handle h, const void* pos, const void* nrm, const void* 
         case NIV_FP8: return niv_launch_query_f8(h, g, io, (cudaStream_t)stream);
         default: return niv_fail(NIV_ERR_UNSUPPORTED, "precision not supported");
     }
+}
+
+int niv_dyn_create(const float* tris, int64_t n_tris, niv_dyn_handle* out) {
+    if (!tris || !out) return niv_fail(NIV_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    return niv_dyn_build(tris, n_tris, out);
+}
+
+int niv_dyn_destroy(niv_dyn_handle d) {
+    if (!d) return NIV_OK;
+    cudaDeviceSynchronize();
+    niv_dyn_free(d);
+    return NIV_OK;
+}
+
+int64_t niv_dyn_node_count(niv_dyn_handle d) { return d ? niv_dyn_node_count(static_cast<const niv_dyn*>(d)) : 0; }
+
+int niv_dyn_ao(niv_dyn_handle d, const void* pos, const void* nrm, int64_t n, int32_t dtype_in, int32_t rays,
+               float radius, uint64_t seed, float* out_ao, void* E_inout, int32_t dtype_E, niv_stream stream) {
+    if (!d) return niv_fail(NIV_ERR_ARG, "dynamic geometry handle is NULL");
+    if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
+    if (n == 0) return NIV_OK;
+    if (rays < 1 || rays > 1024) return niv_fail(NIV_ERR_ARG, "rays must be in 1..1024");
+    if (!(radius > 0.0f) || !std::isfinite(radius)) return niv_fail(NIV_ERR_ARG, "radius must be > 0");
+    if (!pos || !nrm) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if (!aligned16(pos) || !aligned16(nrm) || (E_inout && !aligned16(E_inout)))
+        return niv_fail(NIV_ERR_ALIGN, "record pointers must be 16-byte aligned");
+    if ((dtype_in != NIV_F32 && dtype_in != NIV_F16) || (E_inout && dtype_E != NIV_F32 && dtype_E != NIV_F16))
+        return niv_fail(NIV_ERR_ARG, "record dtype must be NIV_F32 or NIV_F16");
+    int dev = -1;
+    NIV_CUDA(cudaGetDevice(&dev));
+    return niv_launch_ao(d, pos, nrm, n, dtype_in == NIV_F16, rays, radius, seed, out_ao, E_inout,
+                         dtype_E == NIV_F16, (cudaStream_t)stream);
 }
 
 int niv_query_sub(niv_handle h, const void* pos, const void* nrm, int32_t full_width, int32_t full_height,

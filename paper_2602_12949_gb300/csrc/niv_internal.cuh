@@ -147,6 +147,12 @@ int niv_launch_upsample_shade(const void* pos, const void* nrm, const void* albe
                               int32_t height, int32_t in_f16, const void* E_low, int32_t e_f16, int32_t sub, float power,
                               float sigma, float eps, void* out, cudaStream_t s);
 int niv_pack_plain(niv_model* m, const float* mlp_host, cudaStream_t s);
+struct niv_dyn;
+int niv_dyn_build(const float* tri9, int64_t n_tris, niv_dyn** out);
+void niv_dyn_free(niv_dyn* d);
+int64_t niv_dyn_node_count(const niv_dyn* d);
+int niv_launch_ao(const niv_dyn* d, const void* pos, const void* nrm, int64_t n, int32_t in_f16, int32_t rays,
+                  float radius, uint64_t seed, float* ao, void* E, int32_t e_f16, cudaStream_t s);
 int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s);
 // status: device word for kernel-side failures (nullptr = this device's library status word).
 int niv_launch_query_tc(const niv_model* m, const GridArgs& g, const IoArgs& io, int precision, cudaStream_t s,

@@ -258,6 +258,48 @@ class NIVModel:
         return enc, idx
 
 
+class DynamicGeometry:
+    """The frame's dynamic triangles (host float32 [T][9], world space) in a bounding-volume
+    hierarchy on the current device, for the dynamic ambient-occlusion pass (Sec. 4.4)."""
+
+    def __init__(self, tri9):
+        tri9 = np.ascontiguousarray(np.asarray(tri9, np.float32).reshape(-1, 9))
+        h = ctypes.c_void_p()
+        check(lib().niv_dyn_create(ctypes.c_void_p(tri9.ctypes.data), len(tri9), ctypes.byref(h)))
+        self._h = h
+        self.n_tris = len(tri9)
+
+    @property
+    def node_count(self):
+        return int(lib().niv_dyn_node_count(self._h))
+
+    def ao(self, pos, nrm, rays=8, radius=0.5, seed=0, out=None, E=None, stream=None):
+        """AO in [0, 1] per device record (float32 [n]); E ([n][4] device records, optional) is
+        scaled by it in place."""
+        _check_records(pos, "pos")
+        _check_records(nrm, "nrm")
+        if out is None:
+            out = torch.empty(pos.shape[0], dtype=torch.float32, device=pos.device)
+        if E is not None:
+            _check_records(E, "E")
+        check(lib().niv_dyn_ao(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                               pos.shape[0], _rec_dtype(pos), int(rays), float(radius), int(seed),
+                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(E.data_ptr() if E is not None else 0),
+                               _rec_dtype(E) if E is not None else 0, _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().niv_dyn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def upsample_shade(pos, nrm, albedo, direct, width, height, E_low, sub=2, power=8.0, sigma=0.05, eps=1e-4,
                    out=None, stream=None):
     """Full-resolution FP16 rgba from irradiance E_low queried at every sub-th pixel (joint
