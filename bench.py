@@ -118,7 +118,7 @@ def _profiled_traffic():
     kernel sources are unchanged since that capture; else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "niv_query_fp16_1080p.md")
-    srcs = ["query_tc.cu", "niv_internal.cuh", "tc_ptx.cuh"]
+    srcs = ["query_tc.cu", "encoding.cuh", "tc_ptx.cuh"]  # the kernel and every device helper it includes
     try:
         text = open(path).read()
         rec = dict(l.split(":", 1) for l in text.splitlines()

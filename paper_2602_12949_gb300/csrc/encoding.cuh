@@ -1,0 +1,356 @@
+// Kernel-side definitions every query kernel shares: the per-call argument blocks and the
+// encoding, record and tile helpers (Sec. 4.1 encoding, Sec. 4.4 G-buffer records).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#define NIV_MAX_LEVELS 32
+#define NIV_MAX_IN 132  // levels * feat + in_extra upper bound for the plain path
+
+// Spatial-hash constants of the multi-resolution hash encoding adopted in Sec. 4.1
+// (Mueller et al. 2022): pi_1 = 1, pi_2 = 2654435761, pi_3 = 805459861.
+#define NIV_PI1 1u
+#define NIV_PI2 2654435761u
+#define NIV_PI3 805459861u
+
+// Per-call description of the encoding, passed by value to the kernels.
+struct GridArgs {
+    int32_t dims, levels, feat, n_in;
+    uint32_t hash_mask;  // T - 1
+    uint32_t prime_t;
+    uint32_t dense_mask;  // bit l set: level l is dense
+    int32_t pe_bands;     // > 0: frequency encoding of the position (no grid levels)
+    float aabb_min[3];
+    float inv_ext[3];
+    float t;
+    int32_t res[NIV_MAX_LEVELS];
+    uint32_t offset[NIV_MAX_LEVELS];  // first entry of each level
+};
+
+// Where a kernel finds its records and how it walks them.
+struct IoArgs {
+    const void* pos;
+    const void* nrm;
+    void* out;
+    int64_t n;
+    int32_t image_width;  // > 0: 2-D tile traversal of a row-major image
+    int32_t in_f16;       // records are FP16 (else FP32)
+    int32_t out_f16;
+    // Fused shading (Eq. 2 + direct light): when albedo is set, out receives FP16
+    // rgba = (albedo * E / pi + direct, 1) instead of E.  FP16 [n][4] records.
+    const void* albedo = nullptr;
+    const void* direct = nullptr;
+    // Half-resolution rendering (Sec. 4.4): sub > 1 makes record r of the image_width-wide
+    // output the pixel (sub x, sub y) of a src_width-wide full-resolution G-buffer, where
+    // (x, y) is r's position in the output image.
+    int32_t sub = 1;
+    int32_t src_width = 0;
+};
+
+// G-buffer record read for output record r (see IoArgs::sub).
+__device__ __forceinline__ int64_t niv_source_of(const IoArgs& io, int64_t r) {
+    if (io.sub <= 1) return r;
+    const int64_t y = r / io.image_width, x = r - y * io.image_width;
+    return y * io.sub * io.src_width + x * io.sub;
+}
+
+// ---- device helpers shared by the query kernels ----
+
+// u = clamp(fp32(fp32(p - lo) * inv), 0, 1): FP32 operations without contraction.
+__device__ __forceinline__ float niv_unit(float p, float lo, float inv) {
+    float x = __fmul_rn(__fsub_rn(p, lo), inv);
+    return fminf(fmaxf(x, 0.0f), 1.0f);
+}
+
+// Cell of one coordinate at resolution N: s = fp32(u * N), i = min(floor(s), N - 1), w = s - i (exact).
+__device__ __forceinline__ void niv_cell(float u, int32_t N, uint32_t& i, float& w) {
+    float s = __fmul_rn(u, (float)N);
+    int ii = min((int)floorf(s), N - 1);
+    i = (uint32_t)ii;
+    w = __fsub_rn(s, (float)ii);
+}
+
+// Frequency encoding (the models of Table 1 without grid levels): for a coordinate u of
+// the normalised position and band b, (sin(2^b pi u), cos(2^b pi u)); 2^b u is exact in FP32.
+__device__ __forceinline__ void niv_pe_pair(float u, int b, float& s, float& c) {
+    sincospif(__fmul_rn(u, (float)(1 << b)), &s, &c);
+}
+
+// Entry index of vertex v at a level: dense row-major (x fastest) or spatial hash.
+template <int DIMS>
+__device__ __forceinline__ uint32_t niv_vertex_index(bool dense, uint32_t stride, const uint32_t* v,
+                                                     uint32_t mask, uint32_t prime_t) {
+    if (dense) {
+        uint32_t idx = v[DIMS - 1];
+#pragma unroll
+        for (int k = DIMS - 2; k >= 0; --k) idx = idx * stride + v[k];
+        return idx;
+    }
+    uint32_t h = v[0] * NIV_PI1 ^ v[1] * NIV_PI2 ^ v[2] * NIV_PI3;
+    if (DIMS == 4) h ^= v[3] * prime_t;
+    return h & mask;
+}
+
+// Corner entries and multilinear weights of level l at normalised coordinate u
+// (Sec. 4.1), with the per-corner work factored: one cell per axis, per-axis index
+// terms (dense strides or hash products) combined per corner, weights as products
+// of per-axis factors.  Corner c has offset bit d along dimension d.
+template <int DIMS>
+__device__ __forceinline__ void niv_level_corners(const GridArgs& g, int l, const float* u, uint32_t* e,
+                                                  float* wc) {
+    constexpr int NC = 1 << DIMS;
+    const int32_t N = g.res[l];
+    const float fN = (float)N, fmax = (float)(N - 1);
+    uint32_t ci[DIMS];
+    float w1[DIMS], w0[DIMS];
+#pragma unroll
+    for (int d = 0; d < DIMS; ++d) {
+        const float s = __fmul_rn(u[d], fN);
+        const float fl = fminf(floorf(s), fmax);
+        ci[d] = (uint32_t)(int)fl;
+        w1[d] = __fsub_rn(s, fl);
+        w0[d] = 1.0f - w1[d];
+    }
+    {
+        // Products in pairs on the packed FP32 pipe: each lane is an ordinary FP32 product,
+        // so the weights are those of the scalar formulas.
+        const float2 wy = make_float2(w0[1], w1[1]), wx = make_float2(w0[0], w1[0]);
+        float2 wh[NC / 4];  // wh[q] = (w_y0 * w_rest_q, w_y1 * w_rest_q)
+        wh[0] = __fmul2_rn(wy, make_float2(w0[2], w0[2]));
+        wh[1] = __fmul2_rn(wy, make_float2(w1[2], w1[2]));
+        if (DIMS == 4) {
+            const float2 t0 = make_float2(w0[DIMS - 1], w0[DIMS - 1]), t1 = make_float2(w1[DIMS - 1], w1[DIMS - 1]);
+            wh[2 % (NC / 4)] = __fmul2_rn(wh[0], t1);
+            wh[3 % (NC / 4)] = __fmul2_rn(wh[1], t1);
+            wh[0] = __fmul2_rn(wh[0], t0);
+            wh[1] = __fmul2_rn(wh[1], t0);
+        }
+#pragma unroll
+        for (int q = 0; q < NC / 4; ++q) {
+            const float2 a = __fmul2_rn(wx, make_float2(wh[q].x, wh[q].x));
+            const float2 b = __fmul2_rn(wx, make_float2(wh[q].y, wh[q].y));
+            wc[4 * q] = a.x;
+            wc[4 * q + 1] = a.y;
+            wc[4 * q + 2] = b.x;
+            wc[4 * q + 3] = b.y;
+        }
+    }
+    if ((g.dense_mask >> l) & 1u) {
+        const uint32_t S = (uint32_t)N + 1u, S2 = S * S;
+        uint32_t base = ci[2] * S2 + ci[1] * S + ci[0];
+        if (DIMS == 4) base += ci[DIMS - 1] * S2 * S;
+        uint32_t oh[NC / 2];
+        oh[0] = base;
+        oh[1] = base + S;
+        oh[2] = base + S2;
+        oh[3] = base + S2 + S;
+        if (DIMS == 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) oh[(q + 4) % (NC / 2)] = oh[q] + S2 * S;
+        }
+#pragma unroll
+        for (int q = 0; q < NC / 2; ++q) {
+            e[2 * q] = oh[q];
+            e[2 * q + 1] = oh[q] + 1u;
+        }
+    } else {
+        const uint32_t hy0 = ci[1] * NIV_PI2, hy1 = hy0 + NIV_PI2;
+        const uint32_t hz0 = ci[2] * NIV_PI3, hz1 = hz0 + NIV_PI3;
+        uint32_t hh[NC / 2];
+        hh[0] = hy0 ^ hz0;
+        hh[1] = hy1 ^ hz0;
+        hh[2] = hy0 ^ hz1;
+        hh[3] = hy1 ^ hz1;
+        if (DIMS == 4) {
+            const uint32_t ht0 = ci[DIMS - 1] * g.prime_t, ht1 = ht0 + g.prime_t;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                hh[(q + 4) % (NC / 2)] = hh[q] ^ ht1;
+                hh[q] = hh[q] ^ ht0;
+            }
+        }
+        const uint32_t x0 = ci[0], x1 = ci[0] + 1u, m = g.hash_mask;
+#pragma unroll
+        for (int q = 0; q < NC / 2; ++q) {
+            e[2 * q] = (x0 ^ hh[q]) & m;
+            e[2 * q + 1] = (x1 ^ hh[q]) & m;
+        }
+    }
+}
+
+// Raw feature words of the corners: F features of type TabT per entry.
+template <int F, typename TabT>
+struct NivRaw {
+    using T = typename std::conditional<
+        sizeof(TabT) == 2, typename std::conditional<F == 4, uint2, typename std::conditional<F == 2, uint32_t, unsigned short>::type>::type,
+        typename std::conditional<F == 4, float4, typename std::conditional<F == 2, float2, float>::type>::type>::type;
+};
+
+template <int NC, int F, typename TabT>
+__device__ __forceinline__ void niv_level_gather(const TabT* __restrict__ tab, const uint32_t* e,
+                                                 typename NivRaw<F, TabT>::T* raw) {
+    using R = typename NivRaw<F, TabT>::T;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) raw[c] = __ldg(reinterpret_cast<const R*>(tab) + e[c]);
+}
+
+__device__ __forceinline__ void niv_unpack(uint32_t r, float* f) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r));
+    f[0] = a.x;
+    f[1] = a.y;
+}
+__device__ __forceinline__ void niv_unpack(uint2 r, float* f) {
+    niv_unpack(r.x, f);
+    niv_unpack(r.y, f + 2);
+}
+__device__ __forceinline__ void niv_unpack(unsigned short r, float* f) { f[0] = __half2float(__ushort_as_half(r)); }
+__device__ __forceinline__ void niv_unpack(float r, float* f) { f[0] = r; }
+__device__ __forceinline__ void niv_unpack(float2 r, float* f) {
+    f[0] = r.x;
+    f[1] = r.y;
+}
+__device__ __forceinline__ void niv_unpack(float4 r, float* f) {
+    f[0] = r.x;
+    f[1] = r.y;
+    f[2] = r.z;
+    f[3] = r.w;
+}
+
+template <int NC, int F, typename R>
+__device__ __forceinline__ void niv_level_blend(const R* raw, const float* wc, float* acc) {
+#pragma unroll
+    for (int j = 0; j < F; ++j) acc[j] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        float f[F];
+        niv_unpack(raw[c], f);
+#pragma unroll
+        for (int j = 0; j < F; ++j) acc[j] = fmaf(wc[c], f[j], acc[j]);
+    }
+}
+
+// Interpolated features of level l (corners, gathers, blend).
+template <int DIMS, int F, typename TabT>
+__device__ __forceinline__ void niv_encode_level(const GridArgs& g, const TabT* __restrict__ grid, int l,
+                                                 const float* u, float* acc) {
+    constexpr int NC = 1 << DIMS;
+    uint32_t e[NC];
+    float wc[NC];
+    niv_level_corners<DIMS>(g, l, u, e, wc);
+    typename NivRaw<F, TabT>::T raw[NC];
+    niv_level_gather<NC, F, TabT>(grid + (size_t)g.offset[l] * F, e, raw);
+    niv_level_blend<NC, F>(raw, wc, acc);
+}
+
+// Linear record index of thread slot `k` of tile `tile` (128-record tiles).  For images a tile
+// is a 16 x 8 pixel block and each warp of it an 8 x 4 sub-block, so the 32 queries of a warp
+// are as compact on screen (and so in the scene) as possible.
+__device__ __forceinline__ int64_t niv_record_of(int64_t tile, int k, int64_t n, int32_t width) {
+    if (width <= 0) return tile * 128 + k;
+    int64_t tiles_x = (width + 15) / 16;
+    int64_t ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int w = k >> 5, lane = k & 31;
+    int64_t px = tx * 16 + (w & 1) * 8 + (lane & 7), py = ty * 8 + (w >> 1) * 4 + (lane >> 3);
+    if (px >= width) return n;  // outside the image: no record
+    return py * width + px;
+}
+
+// Persistent walk over 128-record tiles with a fixed stride, in the record order of
+// niv_record_of: the image tile coordinates (tx, ty) advance by the stride's column and
+// row parts, so no tile costs a 64-bit division.
+struct NivTileWalk {
+    int64_t tile, stride, ty, sy;
+    int32_t tiles_x, tx, sx, ox, oy;
+
+    __device__ __forceinline__ void init(int64_t first, int64_t step, int k, int32_t width) {
+        tile = first;
+        stride = step;
+        const int w = k >> 5, lane = k & 31;
+        ox = (w & 1) * 8 + (lane & 7);
+        oy = (w >> 1) * 4 + (lane >> 3);
+        tiles_x = width > 0 ? (width + 15) / 16 : 1;
+        ty = first / tiles_x;
+        tx = (int32_t)(first - ty * tiles_x);
+        sy = step / tiles_x;
+        sx = (int32_t)(step - sy * tiles_x);
+    }
+    __device__ __forceinline__ void next() {
+        tile += stride;
+        tx += sx;
+        ty += sy;
+        if (tx >= tiles_x) {
+            tx -= tiles_x;
+            ++ty;
+        }
+    }
+    // Record of thread slot k (n: outside the image).
+    __device__ __forceinline__ int64_t record(int k, int64_t n, int32_t width) const {
+        if (width <= 0) return tile * 128 + k;
+        const int32_t px = tx * 16 + ox;
+        if (px >= width) return n;
+        return (ty * 8 + oy) * (int64_t)width + px;
+    }
+    // G-buffer record of this thread's output record r (see IoArgs::sub).
+    __device__ __forceinline__ int64_t source(int64_t r, const IoArgs& io) const {
+        if (io.sub <= 1) return r;
+        return (ty * 8 + oy) * io.sub * (int64_t)io.src_width + (int64_t)(tx * 16 + ox) * io.sub;
+    }
+};
+
+__device__ __forceinline__ int64_t niv_tile_count(int64_t n, int32_t width) {
+    if (width <= 0) return (n + 127) / 128;
+    int64_t rows = (n + width - 1) / width;
+    return ((width + 15) / 16) * ((rows + 7) / 8);
+}
+
+__host__ __forceinline__ int64_t niv_tile_count_host(int64_t n, int32_t width) {
+    if (width <= 0) return (n + 127) / 128;
+    int64_t rows = (n + width - 1) / width;
+    return ((width + 15) / 16) * ((rows + 7) / 8);
+}
+
+// Load one [4] record (FP16 or FP32) as float4.
+__device__ __forceinline__ float4 niv_load_rec(const void* base, int64_t i, bool f16) {
+    if (f16) {
+        uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + i);
+        __half2 a = *reinterpret_cast<__half2*>(&r.x), b = *reinterpret_cast<__half2*>(&r.y);
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+    return __ldg(reinterpret_cast<const float4*>(base) + i);
+}
+
+__device__ __forceinline__ void niv_store_rec(void* base, int64_t i, float x, float y, float z, bool f16) {
+    if (f16) {
+        __half2 a = __floats2half2_rn(x, y), b = __floats2half2_rn(z, 0.0f);
+        uint2 r;
+        r.x = *reinterpret_cast<uint32_t*>(&a);
+        r.y = *reinterpret_cast<uint32_t*>(&b);
+        reinterpret_cast<uint2*>(base)[i] = r;
+    } else {
+        reinterpret_cast<float4*>(base)[i] = make_float4(x, y, z, 0.0f);
+    }
+}
+
+// Final store of a query: E, or the shaded rgba when the call fused shading.
+__device__ __forceinline__ void niv_store_result(const IoArgs& io, int64_t i, float e0, float e1, float e2) {
+    if (io.albedo) {
+        const float inv_pi = 0.318309886183790671538f;
+        const float4 a = niv_load_rec(io.albedo, i, true), d = niv_load_rec(io.direct, i, true);
+        __half2 rg = __floats2half2_rn(fmaf(a.x * e0, inv_pi, d.x), fmaf(a.y * e1, inv_pi, d.y));
+        __half2 ba = __floats2half2_rn(fmaf(a.z * e2, inv_pi, d.z), 1.0f);
+        uint2 r;
+        r.x = *reinterpret_cast<uint32_t*>(&rg);
+        r.y = *reinterpret_cast<uint32_t*>(&ba);
+        reinterpret_cast<uint2*>(io.out)[i] = r;
+    } else {
+        niv_store_rec(io.out, i, e0, e1, e2, io.out_f16);
+    }
+}
+
+// softplus(z) = max(z, 0) + log1p(exp(-|z|)) in FP32 with CUDA's libm functions.
+__device__ __forceinline__ float niv_softplus(float z) { return fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))); }
