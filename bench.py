@@ -46,10 +46,11 @@ def _args():
     ap.add_argument("--res", default="1080p", choices=["1080p", "4k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison and error checks")
-    ap.add_argument("--workload", default="config1", choices=["config1", "config3", "half", "sweep"],
+    ap.add_argument("--workload", default="config1", choices=["config1", "config3", "half", "sweep", "train"],
                     help="config1: the headline (config-1 model on the room frame); config3: the 4-D model at "
                          "--res with t from the seed; half: quarter-pixel query + upsampling and shading; "
-                         "sweep: memory-error trade-off (hash table sizes against probes of equal memory)")
+                         "sweep: memory-error trade-off (hash table sizes against probes of equal memory); "
+                         "train: niv_fit steps at batch 2^18 and the Monte Carlo target rate (config 2)")
     return ap.parse_args()
 
 
@@ -382,12 +383,73 @@ def run_sweep(a):
     print(json.dumps(line), flush=True)
 
 
+def run_train(a):
+    """Config 2's training step: niv_fit (FP32 forward, hand-written backward, Adam) on batches
+    of 2^18 samples of the room, timed with CUDA events over K steps after W warm-up steps;
+    beside it the GPU Monte Carlo target rate at 1024 spp (INDIRECT) on 2^16 training
+    samples, and the time the whole schedule (5,000 steps, 2^20-sample pools at 1024 spp,
+    one pool per 4 steps) takes at these rates."""
+    import torch
+    from paper_2602_12949_gb300 import NIVModel, mc_irradiance, sync_status
+    from niv_inputs import init_params, room_scene
+    from niv_inputs.configs import MODEL_C1, ROOM_MIN, ROOM_MAX
+    from niv_inputs.samples import training_pool
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    scene = room_scene(0)
+    batch = 1 << 18
+    x4, n4, _ = training_pool(scene, batch, seed=5)
+    dx, dn = torch.from_numpy(x4).to(dev), torch.from_numpy(n4).to(dev)
+    y = torch.rand((batch, 4), device=dev) * 2.0 + 0.1
+    m = NIVModel(**MODEL_C1)
+    g, nm = m.param_count()
+    m.set_params(init_params(g, m.layer_shapes(), seed=0))
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)
+    for _ in range(a.warmup):
+        m.fit(dx, dn, y, want_loss=False, **kw)
+    sync_status()
+    stream = torch.cuda.current_stream()
+    s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(a.steps):
+        m.fit(dx, dn, y, want_loss=False, **kw)
+    e0.record(stream)
+    torch.cuda.synchronize()
+    sync_status()
+    step_ms = s0.elapsed_time(e0) / a.steps
+    mc_n, spp = 1 << 16, 1024
+    mx, mn, _ = training_pool(scene, mc_n, seed=6)
+    mxd, mnd = torch.from_numpy(mx).to(dev), torch.from_numpy(mn).to(dev)
+    mc_irradiance(scene.blob(), mxd, mnd, 16, seed=1, mode="indirect")
+    torch.cuda.synchronize()
+    s0.record(stream)
+    mc_irradiance(scene.blob(), mxd, mnd, spp, seed=2, mode="indirect")
+    e0.record(stream)
+    torch.cuda.synchronize()
+    mc_ms = s0.elapsed_time(e0)
+    paths_per_s = mc_n * spp / (mc_ms * 1e-3)
+    schedule_s = 5000 * step_ms * 1e-3 + (5000 / 4) * (1 << 20) * 1024 / paths_per_s
+    line = {"metric": "niv_fit step time at batch 2^18 (config 2) and Monte Carlo target rate",
+            "value": 1e3 / step_ms, "unit": "steps/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": step_ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "samples_per_s": batch / (step_ms * 1e-3), "mc_paths_per_s": paths_per_s,
+            "mc_ms_per_2e16_samples_1024spp": mc_ms, "projected_config2_schedule_s": schedule_s,
+            "config": {"workload": "config2-train: config-1 model on 2^18 room training samples (80% volume, "
+                                   "20% surface), Eq. 3 loss, Adam lr 1e-2; targets from the GPU Monte Carlo "
+                                   "integrator (INDIRECT, 1024 spp)", "batch": batch, "parallelism": "single"}}
+    print(json.dumps(line), flush=True)
+    m.close()
+
+
 def run_workload(a):
     """One side workload on one GPU, timed like the headline: K steps after W warm-up steps,
     L2 flushed (256 MB write) before each step, CUDA events on the launching stream."""
     import torch
     if a.workload == "sweep":
         run_sweep(a)
+        return
+    if a.workload == "train":
+        run_train(a)
         return
     from paper_2602_12949_gb300 import NIVModel, upsample_shade
     from niv_inputs import init_params

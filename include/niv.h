@@ -198,6 +198,17 @@ typedef struct niv_fit_params {
 NIV_API int niv_grad(niv_handle h, const float* pos, const float* nrm, const float* t, const float* target, int64_t n,
                      const niv_query_params* params, float loss_eps, double* loss_out, niv_stream stream);
 
+/*
+ * Vector-Jacobian product of the query (the hand-written backward of Sec. 4.5 with the
+ * loss left to the caller): for device float32 [n][4] records pos, nrm and grad_E (dL/dE
+ * per sample in xyz), the gradient buffer receives dL/dtheta = sum over samples of
+ * grad_E . dE/dtheta for every parameter (grid values with their hash collisions summed,
+ * weights, biases), E being the FP32 forward against the FP32 master parameters.  t as
+ * in niv_grad.  Read the result with niv_get_grads.  Asynchronous.
+ */
+NIV_API int niv_backward(niv_handle h, const float* pos, const float* nrm, const float* t, const float* grad_E,
+                         int64_t n, const niv_query_params* params, niv_stream stream);
+
 /* Copy the n gradient values of the last niv_grad to `out` (host or device).  Synchronises. */
 NIV_API int niv_get_grads(niv_handle h, float* out, int64_t n, niv_stream stream);
 

@@ -4,9 +4,9 @@
 all the work; this package marshals torch tensors into it.
 """
 from ._lib import lib, NivError, LIB_PATH
-from .model import (NIVModel, ProbeGrid, DynamicGeometry, shade, upsample_shade, sync_status, mc_irradiance,
+from .model import (NIVModel, NIVModule, ProbeGrid, DynamicGeometry, shade, upsample_shade, sync_status, mc_irradiance,
                     compact_targets, PRECISIONS)
 
-__all__ = ["lib", "NivError", "LIB_PATH", "NIVModel", "ProbeGrid", "DynamicGeometry", "shade", "upsample_shade",
+__all__ = ["lib", "NivError", "LIB_PATH", "NIVModel", "NIVModule", "ProbeGrid", "DynamicGeometry", "shade", "upsample_shade",
            "sync_status",
            "mc_irradiance", "compact_targets", "PRECISIONS"]

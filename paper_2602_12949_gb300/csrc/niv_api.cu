@@ -439,8 +439,9 @@ int niv_fp8_get_scales(niv_handle h, float* s_act, float* s_w, float* amax, int3
     return NIV_OK;
 }
 
-int niv_grad(niv_handle h, const float* pos, const float* nrm, const float* t, const float* target, int64_t n,
-             const niv_query_params* params, float eps, double* loss_out, niv_stream stream) {
+namespace {
+int grad_common(niv_handle h, const float* pos, const float* nrm, const float* t, const float* target, int64_t n,
+                const niv_query_params* params, float eps, bool vjp, double* loss_out, niv_stream stream) {
     if (!h || !params) return niv_fail(NIV_ERR_ARG, "handle or params is NULL");
     if (n <= 0) return niv_fail(NIV_ERR_ARG, "n must be positive");
     if (!pos || !nrm || !target) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
@@ -456,7 +457,7 @@ int niv_grad(niv_handle h, const float* pos, const float* nrm, const float* t, c
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     GridArgs g = niv_grid_args(h, params);
-    rc = niv_train_grad(h, g, (const float4*)pos, (const float4*)nrm, t, (const float4*)target, n, eps, s);
+    rc = niv_train_grad(h, g, (const float4*)pos, (const float4*)nrm, t, (const float4*)target, n, eps, vjp, s);
     if (rc) return rc;
     if (loss_out) {
         double acc = 0.0;
@@ -465,6 +466,17 @@ int niv_grad(niv_handle h, const float* pos, const float* nrm, const float* t, c
         *loss_out = acc / (3.0 * (double)n);
     }
     return NIV_OK;
+}
+}  // namespace
+
+int niv_grad(niv_handle h, const float* pos, const float* nrm, const float* t, const float* target, int64_t n,
+             const niv_query_params* params, float eps, double* loss_out, niv_stream stream) {
+    return grad_common(h, pos, nrm, t, target, n, params, eps, false, loss_out, stream);
+}
+
+int niv_backward(niv_handle h, const float* pos, const float* nrm, const float* t, const float* grad_E, int64_t n,
+                 const niv_query_params* params, niv_stream stream) {
+    return grad_common(h, pos, nrm, t, grad_E, n, params, 1.0f, true, nullptr, stream);
 }
 
 int niv_get_grads(niv_handle h, float* out, int64_t n, niv_stream stream) {

@@ -80,8 +80,9 @@ int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s);
 int niv_calibrate_f8(niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s);
 int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s);
 int64_t niv_train_stash_floats(const niv_model* m, int64_t n);
+// vjp: target holds dL/dE per sample (vector-Jacobian product) instead of the Eq. 3 targets.
 int niv_train_grad(niv_model* m, const GridArgs& g, const float4* pos, const float4* nrm, const float* t,
-                   const float4* target, int64_t n, float eps, cudaStream_t s);
+                   const float4* target, int64_t n, float eps, bool vjp, cudaStream_t s);
 int niv_train_adam(niv_model* m, float lr, float b1, float b2, float eps, cudaStream_t s);
 int niv_launch_mc(const float* blob, int64_t blob_len, const float* x4, const float* n4, const float* t, int64_t m,
                   int spp, uint64_t seed, uint64_t index_base, int mode, double* outE, uint8_t* keep, cudaStream_t s);

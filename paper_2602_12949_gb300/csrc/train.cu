@@ -21,6 +21,10 @@ constexpr int kMaxIn = 64;  // widest network input the training kernels take
 
 __device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
 
+// fwd_bwd_kernel mode bits: the target records hold dL/dE (vector-Jacobian product, no
+// loss); the output layer is the identity instead of softplus.
+constexpr int kModeVjp = 1, kModeIdentityOut = 2;
+
 // Row stride (floats) of stashed layer inputs: n_in rounded up to 4, or W.
 __host__ __device__ __forceinline__ int stash_stride(int k) { return (k + 3) & ~3; }
 
@@ -29,7 +33,7 @@ __global__ void __launch_bounds__(kT) fwd_bwd_kernel(GridArgs g, const float4* _
                                                      const float4* __restrict__ nrm, const float* __restrict__ tsamp,
                                                      const float4* __restrict__ target, int64_t n,
                                                      const float* __restrict__ params, int64_t n_grid, int nh,
-                                                     float eps, float inv_count, float* __restrict__ grad,
+                                                     float eps, float inv_count, int mode, float* __restrict__ grad,
                                                      float* __restrict__ stash, double* __restrict__ loss_sum) {
     extern __shared__ float smem[];
     const int n_in = g.n_in, LG = g.levels * F, LF = LG + 6 * g.pe_bands;  // grid values, all encoding values
@@ -109,15 +113,21 @@ __global__ void __launch_bounds__(kT) fwd_bwd_kernel(GridArgs g, const float4* _
         z[2] = fmaf(wo[2 * W + i], a, z[2]);
     }
     const float yy[3] = {y.x, y.y, y.z};
+    const bool vjp = mode & kModeVjp, soft = !(mode & kModeIdentityOut);
     float dz[3];
     double lsum = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float E = niv_softplus(z[c]);
-        const float den = E * E + eps;  // held constant (stop-gradient)
-        const float diff = E - yy[c];
-        lsum += (double)(diff * diff / den);
-        dz[c] = valid ? 2.0f * diff / den * inv_count * sigmoidf(z[c]) : 0.0f;
+        const float act = soft ? sigmoidf(z[c]) : 1.0f;  // d E / d z
+        if (vjp) {  // the record holds dL/dE from the caller
+            dz[c] = valid ? yy[c] * act : 0.0f;
+        } else {
+            const float E = soft ? niv_softplus(z[c]) : z[c];
+            const float den = E * E + eps;  // held constant (stop-gradient)
+            const float diff = E - yy[c];
+            lsum += (double)(diff * diff / den);
+            dz[c] = valid ? 2.0f * diff / den * inv_count * act : 0.0f;
+        }
     }
     if (!valid) lsum = 0.0;
     // block reduction of the loss
@@ -235,7 +245,7 @@ __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, fl
 
 template <int DIMS, int F, int W>
 int launch_fwd_bwd(niv_model* m, const GridArgs& g, const float4* pos, const float4* nrm, const float* t,
-                   const float4* target, int64_t n, float eps, cudaStream_t s) {
+                   const float4* target, int64_t n, float eps, int mode, cudaStream_t s) {
     auto kern = fwd_bwd_kernel<DIMS, F, W>;
     const int nh = m->d.n_hidden;
     const size_t smem = (size_t)(((m->n_mlp + 3) & ~3) + kMaxIn * kT + W * kT) * sizeof(float);
@@ -243,18 +253,18 @@ int launch_fwd_bwd(niv_model* m, const GridArgs& g, const float4* pos, const flo
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
     const unsigned blocks = (unsigned)((n + kT - 1) / kT);
     kern<<<blocks, kT, smem, s>>>(g, pos, nrm, t, target, n, m->params, m->n_grid, nh, eps, 1.0f / (3.0f * (float)n),
-                                  m->grad, m->stash, m->loss_acc);
+                                  mode | (m->d.out_act == 1 ? 0 : kModeIdentityOut), m->grad, m->stash, m->loss_acc);
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }
 
 template <int DIMS, int F>
 int by_width(niv_model* m, const GridArgs& g, const float4* pos, const float4* nrm, const float* t,
-             const float4* target, int64_t n, float eps, cudaStream_t s) {
+             const float4* target, int64_t n, float eps, int mode, cudaStream_t s) {
     switch (m->d.width) {
-        case 16: return launch_fwd_bwd<DIMS, F, 16>(m, g, pos, nrm, t, target, n, eps, s);
-        case 32: return launch_fwd_bwd<DIMS, F, 32>(m, g, pos, nrm, t, target, n, eps, s);
-        case 64: return launch_fwd_bwd<DIMS, F, 64>(m, g, pos, nrm, t, target, n, eps, s);
+        case 16: return launch_fwd_bwd<DIMS, F, 16>(m, g, pos, nrm, t, target, n, eps, mode, s);
+        case 32: return launch_fwd_bwd<DIMS, F, 32>(m, g, pos, nrm, t, target, n, eps, mode, s);
+        case 64: return launch_fwd_bwd<DIMS, F, 64>(m, g, pos, nrm, t, target, n, eps, mode, s);
     }
     return niv_fail(NIV_ERR_UNSUPPORTED, "width must be 16, 32 or 64");
 }
@@ -270,7 +280,8 @@ int64_t niv_train_stash_floats(const niv_model* m, int64_t n) {
 }
 
 int niv_train_grad(niv_model* m, const GridArgs& g, const float4* pos, const float4* nrm, const float* t,
-                   const float4* target, int64_t n, float eps, cudaStream_t s) {
+                   const float4* target, int64_t n, float eps, bool vjp, cudaStream_t s) {
+    const int mode = vjp ? kModeVjp : 0;
     const int W = m->d.width, nh = m->d.n_hidden, n_in = m->n_in;
     if (n_in > kMaxIn) return niv_fail(NIV_ERR_UNSUPPORTED, "training needs a network input of <= 64 values");
     const int64_t need = niv_train_stash_floats(m, n);
@@ -287,15 +298,15 @@ int niv_train_grad(niv_model* m, const GridArgs& g, const float4* pos, const flo
     int rc;
     if (m->d.dims == 4) {
         switch (m->d.feat) {
-            case 1: rc = by_width<4, 1>(m, g, pos, nrm, t, target, n, eps, s); break;
-            case 2: rc = by_width<4, 2>(m, g, pos, nrm, t, target, n, eps, s); break;
-            default: rc = by_width<4, 4>(m, g, pos, nrm, t, target, n, eps, s); break;
+            case 1: rc = by_width<4, 1>(m, g, pos, nrm, t, target, n, eps, mode, s); break;
+            case 2: rc = by_width<4, 2>(m, g, pos, nrm, t, target, n, eps, mode, s); break;
+            default: rc = by_width<4, 4>(m, g, pos, nrm, t, target, n, eps, mode, s); break;
         }
     } else {
         switch (m->d.feat) {
-            case 1: rc = by_width<3, 1>(m, g, pos, nrm, t, target, n, eps, s); break;
-            case 2: rc = by_width<3, 2>(m, g, pos, nrm, t, target, n, eps, s); break;
-            default: rc = by_width<3, 4>(m, g, pos, nrm, t, target, n, eps, s); break;
+            case 1: rc = by_width<3, 1>(m, g, pos, nrm, t, target, n, eps, mode, s); break;
+            case 2: rc = by_width<3, 2>(m, g, pos, nrm, t, target, n, eps, mode, s); break;
+            default: rc = by_width<3, 4>(m, g, pos, nrm, t, target, n, eps, mode, s); break;
         }
     }
     if (rc) return rc;

@@ -202,6 +202,21 @@ class NIVModel:
                              float(loss_eps), ctypes.byref(loss), _stream(stream)))
         return loss.value
 
+    def backward(self, pos, nrm, grad_E, t=None, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), t_scalar=0.0,
+                 stream=None):
+        """Vector-Jacobian product: dL/dtheta for the upstream dL/dE (device float32 [n][4]
+        records, xyz used) lands in the model's gradient buffer."""
+        tp = self._train_args(pos, nrm, grad_E, t)
+        qp = self.query_params(aabb_min, aabb_max, t_scalar, 0)
+        check(lib().niv_backward(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                                 ctypes.c_void_p(tp), ctypes.c_void_p(grad_E.data_ptr()), pos.shape[0],
+                                 ctypes.byref(qp), _stream(stream)))
+
+    def grads_into(self, out):
+        """Copy the gradient buffer into a float32 tensor of param_count() values (host or device)."""
+        check(lib().niv_get_grads(self._h, ctypes.c_void_p(out.data_ptr()), out.numel(), _stream()))
+        return out
+
     def get_grads(self):
         g, m = self.param_count()
         out = np.empty(g + m, np.float32)
@@ -256,6 +271,44 @@ class NIVModel:
                                ctypes.c_void_p(enc.data_ptr()),
                                ctypes.c_void_p(idx.data_ptr() if idx is not None else 0), _stream(stream)))
         return enc, idx
+
+
+class _QueryFunction(torch.autograd.Function):
+    """E(x, n; theta) in FP32 with the hand-written backward (Sec. 4.5) as its gradient."""
+
+    @staticmethod
+    def forward(ctx, params, pos, nrm, model, aabb_min, aabb_max, t):
+        model.set_params(params.detach())
+        E = model.query(pos, nrm, precision="fp32", out_dtype=torch.float32, aabb_min=aabb_min, aabb_max=aabb_max,
+                        t=t)
+        ctx.save_for_backward(pos, nrm)
+        ctx.model, ctx.box, ctx.t = model, (aabb_min, aabb_max), t
+        return E
+
+    @staticmethod
+    def backward(ctx, grad_E):
+        pos, nrm = ctx.saved_tensors
+        model = ctx.model
+        model.backward(pos, nrm, grad_E.detach().contiguous().float(), aabb_min=ctx.box[0], aabb_max=ctx.box[1],
+                       t_scalar=ctx.t)
+        g, m = model.param_count()
+        grad = model.grads_into(torch.empty(g + m, dtype=torch.float32, device=grad_E.device))
+        return grad, None, None, None, None, None, None
+
+
+class NIVModule(torch.nn.Module):
+    """A model as a torch module: the flat FP32 parameter vector [grid | network] is an
+    nn.Parameter, forward returns E ([n][4] float32 records) from the FP32 query, and autograd
+    runs the library's hand-written backward (niv_backward)."""
+
+    def __init__(self, model, params, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), device="cuda"):
+        super().__init__()
+        self.model = model
+        self.aabb_min, self.aabb_max = tuple(aabb_min), tuple(aabb_max)
+        self.params = torch.nn.Parameter(torch.as_tensor(np.asarray(params, np.float32), device=device).clone())
+
+    def forward(self, pos, nrm, t=0.0):
+        return _QueryFunction.apply(self.params, pos, nrm, self.model, self.aabb_min, self.aabb_max, float(t))
 
 
 class DynamicGeometry:

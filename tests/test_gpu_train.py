@@ -112,3 +112,86 @@ def test_fit_reduces_loss_and_trained_model_queries_match_oracle(niv):
     ref16 = oracle.query(om, trained.astype(np.float16).astype(np.float64), pos, nrm)
     assert np.max(np.abs(E16 - ref16) / np.maximum(np.abs(ref16), 1e-3 * np.abs(ref16).max())) <= 2e-3
     m.close()
+
+
+def _groups_max_err(om, got, ref):
+    worst = 0.0
+    for name, a, b in _groups(om):
+        if b > a:
+            scale = np.abs(ref[a:b]).max()
+            if scale > 0:
+                worst = max(worst, float(np.max(np.abs(got[a:b] - ref[a:b])) / scale))
+    return worst
+
+
+def test_autograd_with_eq3_in_torch_matches_oracle(niv):
+    """NIVModule's backward (niv_backward) under Eq. 3 written in torch, with the stop-gradient
+    denominator, gives the oracle's loss gradient."""
+    spec = dict(MODEL_C0, log2_T=10)
+    m = niv.NIVModel(**spec)
+    g, _ = m.param_count()
+    params = init_params(g, m.layer_shapes(), seed=3, feat_range=0.3, bias_std=0.2)
+    om = oracle.Model(**spec)
+    n = 3000
+    pos, nrm = uniform_queries(n, seed=4)
+    y = np.random.default_rng(5).uniform(0.1, 2.0, (n, 3))
+    mod = niv.NIVModule(m, params)
+    dp, dn = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+    E = mod(dp, dn)[:, :3]
+    yt = torch.from_numpy(y).float().cuda()
+    loss = ((E - yt) ** 2 / (E.detach() ** 2 + 0.01)).mean()
+    loss.backward()
+    got = mod.params.grad.cpu().numpy().astype(np.float64)
+    ref_loss, ref = oracle.loss_grad(om, params, pos, nrm, y)
+    assert loss.item() == pytest.approx(ref_loss, rel=1e-5)
+    err = _groups_max_err(om, got, ref)
+    print("autograd Eq. 3: max group error %.2e" % err)
+    assert err <= GRAD_BOUND
+    m.close()
+
+
+def test_autograd_linear_functional_matches_finite_differences(niv):
+    """dL/dtheta for L = sum w . E with random w: autograd through niv_backward against central
+    differences of the FP64 oracle's forward."""
+    spec = dict(MODEL_C0, levels=3, log2_T=8, base=3.0, growth=1.6, n_hidden=2, width=16)
+    m = niv.NIVModel(**spec)
+    g, _ = m.param_count()
+    params = init_params(g, m.layer_shapes(), seed=6, feat_range=0.5, bias_std=0.3).astype(np.float64)
+    om = oracle.Model(**spec)
+    n = 500
+    pos, nrm = uniform_queries(n, seed=7)
+    w = np.random.default_rng(8).standard_normal((n, 3))
+    mod = niv.NIVModule(m, params)
+    E = mod(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda())[:, :3]
+    (E * torch.from_numpy(w).float().cuda()).sum().backward()
+    got = mod.params.grad.cpu().numpy().astype(np.float64)
+    L = lambda p: float(np.sum(w * oracle.query(om, p, pos, nrm)))
+    rng = np.random.default_rng(9)
+    idx = np.concatenate([rng.choice(g, 30, replace=False), g + rng.choice(len(params) - g, 30, replace=False)])
+    h = 1e-6
+    fd = np.array([(L(params + h * np.eye(1, len(params), i)[0]) - L(params - h * np.eye(1, len(params), i)[0])) / (2 * h)
+                   for i in idx])
+    scale = np.abs(fd).max()
+    err = np.max(np.abs(got[idx] - fd)) / scale
+    print("autograd linear functional vs FD: %.2e of max |g| %.3g" % (err, scale))
+    assert err <= 1e-4
+    m.close()
+
+
+def test_identity_output_gradient_matches_oracle(niv):
+    spec = dict(MODEL_C0, log2_T=10, out_act=0)
+    m = niv.NIVModel(**spec)
+    g, _ = m.param_count()
+    params = init_params(g, m.layer_shapes(), seed=10, feat_range=0.3, bias_std=0.2)
+    m.set_params(params)
+    om = oracle.Model(**spec)
+    n = 2000
+    pos, nrm = uniform_queries(n, seed=11)
+    target = np.zeros((n, 4), np.float32)
+    target[:, :3] = np.random.default_rng(12).uniform(-1.0, 1.0, (n, 3))
+    dev = lambda a: torch.from_numpy(a).cuda()
+    loss = m.grad(dev(pos), dev(nrm), dev(target))
+    ref_loss, ref = oracle.loss_grad(om, params, pos, nrm, target[:, :3])
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    assert _groups_max_err(om, m.get_grads().astype(np.float64), ref) <= GRAD_BOUND
+    m.close()
