@@ -209,6 +209,16 @@ NIV_API int niv_grad(niv_handle h, const float* pos, const float* nrm, const flo
 NIV_API int niv_backward(niv_handle h, const float* pos, const float* nrm, const float* t, const float* grad_E,
                          int64_t n, const niv_query_params* params, niv_stream stream);
 
+/*
+ * Forward precision of niv_grad, niv_fit and niv_backward (config 2: "FP16 forward / FP32
+ * master weights").  NIV_FP32 (the default): FP32 throughout against the master
+ * parameters.  NIV_FP16: the forward is the FP16 path of niv_query -- grid values, weights
+ * and biases rounded to binary16 as they are read, the network input and every hidden
+ * activation rounded to binary16, FP32 sums -- and the gradient is that of this function
+ * taken straight through the roundings, applied to the FP32 master parameters.
+ */
+NIV_API int niv_set_train_forward(niv_handle h, int32_t precision);
+
 /* Copy the n gradient values of the last niv_grad to `out` (host or device).  Synchronises. */
 NIV_API int niv_get_grads(niv_handle h, float* out, int64_t n, niv_stream stream);
 

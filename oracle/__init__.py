@@ -102,7 +102,7 @@ def lib():
         L.orc_encode.argtypes = [P(Desc), vp, vp, i64, vp, vp, f, vp, vp, vp]
         L.orc_mlp.argtypes = [P(Desc), vp, vp, i64, vp]
         L.orc_query.argtypes = [P(Desc), vp, vp, vp, i64, vp, vp, f, vp]
-        L.orc_loss_grad.argtypes = [P(Desc), vp, vp, vp, vp, vp, i64, vp, vp, d, vp, vp]
+        L.orc_loss_grad.argtypes = [P(Desc), vp, vp, vp, vp, vp, i64, vp, vp, d, vp, vp, ctypes.c_int]
         L.orc_adam.argtypes = [vp, vp, vp, vp, i64, d, d, d, d, i64]
         L.orc_adam.restype = None
         L.orc_shade.argtypes = [vp, vp, vp, i64, vp]
@@ -247,15 +247,17 @@ def upsample_shade(pos4, nrm4, alb4, dir4, width, height, E_low, sub=2, power=8.
     return out
 
 
-def loss_grad(model, params, pos4, nrm4, target, aabb_min=(0, 0, 0), aabb_max=(1, 1, 1), t=None, eps=0.01):
-    """(loss, grad) of Eq. 3 averaged over samples and channels; grad has params' shape."""
+def loss_grad(model, params, pos4, nrm4, target, aabb_min=(0, 0, 0), aabb_max=(1, 1, 1), t=None, eps=0.01,
+              f16=False):
+    """(loss, grad) of Eq. 3 averaged over samples and channels; grad has params' shape.
+    f16: the FP16 forward path (pass binary16-rounded params), straight-through gradient."""
     params = _f64(params)
     g = np.zeros_like(params)
     loss = ctypes.c_double()
     tt = None if t is None else _f32(t)
     rc = lib().orc_loss_grad(ctypes.byref(model.cdesc()), _p(params), _p(_f32(pos4)), _p(_f32(nrm4)), _p(tt),
                              _p(_f64(target)), len(pos4), _p(_f32(aabb_min)), _p(_f32(aabb_max)), eps,
-                             ctypes.byref(loss), _p(g))
+                             ctypes.byref(loss), _p(g), int(bool(f16)))
     if rc:
         raise ValueError("orc_loss_grad failed")
     return loss.value, g

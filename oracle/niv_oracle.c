@@ -212,13 +212,15 @@ int64_t orc_mlp_param_count(const orc_desc* d)
 static double softplus(double z) { return (z > 0.0 ? z : 0.0) + log1p(exp(-fabs(z))); }
 static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
 
+double orc_f16(double x);
+
 /*
  * Network forward for one input vector x (length n_in).  Stores every layer's
  * pre-activation z_k (layer-major) and post-activation a_k when requested.
- * Returns E (out_dim values).
+ * Returns E (out_dim values).  f16: every hidden activation is rounded to binary16.
  */
 static void mlp_forward(const orc_desc* d, const double* mlp, const double* x, double* z_all, double* a_all,
-                        double* E)
+                        double* E, int f16)
 {
     double buf_a[ORC_MAX_WIDTH], buf_b[ORC_MAX_WIDTH];
     const double* in = x;
@@ -236,7 +238,7 @@ static void mlp_forward(const orc_desc* d, const double* mlp, const double* x, d
             for (int i = 0; i < k_in; ++i) z += W[(int64_t)o * k_in + i] * in[i];
             if (z_all) z_all[layer * ORC_MAX_WIDTH + o] = z;
             double a;
-            if (!last) a = z > 0.0 ? z : 0.0;                   /* ReLU */
+            if (!last) a = f16 ? orc_f16(z > 0.0 ? z : 0.0) : (z > 0.0 ? z : 0.0); /* ReLU */
             else a = d->out_act == 1 ? softplus(z) : z;         /* final layer */
             out[o] = a;
             if (a_all) a_all[layer * ORC_MAX_WIDTH + o] = a;
@@ -290,7 +292,7 @@ int orc_mlp(const orc_desc* d, const double* mlp, const double* x, int64_t n, do
 {
     const int n_in = orc_net_inputs(d);
 #pragma omp parallel for schedule(static)
-    for (int64_t q = 0; q < n; ++q) mlp_forward(d, mlp, x + q * n_in, NULL, NULL, E + q * d->out_dim);
+    for (int64_t q = 0; q < n; ++q) mlp_forward(d, mlp, x + q * n_in, NULL, NULL, E + q * d->out_dim, 0);
     return 0;
 }
 
@@ -315,7 +317,7 @@ int orc_query(const orc_desc* d, const double* params, const float* pos4, const 
         encode_point(d, &L, params, u, enc, NULL, NULL);
         net_input(d, enc, nrm4 + 4 * q, t, x);
         (void)n_in;
-        mlp_forward(d, mlp, x, NULL, NULL, E + q * d->out_dim);
+        mlp_forward(d, mlp, x, NULL, NULL, E + q * d->out_dim, 0);
     }
     return 0;
 }
@@ -326,11 +328,15 @@ int orc_query(const orc_desc* d, const double* params, const float* pos4, const 
  * the steps above.  The denominator is a constant (stop-gradient).  ReLU'(0) = 0.
  * Grid gradients sum over corners and samples (hash collisions add).
  * t4 (nullable) gives a per-sample time input for 4-D models.
+ * f16: the forward is the FP16 path (the caller passes parameters already rounded to
+ * binary16; the network input and the hidden activations are rounded here) and the
+ * gradient is taken straight through the roundings.  The ReLU derivative is 1 where the
+ * stored activation is positive.
  * grad must hold as many values as params and is overwritten.
  */
 int orc_loss_grad(const orc_desc* d, const double* params, const float* pos4, const float* nrm4,
                   const float* t_per_sample, const double* target, int64_t n, const float* aabb_min,
-                  const float* aabb_max, double eps, double* loss_out, double* grad)
+                  const float* aabb_max, double eps, double* loss_out, double* grad, int f16)
 {
     orc_layout_t L;
     if (fill_layout(d, &L)) return -1;
@@ -352,7 +358,9 @@ int orc_loss_grad(const orc_desc* d, const double* params, const float* pos4, co
         normalise(d, pos4 + 4 * q, aabb_min, aabb_max, tq, u);
         encode_point(d, &L, params, u, enc, ix, wc);
         net_input(d, enc, nrm4 + 4 * q, tq, x);
-        mlp_forward(d, mlp, x, z_all, a_all, E);
+        if (f16)
+            for (int i = 0; i < n_in; ++i) x[i] = orc_f16(x[i]);
+        mlp_forward(d, mlp, x, z_all, a_all, E, f16);
         /* dLoss/dE with the denominator held constant */
         double g_out[ORC_MAX_WIDTH], g_in[ORC_MAX_WIDTH + ORC_MAX_ENC];
         for (int c = 0; c < C; ++c) {
@@ -384,7 +392,7 @@ int orc_loss_grad(const orc_desc* d, const double* params, const float* pos4, co
             }
             if (layer > 0) { /* through the ReLU of the layer below */
                 for (int i = 0; i < k_in; ++i)
-                    g_out[i] = z_all[(layer - 1) * ORC_MAX_WIDTH + i] > 0.0 ? g_in[i] : 0.0;
+                    g_out[i] = a_all[(layer - 1) * ORC_MAX_WIDTH + i] > 0.0 ? g_in[i] : 0.0;
             }
         }
         /* g_in now holds dLoss/dx; scatter the encoding part into the tables */
@@ -623,7 +631,7 @@ int orc_fp8_act_amax(const orc_desc* d, const double* params, const float* pos4,
         normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
         encode_point(d, &L, params, u, enc, NULL, NULL);
         net_input(d, enc, nrm4 + 4 * q, t, x);
-        mlp_forward(d, mlp, x, z_all, a_all, E);
+        mlp_forward(d, mlp, x, z_all, a_all, E, 0);
         for (int i = 0; i < n_in; ++i) amax[0] = fabs(x[i]) > amax[0] ? fabs(x[i]) : amax[0];
         for (int l = 1; l < layers; ++l)
             for (int o = 0; o < d->width; ++o) {

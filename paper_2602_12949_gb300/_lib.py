@@ -74,6 +74,7 @@ _SIGNATURES = [
     ("niv_probe_query", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _I64, _I32, _VP, _I32, _I32, _VP]),
     ("niv_grad", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, ctypes.POINTER(QueryParams), _F, _VP, _VP]),
     ("niv_get_grads", ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    ("niv_set_train_forward", ctypes.c_int, [_VP, _I32]),
     ("niv_backward", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, ctypes.POINTER(QueryParams), _VP]),
     ("niv_set_grads", ctypes.c_int, [_VP, _VP, _I64, _VP]),
     ("niv_adam_step", ctypes.c_int, [_VP, _F, _F, _F, _F, _VP]),

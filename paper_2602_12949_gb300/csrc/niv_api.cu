@@ -469,6 +469,14 @@ int grad_common(niv_handle h, const float* pos, const float* nrm, const float* t
 }
 }  // namespace
 
+int niv_set_train_forward(niv_handle h, int32_t precision) {
+    if (!h) return niv_fail(NIV_ERR_ARG, "handle is NULL");
+    if (precision != NIV_FP32 && precision != NIV_FP16)
+        return niv_fail(NIV_ERR_UNSUPPORTED, "training forward precision must be NIV_FP32 or NIV_FP16");
+    h->train_f16 = precision == NIV_FP16;
+    return NIV_OK;
+}
+
 int niv_grad(niv_handle h, const float* pos, const float* nrm, const float* t, const float* target, int64_t n,
              const niv_query_params* params, float eps, double* loss_out, niv_stream stream) {
     return grad_common(h, pos, nrm, t, target, n, params, eps, false, loss_out, stream);

@@ -49,6 +49,7 @@ struct niv_model {
     int64_t stash_floats;
     double* loss_acc;        // device loss accumulator
     int infer_dirty;         // parameters changed on the device since the inference copies were built
+    int train_f16;           // training forward: FP16 path of the query (else FP32)
     // Host staging for niv_query_host.
     void* stage;
     size_t stage_bytes;

@@ -1,6 +1,7 @@
 // Training step of Sec. 4.5: relative-L2 loss (Eq. 3), hand-written backward pass and Adam.
 //
-// Three kernels per step, all FP32 against the FP32 master parameters:
+// Three kernels per step, FP32 against the FP32 master parameters (optionally with the FP16
+// forward of the query, see kModeF16Fwd):
 //   1. fwd_bwd_kernel (one thread per sample): encoding and network forward, the loss
 //      (E - y)^2 / (sg(E^2) + eps) averaged over samples and channels, and the backward
 //      pass through softplus, the output layer and every ReLU layer down to the network
@@ -22,8 +23,13 @@ constexpr int kMaxIn = 64;  // widest network input the training kernels take
 __device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
 
 // fwd_bwd_kernel mode bits: the target records hold dL/dE (vector-Jacobian product, no
-// loss); the output layer is the identity instead of softplus.
-constexpr int kModeVjp = 1, kModeIdentityOut = 2;
+// loss); the output layer is the identity instead of softplus; the forward runs the FP16
+// path of the query (grid values, weights and biases, the network input and the hidden
+// activations rounded to binary16; FP32 sums), and the backward is the gradient of that
+// function taken straight through the roundings, applied to the FP32 master parameters.
+constexpr int kModeVjp = 1, kModeIdentityOut = 2, kModeF16Fwd = 4;
+
+__device__ __forceinline__ float r16(float x) { return __half2float(__float2half_rn(x)); }
 
 // Row stride (floats) of stashed layer inputs: n_in rounded up to 4, or W.
 __host__ __device__ __forceinline__ int stash_stride(int k) { return (k + 3) & ~3; }
@@ -42,7 +48,8 @@ __global__ void __launch_bounds__(kT) fwd_bwd_kernel(GridArgs g, const float4* _
     float* s_w = smem;
     float* s_a = smem + ((n_mlp + 3) & ~3);   // [kMaxIn][kT] current layer input, then scratch
     float* s_b = s_a + kMaxIn * kT;           // [W][kT] current layer output
-    for (int i = threadIdx.x; i < n_mlp; i += kT) s_w[i] = params[n_grid + i];
+    const bool f16 = mode & kModeF16Fwd;
+    for (int i = threadIdx.x; i < n_mlp; i += kT) s_w[i] = f16 ? r16(params[n_grid + i]) : params[n_grid + i];
     __syncthreads();
 
     const int tid = threadIdx.x;
@@ -60,21 +67,35 @@ __global__ void __launch_bounds__(kT) fwd_bwd_kernel(GridArgs g, const float4* _
     // ---- forward: encoding ----
     for (int l = 0; l < g.levels; ++l) {
         float acc[F];
-        niv_encode_level<DIMS, F, float>(g, params, l, u, acc);
+        if (f16) {  // grid values rounded as they are gathered
+            constexpr int NC = 1 << DIMS;
+            uint32_t e[NC];
+            float wc[NC];
+            niv_level_corners<DIMS>(g, l, u, e, wc);
+            const float* tab = params + (size_t)g.offset[l] * F;
 #pragma unroll
-        for (int j = 0; j < F; ++j) s_a[(l * F + j) * kT + tid] = acc[j];
+            for (int j = 0; j < F; ++j) acc[j] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int j = 0; j < F; ++j) acc[j] = fmaf(wc[c], r16(tab[(size_t)e[c] * F + j]), acc[j]);
+        } else {
+            niv_encode_level<DIMS, F, float>(g, params, l, u, acc);
+        }
+#pragma unroll
+        for (int j = 0; j < F; ++j) s_a[(l * F + j) * kT + tid] = f16 ? r16(acc[j]) : acc[j];
     }
     for (int d = 0; d < 3 && g.pe_bands > 0; ++d)
         for (int b = 0; b < g.pe_bands; ++b) {
             float sv, cv;
             niv_pe_pair(u[d], b, sv, cv);
-            s_a[(LG + 2 * (d * g.pe_bands + b)) * kT + tid] = sv;
-            s_a[(LG + 2 * (d * g.pe_bands + b) + 1) * kT + tid] = cv;
+            s_a[(LG + 2 * (d * g.pe_bands + b)) * kT + tid] = f16 ? r16(sv) : sv;
+            s_a[(LG + 2 * (d * g.pe_bands + b) + 1) * kT + tid] = f16 ? r16(cv) : cv;
         }
-    s_a[(LF + 0) * kT + tid] = nv.x;
-    s_a[(LF + 1) * kT + tid] = nv.y;
-    s_a[(LF + 2) * kT + tid] = nv.z;
-    if (n_in > LF + 3) s_a[(LF + 3) * kT + tid] = u[3];
+    s_a[(LF + 0) * kT + tid] = f16 ? r16(nv.x) : nv.x;
+    s_a[(LF + 1) * kT + tid] = f16 ? r16(nv.y) : nv.y;
+    s_a[(LF + 2) * kT + tid] = f16 ? r16(nv.z) : nv.z;
+    if (n_in > LF + 3) s_a[(LF + 3) * kT + tid] = f16 ? r16(u[3]) : u[3];
 
     // stash layout per layer l (input of matrix l): [n][stride_l]; then dz_l: [n][W or 4]
     float* st = stash;
@@ -91,7 +112,7 @@ __global__ void __launch_bounds__(kT) fwd_bwd_kernel(GridArgs g, const float4* _
         for (int o = 0; o < W; ++o) {
             float z = bl[o];
             for (int i = 0; i < k_in; ++i) z = fmaf(w[o * k_in + i], s_a[i * kT + tid], z);
-            s_b[o * kT + tid] = fmaxf(z, 0.0f);
+            s_b[o * kT + tid] = f16 ? r16(fmaxf(z, 0.0f)) : fmaxf(z, 0.0f);
         }
         for (int o = 0; o < W; ++o) s_a[o * kT + tid] = s_b[o * kT + tid];
         w = bl + W;
@@ -281,7 +302,7 @@ int64_t niv_train_stash_floats(const niv_model* m, int64_t n) {
 
 int niv_train_grad(niv_model* m, const GridArgs& g, const float4* pos, const float4* nrm, const float* t,
                    const float4* target, int64_t n, float eps, bool vjp, cudaStream_t s) {
-    const int mode = vjp ? kModeVjp : 0;
+    const int mode = (vjp ? kModeVjp : 0) | (m->train_f16 ? kModeF16Fwd : 0);
     const int W = m->d.width, nh = m->d.n_hidden, n_in = m->n_in;
     if (n_in > kMaxIn) return niv_fail(NIV_ERR_UNSUPPORTED, "training needs a network input of <= 64 values");
     const int64_t need = niv_train_stash_floats(m, n);

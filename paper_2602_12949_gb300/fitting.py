@@ -15,14 +15,16 @@ from .model import mc_irradiance, compact_targets
 
 def train(model, scene, steps, batch, pool=1 << 18, spp=256, reuse=4, seed=0, lr=1e-2, beta1=0.9, beta2=0.99,
           adam_eps=1e-15, loss_eps=0.01, with_t=False, aabb_min=(-5.0, -5.0, -5.0), aabb_max=(5.0, 5.0, 5.0),
-          log_every=0, device="cuda"):
+          log_every=0, forward="fp32", device="cuda"):
     """Train `model` on indirect irradiance of `scene` for `steps` Adam steps.
 
     A fresh pool of `pool` candidates gets Monte Carlo targets (`spp` paths each);
     the kept samples are cut into batches of `batch`, and each pool serves `reuse`
-    passes.  Returns a dict with the loss history and the time spent per phase.
+    passes.  forward: "fp16" runs the FP16 path of the query in the forward (config 2), "fp32"
+    the FP32 one.  Returns a dict with the loss history and the time spent per phase.
     """
     from niv_inputs.samples import training_pool
+    model.set_train_forward(forward)
     blob = scene.blob()
     hist, t_mc, t_fit = [], 0.0, 0.0
     step, pool_id, index_base = 0, 0, 0

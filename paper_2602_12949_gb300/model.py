@@ -202,6 +202,11 @@ class NIVModel:
                              float(loss_eps), ctypes.byref(loss), _stream(stream)))
         return loss.value
 
+    def set_train_forward(self, precision):
+        """Forward precision of grad / fit / backward: "fp32" (default) or "fp16" (the FP16 path of
+        the query, straight-through gradients onto the FP32 master parameters)."""
+        check(lib().niv_set_train_forward(self._h, PRECISIONS[precision]))
+
     def backward(self, pos, nrm, grad_E, t=None, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), t_scalar=0.0,
                  stream=None):
         """Vector-Jacobian product: dL/dtheta for the upstream dL/dE (device float32 [n][4]

@@ -195,3 +195,55 @@ def test_identity_output_gradient_matches_oracle(niv):
     assert loss == pytest.approx(ref_loss, rel=1e-5)
     assert _groups_max_err(om, m.get_grads().astype(np.float64), ref) <= GRAD_BOUND
     m.close()
+
+
+FP16_FWD_GRAD_BOUND = 1e-3  # binary16 roundings decided from FP32 (GPU) and FP64 (oracle) sums may differ
+
+
+@pytest.mark.parametrize("spec", [dict(MODEL_C0, log2_T=10), dict(MODEL_C0, levels=6, feat=4, n_hidden=3, width=32)])
+def test_fp16_forward_gradient_matches_oracle(niv, spec):
+    """Config 2's FP16 forward: the gradient (straight through the roundings, onto the FP32
+    master parameters) matches the oracle's FP16 mode."""
+    m = niv.NIVModel(**spec)
+    g, _ = m.param_count()
+    params = init_params(g, m.layer_shapes(), seed=13, feat_range=0.3, bias_std=0.2)
+    m.set_params(params)
+    m.set_train_forward("fp16")
+    om = oracle.Model(**spec)
+    n = 3000
+    pos, nrm = uniform_queries(n, seed=14)
+    target = np.zeros((n, 4), np.float32)
+    target[:, :3] = np.random.default_rng(15).uniform(0.1, 2.0, (n, 3))
+    dev = lambda a: torch.from_numpy(a).cuda()
+    loss = m.grad(dev(pos), dev(nrm), dev(target))
+    ref_loss, ref = oracle.loss_grad(om, oracle.f16(params), pos, nrm, target[:, :3], f16=True)
+    _, ref32 = oracle.loss_grad(om, params, pos, nrm, target[:, :3])
+    got = m.get_grads().astype(np.float64)
+    err, err32 = _groups_max_err(om, got, ref), _groups_max_err(om, got, ref32)
+    print("fp16 forward: loss %.6g vs %.6g; max group error %.2e (vs the FP32 gradient %.2e)"
+          % (loss, ref_loss, err, err32))
+    assert loss == pytest.approx(ref_loss, rel=1e-4)
+    assert err <= FP16_FWD_GRAD_BOUND
+    assert err < err32  # it is the FP16 function's gradient, not the FP32 one
+    m.close()
+
+
+def test_fp16_forward_fit_reduces_loss(niv):
+    spec = dict(MODEL_C0, log2_T=12)
+    m = niv.NIVModel(**spec)
+    g, _ = m.param_count()
+    m.set_params(init_params(g, m.layer_shapes(), seed=16))
+    m.set_train_forward("fp16")
+    n = 1 << 14
+    pos, nrm = uniform_queries(n, seed=17)
+    target = np.zeros((n, 4), np.float32)
+    x = pos[:, :3].astype(np.float64)
+    target[:, :3] = (0.5 + 0.4 * np.sin(4.0 * x) * (nrm[:, :3] * 0.5 + 0.5)).astype(np.float32)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    dp, dn, dy = dev(pos), dev(nrm), dev(target)
+    first = m.fit(dp, dn, dy)
+    for _ in range(300):
+        last = m.fit(dp, dn, dy, want_loss=False)
+    last = m.fit(dp, dn, dy)
+    assert last < 0.1 * first
+    m.close()

@@ -152,3 +152,61 @@ def test_e4m3_matches_torch_float8():
     ref = torch.from_numpy(x.astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
     np.testing.assert_array_equal(oracle.e4m3(x.astype(np.float32).astype(np.float64)), ref)
     assert oracle.e4m3(np.array([1000.0, -500.0])).tolist() == [448.0, -448.0]
+
+
+# ---- the FP16 forward of training (config 2: FP16 forward, FP32 master weights) ----
+
+def _batch(n, seed):
+    from niv_inputs import uniform_queries
+    pos, nrm = uniform_queries(n, seed=seed)
+    y = np.random.default_rng(seed + 1).uniform(0.1, 2.0, (n, 3))
+    return pos, nrm, y
+
+
+def test_f16_loss_is_eq3_of_the_f16_path_forward():
+    """The loss of the FP16 mode is Eq. 3 evaluated on the FP16 path's forward (query_f16,
+    itself pinned to numpy's binary16 conversion)."""
+    from niv_inputs import init_params
+    m = oracle.Model(levels=4, log2_T=10, base=3.0, growth=1.6, width=16)
+    params = init_params(oracle.grid_value_count(m), oracle.layer_shapes(m), seed=1, feat_range=0.3, bias_std=0.2)
+    p16 = oracle.f16(params)
+    pos, nrm, y = _batch(300, 2)
+    loss, _ = oracle.loss_grad(m, p16, pos, nrm, y, f16=True)
+    E = oracle.query_f16(m, p16, pos, nrm)
+    assert loss == pytest.approx(np.mean((E - y) ** 2 / (E * E + 0.01)), rel=1e-13)
+
+
+def test_f16_gradient_equals_fp32_gradient_when_nothing_rounds():
+    """With grid values, inputs and weights that are dyadic (exact in binary16) and queries on
+    lattice vertices, every activation is exact in binary16, so the FP16 mode's gradient is
+    the FP32 gradient exactly."""
+    m = oracle.Model(levels=1, feat=2, log2_T=10, base=4.0, growth=1.0, n_hidden=2, width=16)
+    rng = np.random.default_rng(3)
+    g = oracle.grid_value_count(m)
+    grid = rng.integers(-4, 5, g) / 8.0
+    mlp = []
+    for (o, i) in oracle.layer_shapes(m):
+        mlp += [rng.integers(-2, 3, o * i) / 4.0, rng.integers(-2, 3, o) / 4.0]
+    params = np.concatenate([grid] + mlp)
+    assert np.array_equal(oracle.f16(params), params)
+    n = 64
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, :3] = rng.integers(0, 5, (n, 3)) / 4.0  # u N is an integer: each query sits on a vertex
+    nrm = np.zeros((n, 4), np.float32)
+    nrm[:, :3] = rng.integers(-2, 3, (n, 3)) / 2.0
+    y = rng.integers(1, 8, (n, 3)) / 4.0
+    l16, g16 = oracle.loss_grad(m, params, pos, nrm, y, f16=True)
+    l32, g32 = oracle.loss_grad(m, params, pos, nrm, y)
+    assert l16 == l32
+    assert np.array_equal(g16, g32)
+
+
+def test_f16_gradient_is_close_to_fp32_gradient():
+    from niv_inputs import init_params
+    m = oracle.Model(levels=6, log2_T=12, base=3.0, growth=1.6, width=32, n_hidden=2)
+    params = init_params(oracle.grid_value_count(m), oracle.layer_shapes(m), seed=4, feat_range=0.3, bias_std=0.2)
+    pos, nrm, y = _batch(2000, 5)
+    _, g16 = oracle.loss_grad(m, oracle.f16(params), pos, nrm, y, f16=True)
+    _, g32 = oracle.loss_grad(m, params, pos, nrm, y)
+    rel = np.abs(g16 - g32).max() / np.abs(g32).max()
+    assert 0.0 < rel < 2e-2
