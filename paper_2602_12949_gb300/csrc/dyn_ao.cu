@@ -9,11 +9,12 @@
 // the irradiance is scaled, E <- AO E, before shading.
 //
 // The triangles (world space, as posed for the frame) are put into a bounding-volume
-// hierarchy on the host: median split of the centroids along the widest axis, at most 4
-// triangles per leaf, nodes in depth-first order (left child next to its parent), bounds
-// padded by 1e-5 of the scene's extent.  One thread per record traverses it with a stack
-// (any hit ends the ray); records whose ray origin lies farther than R from the geometry's
-// bounds skip the rays (AO = 1).
+// hierarchy on the host: binned surface-area-heuristic splits of the centroids (16 bins per
+// axis), leaves of at most 4 triangles or where no split pays (up to 16), nodes in
+// depth-first order (left child next to its parent), bounds
+// padded by 1e-5 of the scene's extent.  One thread per record traverses it with a stack,
+// the child on the ray's side of the split first (any hit ends the ray); records whose ray
+// origin lies farther than R from every depth-3 node box skip the rays (AO = 1).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -21,12 +22,17 @@
 #include "niv_internal.cuh"
 #include "sampling.cuh"
 
+constexpr int kCullBoxes = 8;  // node boxes at depth 3: a record traces rays only within R of one
+
 struct niv_dyn {
     int device;
     int64_t n_tris, n_nodes;
-    float4* nodes;  // per node: (lo.xyz, a), (hi.xyz, b); leaf: a = first triangle, b = count; inner: a = right child, b = 0
-    float4* tris;   // per triangle: v0, e1 = v1 - v0, e2 = v2 - v0
-    float lo[3], hi[3];
+    // per node: (lo.xyz, a), (hi.xyz, b); leaf: a = first triangle, b = count > 0;
+    // inner: a = right child (the left child follows its parent), b = -(split axis + 1)
+    float4* nodes;
+    float4* tris;  // per triangle: v0, e1 = v1 - v0, e2 = v2 - v0
+    int n_cull;
+    float cull_lo[kCullBoxes][3], cull_hi[kCullBoxes][3];
 };
 
 namespace {
@@ -35,6 +41,11 @@ struct HostNode {
     float lo[3], hi[3];
     int32_t a, b;
 };
+
+inline float box_area(const float* lo, const float* hi) {
+    const float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+    return dx * dy + dy * dz + dz * dx;
+}
 
 struct Builder {
     const float* tri;  // [T][9]
@@ -77,26 +88,108 @@ struct Builder {
             nodes[me] = nd;
             return me;
         }
-        const int32_t mid = b + (e - b) / 2;
-        std::nth_element(order.begin() + b, order.begin() + mid, order.begin() + e, [&](int32_t x, int32_t y) {
-            return cen[3 * (int64_t)x + axis] < cen[3 * (int64_t)y + axis];
-        });
+        // binned surface-area heuristic: for 16 centroid bins per axis, the split whose two
+        // sides minimise area x count; a leaf when no split beats testing every triangle
+        constexpr int kBins = 16;
+        float best = INFINITY;
+        int best_axis = axis, best_bin = kBins / 2;
+        for (int k = 0; k < 3; ++k) {
+            if (!(chi[k] > clo[k])) continue;
+            const float scale = kBins / (chi[k] - clo[k]);
+            int cnt[kBins] = {0};
+            float blo[kBins][3], bhi[kBins][3];
+            for (int i = 0; i < kBins; ++i)
+                for (int c = 0; c < 3; ++c) {
+                    blo[i][c] = INFINITY;
+                    bhi[i][c] = -INFINITY;
+                }
+            for (int32_t i = b; i < e; ++i) {
+                const int64_t t = order[i];
+                const int bin = std::min(kBins - 1, (int)((cen[3 * t + k] - clo[k]) * scale));
+                ++cnt[bin];
+                for (int v = 0; v < 3; ++v)
+                    for (int c = 0; c < 3; ++c) {
+                        blo[bin][c] = std::min(blo[bin][c], tri[9 * t + 3 * v + c]);
+                        bhi[bin][c] = std::max(bhi[bin][c], tri[9 * t + 3 * v + c]);
+                    }
+            }
+            float right_area[kBins];
+            int right_cnt[kBins];
+            float rl[3] = {INFINITY, INFINITY, INFINITY}, rh[3] = {-INFINITY, -INFINITY, -INFINITY};
+            int rc = 0;
+            for (int i = kBins - 1; i > 0; --i) {
+                rc += cnt[i];
+                for (int c = 0; c < 3; ++c) {
+                    rl[c] = std::min(rl[c], blo[i][c]);
+                    rh[c] = std::max(rh[c], bhi[i][c]);
+                }
+                right_cnt[i] = rc;
+                right_area[i] = rc ? box_area(rl, rh) : 0.0f;
+            }
+            float ll[3] = {INFINITY, INFINITY, INFINITY}, lh[3] = {-INFINITY, -INFINITY, -INFINITY};
+            int lc = 0;
+            for (int i = 0; i < kBins - 1; ++i) {
+                lc += cnt[i];
+                for (int c = 0; c < 3; ++c) {
+                    ll[c] = std::min(ll[c], blo[i][c]);
+                    lh[c] = std::max(lh[c], bhi[i][c]);
+                }
+                if (lc == 0 || right_cnt[i + 1] == 0) continue;
+                const float cost = lc * box_area(ll, lh) + right_cnt[i + 1] * right_area[i + 1];
+                if (cost < best) {
+                    best = cost;
+                    best_axis = k;
+                    best_bin = i;
+                }
+            }
+        }
+        const float leaf_cost = (float)(e - b) * box_area(nd.lo, nd.hi);
+        if (!(best < INFINITY) || (e - b <= 16 && best >= leaf_cost)) {
+            nd.a = b;
+            nd.b = e - b;
+            nodes[me] = nd;
+            return me;
+        }
+        axis = best_axis;
+        const float scale = kBins / (chi[axis] - clo[axis]);
+        int32_t mid = (int32_t)(std::partition(order.begin() + b, order.begin() + e, [&](int32_t t) {
+                                    return std::min(kBins - 1, (int)((cen[3 * (int64_t)t + axis] - clo[axis]) * scale)) <=
+                                           best_bin;
+                                }) - order.begin());
+        if (mid == b || mid == e) {  // cannot happen for a split with both sides counted; median as a guard
+            mid = b + (e - b) / 2;
+            std::nth_element(order.begin() + b, order.begin() + mid, order.begin() + e, [&](int32_t x, int32_t y) {
+                return cen[3 * (int64_t)x + axis] < cen[3 * (int64_t)y + axis];
+            });
+        }
         build(b, mid, depth + 1);
         nd.a = build(mid, e, depth + 1);
-        nd.b = 0;
+        nd.b = -(axis + 1);
         nodes[me] = nd;
         return me;
     }
 };
 
+// Boxes of the nodes at depth 3 (or of shallower leaves): together they hold every triangle.
+void collect_cull(const std::vector<HostNode>& nodes, int32_t i, int depth, std::vector<int32_t>& out) {
+    const HostNode& n = nodes[(size_t)i];
+    if (depth == 3 || n.b > 0) {
+        out.push_back(i);
+        return;
+    }
+    collect_cull(nodes, i + 1, depth + 1, out);
+    collect_cull(nodes, n.a, depth + 1, out);
+}
+
 constexpr int kStack = 64;
 constexpr float kRayBias = 0.01f;
 
-// Slab test of the ray o + t d, t in [0, tmax], against a node box (inv: finite reciprocals of d).
-__device__ __forceinline__ bool box_hit(const float4& lo, const float4& hi, float3 o, float3 inv, float tmax) {
-    const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
-    const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
-    const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+// Slab test of the ray o + t d, t in [0, tmax], against a node box (inv: finite reciprocals of d,
+// oi = o * inv).  The box bounds are padded, so the FMA's rounding cannot lose a hit.
+__device__ __forceinline__ bool box_hit(const float4& lo, const float4& hi, float3 oi, float3 inv, float tmax) {
+    const float tx0 = fmaf(lo.x, inv.x, -oi.x), tx1 = fmaf(hi.x, inv.x, -oi.x);
+    const float ty0 = fmaf(lo.y, inv.y, -oi.y), ty1 = fmaf(hi.y, inv.y, -oi.y);
+    const float tz0 = fmaf(lo.z, inv.z, -oi.z), tz1 = fmaf(hi.z, inv.z, -oi.z);
     const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
     const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
     return tn <= tf;
@@ -124,19 +217,24 @@ __device__ bool any_hit(const float4* __restrict__ nodes, const float4* __restri
     const float3 inv = make_float3(1.0f / (fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x)),
                                    1.0f / (fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y)),
                                    1.0f / (fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z)));
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
     int stack[kStack];
     int sp = 0, node = 0;
     while (true) {
         const float4 lo = __ldg(nodes + 2 * node), hi = __ldg(nodes + 2 * node + 1);
-        if (box_hit(lo, hi, o, inv, tmax)) {
+        if (box_hit(lo, hi, oi, inv, tmax)) {
             const int a = __float_as_int(lo.w), b = __float_as_int(hi.w);
             if (b > 0) {
                 for (int i = a; i < a + b; ++i)
                     if (tri_hit(__ldg(tris + 3 * i), __ldg(tris + 3 * i + 1), __ldg(tris + 3 * i + 2), o, d, tmax))
                         return true;
             } else {
-                if (sp < kStack) stack[sp++] = a;  // right child later; the builder caps the depth at 60
-                node = node + 1;
+                // the child on the ray's side of the split first: an occluded ray meets its hit sooner
+                const int axis = -b - 1;
+                const float dir = axis == 0 ? d.x : (axis == 1 ? d.y : d.z);
+                const int near = dir >= 0.0f ? node + 1 : a, far = dir >= 0.0f ? a : node + 1;
+                if (sp < kStack) stack[sp++] = far;  // the builder caps the depth at 60
+                node = near;
                 continue;
             }
         }
@@ -151,10 +249,10 @@ struct AoArgs {
     const void* pos;
     const void* nrm;
     int64_t n;
-    int32_t in_f16, rays, e_f16;
+    int32_t in_f16, rays, e_f16, n_cull;
     float radius;
     uint32_t k0, k1;
-    float lo[3], hi[3];
+    float cull_lo[kCullBoxes][3], cull_hi[kCullBoxes][3];
     float* ao;
     void* E;
 };
@@ -166,11 +264,15 @@ __global__ void __launch_bounds__(128) ao_kernel(AoArgs a) {
     const float nl = sqrtf(nv.x * nv.x + nv.y * nv.y + nv.z * nv.z);
     const float3 n = make_float3(nv.x / nl, nv.y / nl, nv.z / nl);
     const float3 o = make_float3(p.x + kRayBias * n.x, p.y + kRayBias * n.y, p.z + kRayBias * n.z);
-    const float gx = fmaxf(fmaxf(a.lo[0] - o.x, o.x - a.hi[0]), 0.0f);
-    const float gy = fmaxf(fmaxf(a.lo[1] - o.y, o.y - a.hi[1]), 0.0f);
-    const float gz = fmaxf(fmaxf(a.lo[2] - o.z, o.z - a.hi[2]), 0.0f);
+    bool near = false;  // within R of a depth-3 node box (every triangle lies in one)
+    for (int c = 0; c < a.n_cull; ++c) {
+        const float gx = fmaxf(fmaxf(a.cull_lo[c][0] - o.x, o.x - a.cull_hi[c][0]), 0.0f);
+        const float gy = fmaxf(fmaxf(a.cull_lo[c][1] - o.y, o.y - a.cull_hi[c][1]), 0.0f);
+        const float gz = fmaxf(fmaxf(a.cull_lo[c][2] - o.z, o.z - a.cull_hi[c][2]), 0.0f);
+        near |= gx * gx + gy * gy + gz * gz <= a.radius * a.radius;
+    }
     int blocked = 0;
-    if (gx * gx + gy * gy + gz * gz <= a.radius * a.radius) {
+    if (near) {
         for (int j = 0; j < a.rays; ++j) {
             const uint4 u = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)(r >> 32), (uint32_t)j, 0xA0u), a.k0, a.k1);
             const float3 d = cosine_dir(n, u01(u.x), u01(u.y));
@@ -227,10 +329,14 @@ int niv_dyn_build(const float* tri9, int64_t n_tris, niv_dyn** out) {
     niv_dyn* d = new niv_dyn();
     d->n_tris = n_tris;
     d->n_nodes = (int64_t)B.nodes.size();
-    for (int k = 0; k < 3; ++k) {
-        d->lo[k] = lo[k] - B.pad;
-        d->hi[k] = hi[k] + B.pad;
-    }
+    std::vector<int32_t> cull;
+    collect_cull(B.nodes, 0, 0, cull);
+    d->n_cull = (int)cull.size();  // at most 2^3 = kCullBoxes
+    for (int c = 0; c < d->n_cull; ++c)
+        for (int k = 0; k < 3; ++k) {
+            d->cull_lo[c][k] = B.nodes[(size_t)cull[c]].lo[k];
+            d->cull_hi[c][k] = B.nodes[(size_t)cull[c]].hi[k];
+        }
     cudaError_t e = cudaGetDevice(&d->device);
     d->nodes = nullptr;
     d->tris = nullptr;
@@ -271,10 +377,12 @@ int niv_launch_ao(const niv_dyn* d, const void* pos, const void* nrm, int64_t n,
     a.radius = radius;
     a.k0 = (uint32_t)seed;
     a.k1 = (uint32_t)(seed >> 32);
-    for (int k = 0; k < 3; ++k) {
-        a.lo[k] = d->lo[k];
-        a.hi[k] = d->hi[k];
-    }
+    a.n_cull = d->n_cull;
+    for (int c = 0; c < d->n_cull; ++c)
+        for (int k = 0; k < 3; ++k) {
+            a.cull_lo[c][k] = d->cull_lo[c][k];
+            a.cull_hi[c][k] = d->cull_hi[c][k];
+        }
     a.ao = ao;
     a.E = E;
     ao_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
