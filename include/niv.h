@@ -74,6 +74,11 @@ typedef struct niv_model* niv_handle;
  * coordinate-major; the network input is then [those 6 * pe_bands values,
  * n.xyz].  Such models run in FP32 and FP16 (NIV_FP8 returns
  * NIV_ERR_UNSUPPORTED).  pe_bands = 0 for grid models.
+ *
+ * t_bands > 0 is Sec. 6's form of a higher-dimensional field: the grid stays 3-D and the
+ * scene parameter t (clamped to [0, 1]) enters the network frequency-encoded, as the
+ * pairs (sin(2^b pi t), cos(2^b pi t)) for b < t_bands after n.xyz; in_extra must be 3
+ * and dims 3.  FP32 and FP16 (NIV_FP8 returns NIV_ERR_UNSUPPORTED).
  */
 typedef struct niv_model_desc {
     int32_t dims;     /* 3, or 4 for a time-varying field (x, y, z, t) */
@@ -89,6 +94,7 @@ typedef struct niv_model_desc {
     int32_t out_act;  /* 0 identity, 1 softplus */
     uint32_t prime_t; /* odd hash constant of the 4th dimension */
     int32_t pe_bands; /* 0: hash grid; 1..16: frequency encoding, no grid */
+    int32_t t_bands;  /* 0: t raw (in_extra 4) or absent; 1..6: t frequency-encoded (Sec. 6) */
 } niv_model_desc;
 
 /*

@@ -50,7 +50,7 @@ class Desc(ctypes.Structure):
         ("log2_T", ctypes.c_int32), ("base", ctypes.c_double), ("growth", ctypes.c_double),
         ("n_hidden", ctypes.c_int32), ("width", ctypes.c_int32), ("in_extra", ctypes.c_int32),
         ("out_dim", ctypes.c_int32), ("out_act", ctypes.c_int32), ("prime_t", ctypes.c_uint32),
-        ("pe_bands", ctypes.c_int32),
+        ("pe_bands", ctypes.c_int32), ("t_bands", ctypes.c_int32),
     ]
 
 
@@ -70,11 +70,12 @@ class Model:
     out_act: int = 1
     prime_t: int = 0x9E3779B1
     pe_bands: int = 0  # > 0: frequency-encoded position (Table 1's models without grid levels)
+    t_bands: int = 0   # > 0: the scene parameter t frequency-encoded after n (Sec. 6)
 
     def cdesc(self):
         return Desc(self.dims, self.levels, self.feat, self.log2_T, self.base, self.growth,
                     self.n_hidden, self.width, self.in_extra, self.out_dim, self.out_act, self.prime_t,
-                    self.pe_bands)
+                    self.pe_bands, self.t_bands)
 
     @property
     def enc_dim(self):
@@ -82,7 +83,7 @@ class Model:
 
     @property
     def n_in(self):
-        return self.enc_dim + self.in_extra
+        return self.enc_dim + self.in_extra + 2 * self.t_bands
 
 
 def lib():

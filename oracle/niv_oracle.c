@@ -64,6 +64,7 @@ typedef struct {
     int32_t out_act;   /* 0 identity, 1 softplus */
     uint32_t prime_t;  /* hash constant of the 4th dimension */
     int32_t pe_bands;  /* > 0: frequency encoding of the position with that many bands (levels may be 0) */
+    int32_t t_bands;   /* > 0: the scene parameter enters as sin / cos of 2^b pi t after n (Sec. 6) */
 } orc_desc;
 
 typedef struct {
@@ -198,7 +199,7 @@ static void encode_point(const orc_desc* d, const orc_layout_t* L, const double*
 /* encoding values of one query: grid features, then frequency-encoding values */
 int orc_enc_dim(const orc_desc* d) { return d->levels * d->feat + 6 * d->pe_bands; }
 
-int orc_net_inputs(const orc_desc* d) { return orc_enc_dim(d) + d->in_extra; }
+int orc_net_inputs(const orc_desc* d) { return orc_enc_dim(d) + d->in_extra + 2 * d->t_bands; }
 
 /* number of network parameters (all layers, weights and biases) */
 int64_t orc_mlp_param_count(const orc_desc* d)
@@ -250,7 +251,7 @@ static void mlp_forward(const orc_desc* d, const double* mlp, const double* x, d
     }
 }
 
-/* assemble the network input of one query: [encoding, n.xyz, (t)] */
+/* assemble the network input of one query: [encoding, n.xyz, (t or its frequency encoding)] */
 static void net_input(const orc_desc* d, const double* enc, const float* nrm, float t, double* x)
 {
     int ne = orc_enc_dim(d);
@@ -258,8 +259,14 @@ static void net_input(const orc_desc* d, const double* enc, const float* nrm, fl
     x[ne + 0] = nrm[0];
     x[ne + 1] = nrm[1];
     x[ne + 2] = nrm[2];
-    /* the scene parameter enters clamped to [0, 1], as it does the grid's 4th axis */
-    if (d->in_extra == 4) x[ne + 3] = t < 0.0f ? 0.0 : (t > 1.0f ? 1.0 : (double)t);
+    /* the scene parameter enters clamped to [0, 1], as it does the grid's 4th axis; with
+     * t_bands > 0 (Sec. 6) as the pairs sin, cos of 2^b pi t instead */
+    const double tc = t < 0.0f ? 0.0 : (t > 1.0f ? 1.0 : (double)t);
+    if (d->in_extra == 4) x[ne + 3] = tc;
+    for (int b = 0; b < d->t_bands; ++b) {
+        x[ne + 3 + 2 * b] = sin(M_PI * ldexp(tc, b));
+        x[ne + 4 + 2 * b] = cos(M_PI * ldexp(tc, b));
+    }
 }
 
 /*

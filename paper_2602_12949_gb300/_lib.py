@@ -34,7 +34,7 @@ class ModelDesc(ctypes.Structure):
         ("log2_T", ctypes.c_int32), ("base", ctypes.c_double), ("growth", ctypes.c_double),
         ("n_hidden", ctypes.c_int32), ("width", ctypes.c_int32), ("in_extra", ctypes.c_int32),
         ("out_dim", ctypes.c_int32), ("out_act", ctypes.c_int32), ("prime_t", ctypes.c_uint32),
-        ("pe_bands", ctypes.c_int32),
+        ("pe_bands", ctypes.c_int32), ("t_bands", ctypes.c_int32),
     ]
 
 

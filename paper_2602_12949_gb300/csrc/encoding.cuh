@@ -24,6 +24,7 @@ struct GridArgs {
     uint32_t prime_t;
     uint32_t dense_mask;  // bit l set: level l is dense
     int32_t pe_bands;     // > 0: frequency encoding of the position (no grid levels)
+    int32_t t_bands;      // > 0: the scene parameter enters as sin / cos of 2^b pi t after n
     float aabb_min[3];
     float inv_ext[3];
     float t;

@@ -49,9 +49,12 @@ int validate_desc(const niv_model_desc* d) {
     if (d->width != 16 && d->width != 32 && d->width != 64)
         return niv_fail(NIV_ERR_UNSUPPORTED, "width must be 16, 32 or 64");
     if (d->in_extra != 3 && d->in_extra != 4) return niv_fail(NIV_ERR_ARG, "in_extra must be 3 or 4");
+    if (d->t_bands < 0 || d->t_bands > 6) return niv_fail(NIV_ERR_ARG, "t_bands must be in 0..6");
+    if (d->t_bands > 0 && (d->dims != 3 || d->in_extra != 3))
+        return niv_fail(NIV_ERR_ARG, "a frequency-encoded scene parameter needs dims = 3 and in_extra = 3");
     if (d->out_dim != 3) return niv_fail(NIV_ERR_UNSUPPORTED, "out_dim must be 3");
     if (d->out_act != 0 && d->out_act != 1) return niv_fail(NIV_ERR_ARG, "out_act must be 0 or 1");
-    if (d->levels * d->feat + 6 * d->pe_bands + d->in_extra > NIV_MAX_IN)
+    if (d->levels * d->feat + 6 * d->pe_bands + d->in_extra + 2 * d->t_bands > NIV_MAX_IN)
         return niv_fail(NIV_ERR_UNSUPPORTED, "network input too wide");
     if (d->dims == 4 && (d->prime_t & 1u) == 0) return niv_fail(NIV_ERR_ARG, "prime_t must be odd");
     return NIV_OK;
@@ -158,6 +161,7 @@ GridArgs niv_grid_args(const niv_model* m, const niv_query_params* p) {
     g.dims = m->d.dims;
     g.levels = m->d.levels;
     g.pe_bands = m->d.pe_bands;
+    g.t_bands = m->d.t_bands;
     g.feat = m->d.feat;
     g.n_in = m->n_in;
     g.hash_mask = (uint32_t)((1ull << m->d.log2_T) - 1ull);
@@ -239,7 +243,7 @@ int niv_create(const niv_model_desc* desc, niv_handle* out) {
         off += m->entries[l];
     }
     m->total_entries = off;
-    m->n_in = desc->levels * desc->feat + 6 * desc->pe_bands + desc->in_extra;
+    m->n_in = desc->levels * desc->feat + 6 * desc->pe_bands + desc->in_extra + 2 * desc->t_bands;
     m->n_grid = off * desc->feat;
     int64_t n = 0, k = m->n_in;
     for (int h = 0; h < desc->n_hidden; ++h) {

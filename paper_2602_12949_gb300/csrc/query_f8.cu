@@ -423,7 +423,8 @@ int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s) {
 
 // Run the calibration pass over n records and set the activation scales (host side waits).
 int niv_calibrate_f8(niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
-    if (m->d.pe_bands > 0) return niv_fail(NIV_ERR_UNSUPPORTED, "the FP8 path takes grid models only");
+    if (m->d.pe_bands > 0 || m->d.t_bands > 0)
+        return niv_fail(NIV_ERR_UNSUPPORTED, "the FP8 path takes grid models with a raw t only");
     if (m->d.width > 64 || m->n_in > NIV_MAX_IN) return niv_fail(NIV_ERR_UNSUPPORTED, "calibration shape");
     const int nh = m->d.n_hidden;
     if (!m->fp8_amax) NIV_CUDA(cudaMalloc(&m->fp8_amax, sizeof(unsigned) * 8));
@@ -463,7 +464,8 @@ int niv_calibrate_f8(niv_model* m, const GridArgs& g, const IoArgs& io, cudaStre
 }
 
 int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
-    if (m->d.pe_bands > 0) return niv_fail(NIV_ERR_UNSUPPORTED, "the FP8 path takes grid models only");
+    if (m->d.pe_bands > 0 || m->d.t_bands > 0)
+        return niv_fail(NIV_ERR_UNSUPPORTED, "the FP8 path takes grid models with a raw t only");
     if (!m->fp8_ready) return niv_fail(NIV_ERR_ARG, "FP8 path needs niv_fp8_calibrate after the last niv_set_params");
     const F8Layout* lay = reinterpret_cast<const F8Layout*>(m->f8_layout);
     if (lay->K1 > 128) return niv_fail(NIV_ERR_UNSUPPORTED, "FP8 path needs a network input of <= 112 values");

@@ -55,7 +55,16 @@ __global__ void __launch_bounds__(kThreads) query_fp32_kernel(GridArgs g, IoArgs
         s_x[(LF + 0) * kThreads + k] = nv.x;
         s_x[(LF + 1) * kThreads + k] = nv.y;
         s_x[(LF + 2) * kThreads + k] = nv.z;
-        if (g.n_in > LF + 3) s_x[(LF + 3) * kThreads + k] = u[3];
+        if (g.t_bands > 0) {  // Sec. 6: the scene parameter frequency-encoded after n
+            for (int b = 0; b < g.t_bands; ++b) {
+                float sv, cv;
+                niv_pe_pair(u[3], b, sv, cv);
+                s_x[(LF + 3 + 2 * b) * kThreads + k] = sv;
+                s_x[(LF + 4 + 2 * b) * kThreads + k] = cv;
+            }
+        } else if (g.n_in > LF + 3) {
+            s_x[(LF + 3) * kThreads + k] = u[3];
+        }
 
         // ---- first hidden layer: x (shared column) -> h (registers) ----
         const float* W1t = s_w;  // [n_in][W]

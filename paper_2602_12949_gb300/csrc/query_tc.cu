@@ -251,14 +251,36 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             for (int l0 = 0; l0 < L; l0 += G)
                 *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, L, u);
         }
-        {   // [n.x, n.y, n.z, (t), 1, 0, ...]: the 1 multiplies the first layer's bias column
+        int tail = 8;  // columns written from col_extra on
+        if (g.t_bands == 0) {  // [n.x, n.y, n.z, (t), 1, 0, ...]: the 1 multiplies the first layer's bias column
             const bool has_t = g.n_in > (PE != 0 ? 0 : L * F) + 6 * g.pe_bands + 3;
             const uint32_t one = (uint32_t)__half_as_ushort(__float2half_rn(1.0f));
             uint4 c = make_uint4(pack_half2(nv.x, nv.y), has_t ? pack_half2(nv.z, u[3]) : (pack_half2(nv.z, 0.0f) & 0xFFFFu) | (one << 16), 0u, 0u);
             if (has_t) c.z = one;
             *reinterpret_cast<uint4*>(s_act + core_off(tid, lay.col_extra, K1)) = c;
+        } else {  // Sec. 6: [n.x, n.y, n.z, sin, cos of 2^b pi t (b < t_bands <= 6), 1, 0, ...]
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+            v[0] = nv.x;
+            v[1] = nv.y;
+            v[2] = nv.z;
+#pragma unroll
+            for (int b = 0; b < 6; ++b)
+                if (b < g.t_bands) niv_pe_pair(u[3], b, v[3 + 2 * b], v[4 + 2 * b]);
+#pragma unroll
+            for (int i = 3; i < 16; ++i)
+                if (i == 3 + 2 * g.t_bands) v[i] = 1.0f;
+            *reinterpret_cast<uint4*>(s_act + core_off(tid, lay.col_extra, K1)) =
+                make_uint4(pack_half2(v[0], v[1]), pack_half2(v[2], v[3]), pack_half2(v[4], v[5]), pack_half2(v[6], v[7]));
+            if (4 + 2 * g.t_bands > 8) {
+                *reinterpret_cast<uint4*>(s_act + core_off(tid, lay.col_extra + 8, K1)) =
+                    make_uint4(pack_half2(v[8], v[9]), pack_half2(v[10], v[11]), pack_half2(v[12], v[13]),
+                               pack_half2(v[14], v[15]));
+                tail = 16;
+            }
         }
-        for (int k = lay.col_extra + 8; k < K1; k += 8)
+        for (int k = lay.col_extra + tail; k < K1; k += 8)
             *reinterpret_cast<uint4*>(s_act + core_off(tid, k, K1)) = make_uint4(0u, 0u, 0u, 0u);
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -451,7 +473,7 @@ int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s) {
     TcLayout lay;
     memset(&lay, 0, sizeof lay);
     lay.col_extra = (LF + 7) & ~7;
-    lay.col_one = lay.col_extra + m->d.in_extra;
+    lay.col_one = lay.col_extra + m->d.in_extra + 2 * m->d.t_bands;
     lay.K1 = (lay.col_one + 1 + 15) & ~15;
     lay.W = W;
     lay.n_hidden = nh;

@@ -95,7 +95,16 @@ __global__ void __launch_bounds__(kT) fwd_bwd_kernel(GridArgs g, const float4* _
     s_a[(LF + 0) * kT + tid] = f16 ? r16(nv.x) : nv.x;
     s_a[(LF + 1) * kT + tid] = f16 ? r16(nv.y) : nv.y;
     s_a[(LF + 2) * kT + tid] = f16 ? r16(nv.z) : nv.z;
-    if (n_in > LF + 3) s_a[(LF + 3) * kT + tid] = f16 ? r16(u[3]) : u[3];
+    if (g.t_bands > 0) {  // Sec. 6: the scene parameter frequency-encoded after n
+        for (int b = 0; b < g.t_bands; ++b) {
+            float sv, cv;
+            niv_pe_pair(u[3], b, sv, cv);
+            s_a[(LF + 3 + 2 * b) * kT + tid] = f16 ? r16(sv) : sv;
+            s_a[(LF + 4 + 2 * b) * kT + tid] = f16 ? r16(cv) : cv;
+        }
+    } else if (n_in > LF + 3) {
+        s_a[(LF + 3) * kT + tid] = f16 ? r16(u[3]) : u[3];
+    }
 
     // stash layout per layer l (input of matrix l): [n][stride_l]; then dz_l: [n][W or 4]
     float* st = stash;

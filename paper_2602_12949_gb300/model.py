@@ -38,11 +38,11 @@ class NIVModel:
     """One Neural Irradiance Volume on the current CUDA device."""
 
     def __init__(self, dims=3, levels=16, feat=2, log2_T=17, base=16.0, growth=1.38, n_hidden=2, width=64,
-                 in_extra=None, out_dim=3, out_act=1, prime_t=0x9E3779B1, pe_bands=0):
+                 in_extra=None, out_dim=3, out_act=1, prime_t=0x9E3779B1, pe_bands=0, t_bands=0):
         if in_extra is None:
             in_extra = 4 if dims == 4 else 3
         self.desc = ModelDesc(dims, levels, feat, log2_T, float(base), float(growth), n_hidden, width, in_extra,
-                              out_dim, out_act, prime_t, pe_bands)
+                              out_dim, out_act, prime_t, pe_bands, t_bands)
         h = ctypes.c_void_p()
         check(lib().niv_create(ctypes.byref(self.desc), ctypes.byref(h)))
         self._h = h
@@ -64,7 +64,8 @@ class NIVModel:
 
     @property
     def n_in(self):
-        return self.desc.levels * self.desc.feat + 6 * self.desc.pe_bands + self.desc.in_extra
+        return (self.desc.levels * self.desc.feat + 6 * self.desc.pe_bands + self.desc.in_extra
+                + 2 * self.desc.t_bands)
 
     def param_count(self):
         g, m = ctypes.c_int64(), ctypes.c_int64()

@@ -150,3 +150,75 @@ def test_descriptor_rules(niv):
         niv.NIVModel(**dict(MODEL_PE16, dims=4, in_extra=4))
     with pytest.raises(niv.NivError):
         niv.NIVModel(**dict(MODEL_PE16, pe_bands=17))
+
+
+# ---- Sec. 6: a 3-D grid with the scene parameter frequency-encoded after n ----
+
+MODEL_SEC6 = dict(dims=3, levels=16, feat=2, log2_T=18, base=16.0, growth=1.38, n_hidden=3, width=64, t_bands=4)
+
+
+@pytest.mark.parametrize("t", [0.0, 0.3, 0.8125, 1.0])
+def test_time_encoded_model_matches_oracle(niv, t):
+    m = niv.NIVModel(**MODEL_SEC6)
+    g, _ = m.param_count()
+    params = init_params(g, m.layer_shapes(), seed=31, bias_std=0.1)
+    m.set_params(params)
+    om = oracle.Model(**MODEL_SEC6)
+    pos, nrm, _ = room_gbuffer(320, 180)
+    pos32, nrm32 = pos.astype(np.float32), nrm.astype(np.float32)
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=t)
+    p16 = params.astype(np.float16).astype(np.float64)
+    ref = oracle.query(om, params, pos32, nrm32, **kw)
+    ref16 = oracle.query(om, p16, pos32, nrm32, **kw)
+    ref16_path = oracle.query_f16(om, p16, pos32, nrm32, **kw)
+    dp, dn = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+    e32 = m.query(dp, dn, precision="fp32", out_dtype=torch.float32, image_width=320, **kw)[:, :3].cpu().numpy()
+    e16 = m.query(dp, dn, precision="fp16", out_dtype=torch.float32, image_width=320, **kw)[:, :3].cpu().numpy()
+    worst, agree = path_parity(e16, ref16_path)
+    fmt = rel_err(ref16_path, ref16)
+    print("t=%.4f: fp32 %.2e  fp16 vs path: max %.2e agree %.4f  vs network %.2e (format %.2e)"
+          % (t, rel_err(e32, ref), worst, agree, rel_err(e16, ref16), fmt))
+    assert rel_err(e32, ref) <= FP32_BOUND
+    assert worst <= FP16_PATH_NORM_BOUND and agree >= FP16_PATH_AGREE
+    assert rel_err(e16, ref16) <= max(FP16_BOUND, 1.5 * fmt)
+    m.close()
+
+
+def test_time_encoded_gradient_matches_oracle(niv):
+    spec = dict(MODEL_SEC6, levels=6, log2_T=12, n_hidden=2, width=32, t_bands=3)
+    m = niv.NIVModel(**spec)
+    g, _ = m.param_count()
+    params = init_params(g, m.layer_shapes(), seed=32, feat_range=0.3, bias_std=0.2)
+    m.set_params(params)
+    om = oracle.Model(**spec)
+    n = 3000
+    pos, nrm = uniform_queries(n, seed=33)
+    t = np.random.default_rng(34).random(n).astype(np.float32)
+    target = np.zeros((n, 4), np.float32)
+    target[:, :3] = np.random.default_rng(35).uniform(0.1, 2.0, (n, 3))
+    dev = lambda a: torch.from_numpy(a).cuda()
+    loss = m.grad(dev(pos), dev(nrm), dev(target), t=dev(t))
+    ref_loss, ref = oracle.loss_grad(om, params, pos, nrm, target[:, :3], t=t)
+    got = m.get_grads().astype(np.float64)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    off = oracle.grid_value_count(om)
+    assert np.max(np.abs(got[:off] - ref[:off])) <= GRAD_BOUND * np.abs(ref[:off]).max()
+    for (o, i) in oracle.layer_shapes(om):
+        for a, b in ((off, off + o * i), (off + o * i, off + o * i + o)):
+            assert np.max(np.abs(got[a:b] - ref[a:b])) <= GRAD_BOUND * np.abs(ref[a:b]).max()
+        off += o * i + o
+    m.close()
+
+
+def test_time_encoding_rules(niv):
+    with pytest.raises(niv.NivError):
+        niv.NIVModel(**dict(MODEL_SEC6, t_bands=7))
+    with pytest.raises(niv.NivError):
+        niv.NIVModel(**dict(MODEL_SEC6, dims=4, in_extra=4))
+    m = niv.NIVModel(**dict(MODEL_SEC6, levels=4, log2_T=10))
+    g, _ = m.param_count()
+    m.set_params(init_params(g, m.layer_shapes(), seed=1))
+    pos, nrm = uniform_queries(256, seed=1)
+    with pytest.raises(niv.NivError):
+        m.fp8_calibrate(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda())
+    m.close()

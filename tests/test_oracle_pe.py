@@ -209,3 +209,63 @@ def test_f16_path_rounds_inputs_and_hidden_activations():
     E = oracle.query_f16(m, _one_layer_net(m, w, 3.0), pos, nrm)
     hid = f16(np.maximum(w * f16(s), 0.0)) - f16(np.maximum(-w * f16(s), 0.0))
     np.testing.assert_allclose(E[:, 0], sp(3.0 * hid), rtol=1e-15, atol=0)
+
+
+# ---- Sec. 6: the scene parameter t frequency-encoded after n (3-D grid) ----
+
+def t_model(t_bands=4, n_hidden=1):
+    return oracle.Model(dims=3, levels=2, feat=2, log2_T=10, base=2.0, growth=2.0, n_hidden=n_hidden, width=16,
+                        t_bands=t_bands)
+
+
+def test_t_encoding_closed_forms_through_a_hand_network():
+    # unit 0 = +sin(2^b pi t), unit 1 = -sin(2^b pi t), unit 2 = +cos(2^b pi t), unit 3 = -cos(...)
+    # for band b = 2; outputs: sin, cos, 0 through softplus
+    m = t_model()
+    n_in = m.n_in
+    assert n_in == 2 * 2 + 3 + 8
+    b = 2
+    col_s = 2 * 2 + 3 + 2 * b  # after the 4 grid features and n.xyz
+    W1 = np.zeros((16, n_in))
+    W1[0, col_s], W1[1, col_s], W1[2, col_s + 1], W1[3, col_s + 1] = 1.0, -1.0, 1.0, -1.0
+    W2 = np.zeros((3, 16))
+    W2[0, 0], W2[0, 1], W2[1, 2], W2[1, 3] = 1.0, -1.0, 1.0, -1.0
+    grid = np.zeros(oracle.grid_value_count(m))
+    params = np.concatenate([grid, W1.ravel(), np.zeros(16), W2.ravel(), np.zeros(3)])
+    pos = np.full((1, 4), 0.3, np.float32)
+    nrm = np.zeros((1, 4), np.float32)
+    sp = lambda z: np.maximum(z, 0) + np.log1p(np.exp(-np.abs(z)))
+    for t, s4, c4 in ((0.0, 0.0, 1.0), (0.125, 1.0, 0.0), (0.25, 0.0, -1.0), (0.375, -1.0, 0.0),
+                      (1.7, 0.0, 1.0), (-0.3, 0.0, 1.0)):  # t is clamped to [0, 1]
+        E = oracle.query(m, params, pos, nrm, t=t)[0]
+        np.testing.assert_allclose(E[:2], sp(np.array([s4, c4])), atol=1e-15)
+        assert E[2] == np.log(2.0)
+
+
+def test_t_encoding_gradient_matches_finite_differences():
+    from niv_inputs import init_params
+    m = t_model(t_bands=3, n_hidden=2)
+    params = init_params(oracle.grid_value_count(m), oracle.layer_shapes(m), seed=21, feat_range=0.3,
+                         bias_std=0.2).astype(np.float64)
+    rng = np.random.default_rng(22)
+    pos = np.zeros((40, 4), np.float32)
+    pos[:, :3] = rng.random((40, 3))
+    nrm = np.zeros((40, 4), np.float32)
+    nrm[:, :3] = rng.standard_normal((40, 3))
+    t = rng.random(40).astype(np.float32)
+    y = rng.random((40, 3)) + 0.1
+    _, g = oracle.loss_grad(m, params, pos, nrm, y, t=t)
+
+    def frozen(p, den):
+        E = np.stack([oracle.query(m, p, pos[i:i + 1], nrm[i:i + 1], t=float(t[i]))[0] for i in range(40)])
+        return np.mean((E - y) ** 2 / den)
+
+    E0 = np.stack([oracle.query(m, params, pos[i:i + 1], nrm[i:i + 1], t=float(t[i]))[0] for i in range(40)])
+    den = E0 ** 2 + 0.01
+    h = 1e-6
+    for i in rng.choice(len(params), 25, replace=False):
+        p1, p0 = params.copy(), params.copy()
+        p1[i] += h
+        p0[i] -= h
+        fd = (frozen(p1, den) - frozen(p0, den)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9, (i, fd, g[i])
