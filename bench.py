@@ -46,11 +46,12 @@ def _args():
     ap.add_argument("--res", default="1080p", choices=["1080p", "4k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison and error checks")
-    ap.add_argument("--workload", default="config1", choices=["config1", "config3", "half", "sweep", "train"],
+    ap.add_argument("--workload", default="config1", choices=["config1", "config3", "half", "sweep", "train", "time"],
                     help="config1: the headline (config-1 model on the room frame); config3: the 4-D model at "
                          "--res with t from the seed; half: quarter-pixel query + upsampling and shading; "
                          "sweep: memory-error trade-off (hash table sizes against probes of equal memory); "
-                         "train: niv_fit steps at batch 2^18 and the Monte Carlo target rate (config 2)")
+                         "train: niv_fit steps at batch 2^18 and the Monte Carlo target rate (config 2); "
+                         "time: time-varying fields, config 3's 4-D grid against Sec. 6's frequency-encoded t")
     return ap.parse_args()
 
 
@@ -383,6 +384,33 @@ def run_sweep(a):
     print(json.dumps(line), flush=True)
 
 
+def run_time(a):
+    """Fields that change with t (Sec. 6; config 3): config 3's 4-D grid, Sec. 6's 3-D grid
+    (T = 2^18) with t frequency-encoded after n, and a static model without t, trained alike
+    (2000 steps) on the room whose emitter rotates with t; held-out MSE and the FP16 query
+    time on the 4K room frame."""
+    import torch
+    from paper_2602_12949_gb300 import fitting
+    from niv_inputs import room_scene
+    from niv_inputs.configs import MODEL_C3, room_gbuffer
+    torch.cuda.set_device(0)
+    pos, nrm, _ = room_gbuffer(3840, 2160)
+    frame = (torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda(), 3840)
+    sec6 = dict(dims=3, levels=16, feat=2, log2_T=18, base=16.0, growth=1.38, n_hidden=3, width=64)
+    shapes = {"4d_grid_config3": MODEL_C3, "3d_grid_t_bands4_sec6": dict(sec6, t_bands=4), "static_3d_no_t": sec6}
+    t0 = time.perf_counter()
+    rows = fitting.time_field_comparison(room_scene(0), shapes, steps=2000, frame=frame)
+    by = {r["model"]: r for r in rows}
+    line = {"metric": "held-out MSE of time-varying fields (config 3's 4-D grid vs Sec. 6's encoded t)",
+            "value": by["4d_grid_config3"]["mse"] / by["3d_grid_t_bands4_sec6"]["mse"],
+            "unit": "x (4-D grid MSE / Sec. 6 MSE)", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "dtype": "f16", "config": {"workload": "room scene seed 0, emitter rotating with t; 2000 Adam steps, "
+                                                   "batch 2^16, 128-spp targets with uniform per-sample t; held-out "
+                                                   "2^14 samples at 16 values of t, 4096 spp"},
+            "rows": rows, "seconds": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def run_train(a):
     """Config 2's training step: niv_fit (FP32 forward, hand-written backward, Adam) on batches
     of 2^18 samples of the room, timed with CUDA events over K steps after W warm-up steps;
@@ -455,6 +483,9 @@ def run_workload(a):
         return
     if a.workload == "train":
         run_train(a)
+        return
+    if a.workload == "time":
+        run_time(a)
         return
     from paper_2602_12949_gb300 import NIVModel, upsample_shade
     from niv_inputs import init_params

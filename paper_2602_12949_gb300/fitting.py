@@ -61,10 +61,13 @@ def train(model, scene, steps, batch, pool=1 << 18, spp=256, reuse=4, seed=0, lr
     return {"loss": hist, "seconds_mc": t_mc, "seconds_fit": t_fit, "pools": pool_id}
 
 
-def held_out(scene, n, spp, seed, with_t=False, device="cuda"):
-    """Evaluation samples (kept after culling) and their Monte Carlo reference E (float64, [k][3])."""
+def held_out(scene, n, spp, seed, with_t=False, t_levels=0, device="cuda"):
+    """Evaluation samples (kept after culling) and their Monte Carlo reference E (float64, [k][3]).
+    t_levels > 0: sample i takes t = ((i mod t_levels) + 1/2) / t_levels instead of a uniform t."""
     from niv_inputs.samples import training_pool
     x4, n4, t = training_pool(scene, n, seed=seed, with_t=with_t)
+    if with_t and t_levels > 0:
+        t = ((np.arange(len(t)) % t_levels + 0.5) / t_levels).astype(np.float32)
     dx, dn = torch.from_numpy(x4).to(device), torch.from_numpy(n4).to(device)
     dt = torch.from_numpy(t).to(device) if t is not None else None
     E, keep = mc_irradiance(scene.blob(), dx, dn, spp, seed=seed + 77, mode="indirect", t=dt, index_base=1 << 40)
@@ -117,4 +120,51 @@ def memory_error_sweep(scene, log2_Ts, shape, steps=2000, batch=1 << 16, pool=1 
         rows.append({"log2_T": int(lt), "mb": nbytes / 1e6, "niv_mse": niv[0], "niv_rel": niv[1],
                      "probes_per_axis": P, "probe_mb": grid.nbytes / 1e6, "probe_mse": probe[0],
                      "probe_rel": probe[1], "probe_rt_mse": probe_rt[0], "probe_rt_rel": probe_rt[1]})
+    return rows
+
+
+def time_field_comparison(scene, shapes, steps=2000, batch=1 << 16, pool=1 << 18, spp=128, reuse=2,
+                          held=(1 << 14, 4096), seed=1, aabb_min=(-5.0, -5.0, -5.0), aabb_max=(5.0, 5.0, 5.0),
+                          frame=None, device="cuda"):
+    """Fields that change with a scene parameter t (Sec. 6; config 3): every model in `shapes`
+    (name -> NIVModel keyword arguments) is trained on samples with a uniform per-sample t of
+    `scene` (its rotating emitter moves with t) and scored on the same held-out (x, n, t)
+    samples.  frame (optional (pos, nrm, width) device records): the FP16 query time of each
+    model on it at t = 0.5.  Returns one row per model: FP16 memory, MSE, relative MSE, ms."""
+    import torch
+    from niv_inputs import init_params
+    from .model import NIVModel
+    hx, hn, hE, ht = held_out(scene, held[0], held[1], seed=199, with_t=True, t_levels=16, device=device)
+    rows = []
+    for name, shape in shapes.items():
+        m = NIVModel(**shape)
+        g, nm = m.param_count()
+        m.set_params(init_params(g, m.layer_shapes(), seed=0))
+        train(m, scene, steps=steps, batch=batch, pool=pool, spp=spp, reuse=reuse, seed=seed, with_t=True,
+              aabb_min=aabb_min, aabb_max=aabb_max, device=device)
+        E = torch.empty((hx.shape[0], 4), dtype=torch.float32, device=hx.device)
+        # the query takes one t per call: evaluate the held-out samples grouped by their 16 t values
+        order = torch.argsort(ht)
+        hts = ht[order].cpu().numpy()
+        for t in np.unique(hts):
+            sel = order[torch.from_numpy(np.nonzero(hts == t)[0]).to(hx.device)]
+            E[sel] = m.query(hx[sel].contiguous(), hn[sel].contiguous(), precision="fp16", out_dtype=torch.float32,
+                             aabb_min=aabb_min, aabb_max=aabb_max, t=float(t))
+        mse, rel = errors(E, hE)
+        row = {"model": name, "mb": 2 * (g + nm) / 1e6, "mse": mse, "rel_mse": rel}
+        if frame is not None:
+            fp, fn, fw = frame
+            out = torch.empty((fp.shape[0], 4), dtype=torch.float16, device=fp.device)
+            for _ in range(3):
+                m.query(fp, fn, out=out, aabb_min=aabb_min, aabb_max=aabb_max, t=0.5, image_width=fw)
+            torch.cuda.synchronize()
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            for _ in range(10):
+                m.query(fp, fn, out=out, aabb_min=aabb_min, aabb_max=aabb_max, t=0.5, image_width=fw)
+            e0.record()
+            torch.cuda.synchronize()
+            row["fp16_ms_per_frame"] = s0.elapsed_time(e0) / 10
+        rows.append(row)
+        m.close()
     return rows
