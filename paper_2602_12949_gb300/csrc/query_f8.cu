@@ -34,20 +34,23 @@ __host__ __device__ __forceinline__ uint32_t core_off8(int r, int k, int K) {
 
 struct F8Layout {
     int32_t K1, W, n_hidden, col_extra;  // col_extra: tile column of n.x (features end before it)
-    uint32_t w1, wh, wo, scal, total;    // byte offsets; scal = FP32 block [c | qmul | biases]
+    uint32_t w1, wh, wo, scal, total;    // byte offsets; scal = FP32 block [c | qmul | biases | cq | bq]
 };
 
-__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
-    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-    return (lo & 0xFFFFu) | (hi << 16);
+// E4M3 codes of max(lo, 0) (low byte) and max(hi, 0) (high byte), rounded to nearest with
+// saturation to +-448.
+__device__ __forceinline__ uint32_t e4m3x2_relu(float lo, float hi) {
+    uint16_t r;
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
-__device__ __forceinline__ uint4 e4m3x16(const float* v, float mul) {
-    return make_uint4(e4m3x4(v[0] * mul, v[1] * mul, v[2] * mul, v[3] * mul),
-                      e4m3x4(v[4] * mul, v[5] * mul, v[6] * mul, v[7] * mul),
-                      e4m3x4(v[8] * mul, v[9] * mul, v[10] * mul, v[11] * mul),
-                      e4m3x4(v[12] * mul, v[13] * mul, v[14] * mul, v[15] * mul));
+// The same for 16 values, in order.
+__device__ __forceinline__ uint4 e4m3x16_relu(const float* v) {
+    return make_uint4(e4m3x2_relu(v[0], v[1]) | (e4m3x2_relu(v[2], v[3]) << 16),
+                      e4m3x2_relu(v[4], v[5]) | (e4m3x2_relu(v[6], v[7]) << 16),
+                      e4m3x2_relu(v[8], v[9]) | (e4m3x2_relu(v[10], v[11]) << 16),
+                      e4m3x2_relu(v[12], v[13]) | (e4m3x2_relu(v[14], v[15]) << 16));
 }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
@@ -154,6 +157,8 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
     const float* s_c = reinterpret_cast<const float*>(s_net + lay.scal);  // acc -> z multipliers
     const float* s_q = s_c + (nh + 1);                                   // 1 / s_a per matrix input
     const float* s_b = s_q + (nh + 1);                                   // biases
+    const float* s_cq = s_b + nh * W + 4;                                // hidden layers: c / s_a'
+    const float* s_bq = s_cq + nh;                                       // hidden layers: b / s_a'
     const int L = LV > 0 ? LV : g.levels, LF = L * F;
     constexpr int G = 16 / F;  // levels per 16-byte chunk of E4M3 inputs
     uint32_t phase = 0;
@@ -208,14 +213,14 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
             }
             phase ^= 1u;
             tc::fence_after_sync();
-            const float c = s_c[layer], qn = s_q[layer + 1];
-            const float* bias = s_b + layer * W;
+            const float cq = s_cq[layer];
+            const float* bq = s_bq + layer * W;
             for (int ch = 0; ch < W / 16; ++ch) {
                 float v[16];
                 tc::tmem_ld16(tmem_row + (uint32_t)(ch * 16), v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = fmaxf(fmaf(v[j], c, bias[ch * 16 + j]), 0.0f);
-                *reinterpret_cast<uint4*>(s_act + core_off8(tid, ch * 16, W)) = e4m3x16(v, qn);
+                for (int j = 0; j < 16; ++j) v[j] = fmaf(v[j], cq, bq[ch * 16 + j]);
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, ch * 16, W)) = e4m3x16_relu(v);
             }
             tc::fence_async_smem();
             tc::fence_before_sync();
@@ -378,7 +383,8 @@ int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s) {
     lay.wh = up(lay.w1 + (uint32_t)(W * lay.K1));
     lay.wo = up(lay.wh + (uint32_t)((nh - 1) * W * W));
     lay.scal = up(lay.wo + (uint32_t)(kNO * W));
-    lay.total = up(lay.scal + (uint32_t)((2 * (nh + 1) + nh * W + 4) * 4));
+    // [c (nh+1) | 1/s_a (nh+1) | biases (nh W + 3, padded to + 4) | c / s_a' (nh) | b / s_a' (nh W)]
+    lay.total = up(lay.scal + (uint32_t)((2 * (nh + 1) + nh * W + 4 + nh + nh * W) * 4));
     static_assert(sizeof(F8Layout) <= sizeof(((niv_model*)0)->f8_layout), "layout slot too small");
     std::vector<uint8_t> buf(lay.total, 0);
     float* c = reinterpret_cast<float*>(&buf[lay.scal]);
@@ -407,6 +413,15 @@ int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s) {
         c[l] = (float)(sw * (double)m->fp8_sact[l]);
         qm[l] = (float)(1.0 / (double)m->fp8_sact[l]);
         k_in = n_out;
+    }
+    // hidden layers' epilogue in one FMA: (acc c + b) / s_a' with the next input scale s_a' a
+    // power of two, so c / s_a' and b / s_a' are exact and fma(acc, c / s_a', b / s_a') equals
+    // the rounded (acc c + b) scaled
+    float* cq = bias + nh * W + 4;
+    float* bq = cq + nh;
+    for (int l = 0; l < nh; ++l) {
+        cq[l] = c[l] * qm[l + 1];
+        for (int r = 0; r < W; ++r) bq[l * W + r] = bias[l * W + r] * qm[l + 1];
     }
     memcpy(m->f8_layout, &lay, sizeof lay);
     if (m->mlp_f8_bytes < lay.total) {
