@@ -46,12 +46,17 @@ def _args():
     ap.add_argument("--res", default="1080p", choices=["1080p", "4k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison and error checks")
-    ap.add_argument("--workload", default="config1", choices=["config1", "config3", "half", "sweep", "train", "time"],
+    ap.add_argument("--workload", default="config1",
+                    choices=["config1", "config3", "half", "sweep", "train", "time", "config2"],
                     help="config1: the headline (config-1 model on the room frame); config3: the 4-D model at "
                          "--res with t from the seed; half: quarter-pixel query + upsampling and shading; "
                          "sweep: memory-error trade-off (hash table sizes against probes of equal memory); "
                          "train: niv_fit steps at batch 2^18 and the Monte Carlo target rate (config 2); "
-                         "time: time-varying fields, config 3's 4-D grid against Sec. 6's frequency-encoded t")
+                         "time: time-varying fields, config 3's 4-D grid against Sec. 6's frequency-encoded t; "
+                         "config2: the training schedule of config 2 (see --train-steps, --spp)")
+    ap.add_argument("--train-steps", type=int, default=5000, help="config2: Adam steps")
+    ap.add_argument("--spp", type=int, default=1024, help="config2: Monte Carlo paths per training target")
+    ap.add_argument("--reuse", type=int, default=1, help="config2: passes over each pool of targets")
     return ap.parse_args()
 
 
@@ -115,23 +120,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _profiled_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if the
-    kernel sources are unchanged since that capture; else None."""
+def _profiled_record():
+    """DRAM bytes and warp instructions per launch of the fused kernel from the committed ncu
+    summary, if the kernel sources are unchanged since that capture; else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "niv_query_fp16_1080p.md")
     srcs = ["query_tc.cu", "encoding.cuh", "tc_ptx.cuh"]  # the kernel and every device helper it includes
     try:
         text = open(path).read()
         rec = dict(l.split(":", 1) for l in text.splitlines()
-                   if l.startswith(("traffic_bytes_per_launch:", "source_sha256_16:")))
+                   if l.startswith(("traffic_bytes_per_launch:", "source_sha256_16:",
+                                    "warp_instructions_per_launch:")))
         h = hashlib.sha256()
         for f in srcs:
             with open(os.path.join(ROOT, "paper_2602_12949_gb300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
         if h.hexdigest()[:16] != rec["source_sha256_16"].strip():
             return None
-        return int(rec["traffic_bytes_per_launch"].strip())
+        return {"traffic": int(rec["traffic_bytes_per_launch"].strip()),
+                "instructions": int(rec["warp_instructions_per_launch"].strip())}
     except Exception:
         return None
 
@@ -384,6 +391,51 @@ def run_sweep(a):
     print(json.dumps(line), flush=True)
 
 
+def run_config2(a):
+    """Config 2: niv_fit on the room (sky + rotating-free emitter at t = 0) with the FP16 forward and
+    FP32 master weights, batch 2^18, --train-steps Adam steps at lr 1e-2, targets from the GPU
+    Monte Carlo integrator (INDIRECT, --spp paths) on pools of 2^20 candidates (80% volume, 20%
+    surface, culled), each pool serving --reuse passes; then the held-out MSE against 4096-spp
+    references beside the SH probe grid of the same memory, with and without ray-traced
+    visibility."""
+    import torch
+    from paper_2602_12949_gb300 import NIVModel, ProbeGrid, fitting
+    from niv_inputs import init_params, room_scene
+    from niv_inputs.configs import MODEL_C1, ROOM_MIN, ROOM_MAX
+    torch.cuda.set_device(0)
+    scene = room_scene(0)
+    m = NIVModel(**MODEL_C1)
+    g, nm = m.param_count()
+    m.set_params(init_params(g, m.layer_shapes(), seed=0))
+    t0 = time.perf_counter()
+    info = fitting.train(m, scene, steps=a.train_steps, batch=1 << 18, pool=1 << 20, spp=a.spp, reuse=a.reuse,
+                         seed=1, log_every=500, forward="fp16")
+    train_s = time.perf_counter() - t0
+    hx, hn, hE, _ = fitting.held_out(scene, 1 << 16, 4096, seed=99)
+    q = dict(out_dtype=torch.float32, aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)
+    niv = {p: fitting.errors(m.query(hx, hn, precision=p, **q), hE) for p in ("fp16", "fp32")}
+    nbytes = 2 * (g + nm)
+    P = int((nbytes / 54.0) ** (1.0 / 3.0))
+    grid = ProbeGrid((P,) * 3, ROOM_MIN, ROOM_MAX)
+    grid.bake(scene.blob(), rays=4096, seed=3)
+    probe = fitting.errors(grid.query(hx, hn, out_dtype=torch.float32), hE)
+    probe_rt = fitting.errors(grid.query(hx, hn, out_dtype=torch.float32, scene_blob=scene.blob()), hE)
+    line = {"metric": "config 2: held-out MSE of the trained NIV vs the same-memory SH probe grid",
+            "value": probe[0] / niv["fp16"][0], "unit": "x (probe MSE / NIV FP16 MSE)", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f16 forward, f32 master weights",
+            "config": {"workload": "config2: room scene seed 0 (uniform sky through the skylight + sphere emitter), "
+                                   "config-1 model (6.81 MB FP16), batch 2^18, lr 1e-2, Adam (0.9, 0.99, 1e-15), "
+                                   "pools of 2^20 candidates", "steps": a.train_steps, "spp": a.spp,
+                       "reuse": a.reuse, "held_out": "2^16 samples, 4096-spp references"},
+            "niv_mse_fp16": niv["fp16"][0], "niv_rel_mse_fp16": niv["fp16"][1], "niv_mse_fp32": niv["fp32"][0],
+            "probe_grid": "%d^3 (%.2f MB)" % (P, grid.nbytes / 1e6), "probe_mse": probe[0], "probe_rel_mse": probe[1],
+            "probe_rt_mse": probe_rt[0], "probe_rt_rel_mse": probe_rt[1], "loss": info["loss"],
+            "seconds_monte_carlo": info["seconds_mc"], "seconds_fit": info["seconds_fit"], "pools": info["pools"],
+            "seconds_total": train_s}
+    print(json.dumps(line), flush=True)
+    m.close()
+
+
 def run_time(a):
     """Fields that change with t (Sec. 6; config 3): config 3's 4-D grid, Sec. 6's 3-D grid
     (T = 2^18) with t frequency-encoded after n, and a static model without t, trained alike
@@ -486,6 +538,9 @@ def run_workload(a):
         return
     if a.workload == "time":
         run_time(a)
+        return
+    if a.workload == "config2":
+        run_config2(a)
         return
     from paper_2602_12949_gb300 import NIVModel, upsample_shade
     from niv_inputs import init_params
@@ -652,11 +707,19 @@ def main():
     mean_ms = statistics.mean(ms)
     flop = FLOP_PER_QUERY["c1"] * npx
     achieved = flop / (mean_ms * 1e-3) / 1e12
-    traffic = _profiled_traffic() if (a.precision == "fp16" and a.res == "1080p") else None
+    prof = _profiled_record() if (a.precision == "fp16" and a.res == "1080p") else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["tensor"], "unit": "TFLOP/s",
-                "frac": achieved / peaks["tensor"], "traffic": traffic,
+                "frac": achieved / peaks["tensor"], "traffic": prof["traffic"] if prof else None,
                 "peak_source": "%s bf16 burst (fp16 dense rate equal)" % peaks["src"],
                 "hbm_achieved_gbs": GBUF_BYTES_PER_QUERY * npx / (mean_ms * 1e-3) / 1e9}
+    if prof:
+        # encoding-aware bound: the kernel's warp instructions (ncu) issued at one per cycle on
+        # each of the 4 schedulers of every SM, at the SM clock sampled during the timed steps
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk_mhz = clk.summary().get("sm_mhz") or clk.summary().get("sm_max_mhz") or 2070.0
+        issue_ms = prof["instructions"] / (sms * 4 * clk_mhz * 1e6) * 1e3
+        roofline["issue_bound"] = {"ms": issue_ms, "frac": issue_ms / mean_ms, "warp_instructions": prof["instructions"],
+                                   "sm_mhz": clk_mhz}
 
     cpu = None
     errs = {}
