@@ -173,9 +173,19 @@ NIV_API int niv_query(niv_handle h, const void* pos, const void* nrm, int64_t n,
               niv_stream stream);
 
 /*
- * niv_query for HOST buffers (pageable or pinned): copies pos/nrm to a
- * handle-owned device staging area, runs the query, copies E back and
- * synchronises `stream` before returning.
+ * niv_query for HOST buffers (pageable or pinned); results are those of niv_query,
+ * bit for bit, and `stream` is synchronised before returning.
+ *  - Page-locked buffers that the GPU can address (cudaHostAlloc, torch pin_memory;
+ *    16-byte aligned): one query reads the records from host memory and writes E to
+ *    out_E directly (over NVLink-C2C on Grace systems), with no staging copies.
+ *  - Other memory: pos/nrm are copied to a handle-owned device staging area and E
+ *    back.  Calls of more than 131072 records are split into up to 32 chunks of whole
+ *    128-record tiles (whole 8-row bands of the image when image_width > 0), about
+ *    two waves of the FP16 kernel each, whose host-to-device copy, query and
+ *    device-to-host copy run on three streams at once (two copy streams owned by the
+ *    handle, ordered after the work already queued on `stream`).
+ * Environment: NIV_HOST_MODE=1 forces the staged path; NIV_HOST_CHUNKS=k sets the
+ * chunk count of the staged path.
  */
 NIV_API int niv_query_host(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
                    const niv_query_params* params, void* out_E, int32_t dtype_out, int32_t precision,

@@ -96,49 +96,54 @@ __device__ __forceinline__ uint32_t niv_vertex_index(bool dense, uint32_t stride
     return h & mask;
 }
 
-// Corner entries and multilinear weights of level l at normalised coordinate u
-// (Sec. 4.1), with the per-corner work factored: one cell per axis, per-axis index
-// terms (dense strides or hash products) combined per corner, weights as products
-// of per-axis factors.  Corner c has offset bit d along dimension d.
+// Multilinear weights of the 2^d corners from the per-axis fractions w1 (Sec. 4.1):
+// products of per-axis factors (1 - w1, w1); corner c has offset bit d along dimension d.
 template <int DIMS>
-__device__ __forceinline__ void niv_level_corners(const GridArgs& g, int l, const float* u, uint32_t* e,
-                                                  float* wc) {
+__device__ __forceinline__ void niv_level_weights(const float* w1, float* wc) {
+    constexpr int NC = 1 << DIMS;
+    float w0[DIMS];
+#pragma unroll
+    for (int d = 0; d < DIMS; ++d) w0[d] = 1.0f - w1[d];
+    // Products in pairs on the packed FP32 pipe: each lane is an ordinary FP32 product,
+    // so the weights are those of the scalar formulas.
+    const float2 wy = make_float2(w0[1], w1[1]), wx = make_float2(w0[0], w1[0]);
+    float2 wh[NC / 4];  // wh[q] = (w_y0 * w_rest_q, w_y1 * w_rest_q)
+    wh[0] = __fmul2_rn(wy, make_float2(w0[2], w0[2]));
+    wh[1] = __fmul2_rn(wy, make_float2(w1[2], w1[2]));
+    if (DIMS == 4) {
+        const float2 t0 = make_float2(w0[DIMS - 1], w0[DIMS - 1]), t1 = make_float2(w1[DIMS - 1], w1[DIMS - 1]);
+        wh[2 % (NC / 4)] = __fmul2_rn(wh[0], t1);
+        wh[3 % (NC / 4)] = __fmul2_rn(wh[1], t1);
+        wh[0] = __fmul2_rn(wh[0], t0);
+        wh[1] = __fmul2_rn(wh[1], t0);
+    }
+#pragma unroll
+    for (int q = 0; q < NC / 4; ++q) {
+        const float2 a = __fmul2_rn(wx, make_float2(wh[q].x, wh[q].x));
+        const float2 b = __fmul2_rn(wx, make_float2(wh[q].y, wh[q].y));
+        wc[4 * q] = a.x;
+        wc[4 * q + 1] = a.y;
+        wc[4 * q + 2] = b.x;
+        wc[4 * q + 3] = b.y;
+    }
+}
+
+// Corner entries of level l at normalised coordinate u and the per-axis fractions w1
+// (Sec. 4.1), with the per-corner work factored: one cell per axis, per-axis index terms
+// (dense strides or hash products) combined per corner.  Corner c has offset bit d along
+// dimension d.
+template <int DIMS>
+__device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, const float* u, uint32_t* e, float* w1) {
     constexpr int NC = 1 << DIMS;
     const int32_t N = g.res[l];
     const float fN = (float)N, fmax = (float)(N - 1);
     uint32_t ci[DIMS];
-    float w1[DIMS], w0[DIMS];
 #pragma unroll
     for (int d = 0; d < DIMS; ++d) {
         const float s = __fmul_rn(u[d], fN);
         const float fl = fminf(floorf(s), fmax);
         ci[d] = (uint32_t)(int)fl;
         w1[d] = __fsub_rn(s, fl);
-        w0[d] = 1.0f - w1[d];
-    }
-    {
-        // Products in pairs on the packed FP32 pipe: each lane is an ordinary FP32 product,
-        // so the weights are those of the scalar formulas.
-        const float2 wy = make_float2(w0[1], w1[1]), wx = make_float2(w0[0], w1[0]);
-        float2 wh[NC / 4];  // wh[q] = (w_y0 * w_rest_q, w_y1 * w_rest_q)
-        wh[0] = __fmul2_rn(wy, make_float2(w0[2], w0[2]));
-        wh[1] = __fmul2_rn(wy, make_float2(w1[2], w1[2]));
-        if (DIMS == 4) {
-            const float2 t0 = make_float2(w0[DIMS - 1], w0[DIMS - 1]), t1 = make_float2(w1[DIMS - 1], w1[DIMS - 1]);
-            wh[2 % (NC / 4)] = __fmul2_rn(wh[0], t1);
-            wh[3 % (NC / 4)] = __fmul2_rn(wh[1], t1);
-            wh[0] = __fmul2_rn(wh[0], t0);
-            wh[1] = __fmul2_rn(wh[1], t0);
-        }
-#pragma unroll
-        for (int q = 0; q < NC / 4; ++q) {
-            const float2 a = __fmul2_rn(wx, make_float2(wh[q].x, wh[q].x));
-            const float2 b = __fmul2_rn(wx, make_float2(wh[q].y, wh[q].y));
-            wc[4 * q] = a.x;
-            wc[4 * q + 1] = a.y;
-            wc[4 * q + 2] = b.x;
-            wc[4 * q + 3] = b.y;
-        }
     }
     if ((g.dense_mask >> l) & 1u) {
         const uint32_t S = (uint32_t)N + 1u, S2 = S * S;
@@ -181,6 +186,15 @@ __device__ __forceinline__ void niv_level_corners(const GridArgs& g, int l, cons
             e[2 * q + 1] = (x1 ^ hh[q]) & m;
         }
     }
+}
+
+// Corner entries and multilinear weights of level l at normalised coordinate u.
+template <int DIMS>
+__device__ __forceinline__ void niv_level_corners(const GridArgs& g, int l, const float* u, uint32_t* e,
+                                                  float* wc) {
+    float w1[DIMS];
+    niv_level_entries<DIMS>(g, l, u, e, w1);
+    niv_level_weights<DIMS>(w1, wc);
 }
 
 // Raw feature words of the corners: F features of type TabT per entry.

@@ -91,6 +91,13 @@ void free_model(niv_model* m) {
     cudaFree(m->stash);
     cudaFree(m->loss_acc);
     cudaFree(m->stage);
+    if (m->host_pipe) {
+        for (int i = 0; i < 2; ++i) {
+            cudaStreamDestroy(m->host_copy[i]);
+            cudaEventDestroy(m->host_join[i]);
+            for (int c = 0; c < NIV_HOST_CHUNKS_MAX; ++c) cudaEventDestroy(m->host_ev[i][c]);
+        }
+    }
     delete m;
 }
 
@@ -357,19 +364,135 @@ int niv_query(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t
     }
 }
 
+namespace {
+// Streams and events of the pipelined host query, created once per handle.
+int host_pipe_init(niv_model* h) {
+    if (h->host_pipe) return NIV_OK;
+    for (int i = 0; i < 2; ++i) {
+        NIV_CUDA(cudaStreamCreateWithFlags(&h->host_copy[i], cudaStreamNonBlocking));
+        NIV_CUDA(cudaEventCreateWithFlags(&h->host_join[i], cudaEventDisableTiming));
+        for (int c = 0; c < NIV_HOST_CHUNKS_MAX; ++c)
+            NIV_CUDA(cudaEventCreateWithFlags(&h->host_ev[i][c], cudaEventDisableTiming));
+    }
+    h->host_pipe = 1;
+    return NIV_OK;
+}
+
+// Chunking of one host query: `count` chunks of `per` records (the last one shorter).
+struct HostChunks {
+    int64_t per;
+    int count;
+};
+
+// Chunks of whole tiles (whole 8-row bands of 16 x 8-pixel tiles for images) of about two
+// waves of the tensor-core kernel (8 warpgroups on every SM), at least 65,536 records
+// each and at most NIV_HOST_CHUNKS_MAX of them; NIV_HOST_CHUNKS sets the count instead.
+HostChunks host_chunks(int64_t n, int64_t W) {
+    const int64_t granule = W > 0 ? 8 * W : 128;  // records of one band / one tile
+    const int64_t granule_tiles = W > 0 ? (W + 15) / 16 : 1;
+    const int64_t granules = (n + granule - 1) / granule;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t per_g = (2 * 8 * (int64_t)sms + granule_tiles / 2) / granule_tiles;  // granules per chunk
+    const int forced = niv_env_int("NIV_HOST_CHUNKS", 0);
+    if (forced > 0) per_g = (granules + forced - 1) / forced;
+    const int64_t min_g = (65536 + granule - 1) / granule;
+    if (per_g < min_g) per_g = min_g;
+    if (per_g < 1) per_g = 1;
+    if ((granules + per_g - 1) / per_g > NIV_HOST_CHUNKS_MAX) per_g = (granules + NIV_HOST_CHUNKS_MAX - 1) / NIV_HOST_CHUNKS_MAX;
+    HostChunks c;
+    c.per = per_g * granule;
+    c.count = (int)((n + c.per - 1) / c.per);
+    return c;
+}
+
+// Queue the chunked pipeline: host->device copies on host_copy[0], queries on `s`,
+// device->host copies on host_copy[1], ordered after the work already queued on `s` and
+// joined back into it.  All copies in and queries are queued before the first copy out,
+// so that a copy out (which can hold the calling thread with pageable memory) never holds
+// up the queueing of later chunks.
+int host_pipeline(niv_model* h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
+                  const niv_query_params* params, void* out_E, int32_t dtype_out, int32_t precision,
+                  cudaStream_t s, const HostChunks& ch) {
+    const size_t rin = dtype_in == NIV_F16 ? 8 : 16, rout = dtype_out == NIV_F16 ? 8 : 16;
+    const size_t a_in = ((size_t)n * rin + 255) & ~(size_t)255;
+    char* base = (char*)h->stage;
+    cudaStream_t up = h->host_copy[0], down = h->host_copy[1];
+    NIV_CUDA(cudaEventRecord(h->host_join[0], s));
+    NIV_CUDA(cudaStreamWaitEvent(up, h->host_join[0], 0));
+    for (int c = 0; c < ch.count; ++c) {
+        const int64_t r0 = c * ch.per, m = n - r0 < ch.per ? n - r0 : ch.per;
+        char* dpos = base + r0 * rin;
+        char* dnrm = base + a_in + r0 * rin;
+        NIV_CUDA(cudaMemcpyAsync(dpos, (const char*)pos + r0 * rin, m * rin, cudaMemcpyHostToDevice, up));
+        NIV_CUDA(cudaMemcpyAsync(dnrm, (const char*)nrm + r0 * rin, m * rin, cudaMemcpyHostToDevice, up));
+        NIV_CUDA(cudaEventRecord(h->host_ev[0][c], up));
+        NIV_CUDA(cudaStreamWaitEvent(s, h->host_ev[0][c], 0));
+        int rc = niv_query(h, dpos, dnrm, m, dtype_in, params, base + 2 * a_in + r0 * rout, dtype_out, precision,
+                           (niv_stream)s);
+        if (rc) return rc;
+        NIV_CUDA(cudaEventRecord(h->host_ev[1][c], s));
+    }
+    for (int c = 0; c < ch.count; ++c) {
+        const int64_t r0 = c * ch.per, m = n - r0 < ch.per ? n - r0 : ch.per;
+        NIV_CUDA(cudaStreamWaitEvent(down, h->host_ev[1][c], 0));
+        NIV_CUDA(cudaMemcpyAsync((char*)out_E + r0 * rout, base + 2 * a_in + r0 * rout, m * rout,
+                                 cudaMemcpyDeviceToHost, down));
+    }
+    NIV_CUDA(cudaEventRecord(h->host_join[1], down));
+    NIV_CUDA(cudaStreamWaitEvent(s, h->host_join[1], 0));
+    return NIV_OK;
+}
+
+// Device address of page-locked host memory that kernels may load and store directly
+// (over NVLink-C2C on Grace systems, PCIe elsewhere); nullptr for other memory.
+void* mapped_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+}  // namespace
+
+// Page-locked host buffers that the GPU can address are read and written by the query
+// kernel itself (over NVLink-C2C on Grace systems): one launch, no staging copies.  Other
+// host memory is split into chunks of whole tiles (whole 8-row bands of the image when
+// image_width > 0) that flow through three engines at once: the host->device copy of
+// chunk c+1, the query of chunk c and the device->host copy of chunk c-1 overlap, so a
+// call costs about the slowest of the three plus one chunk of each of the others.
 int niv_query_host(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
                    const niv_query_params* params, void* out_E, int32_t dtype_out, int32_t precision,
                    niv_stream stream) {
-    if (!h) return niv_fail(NIV_ERR_ARG, "handle is NULL");
+    if (!h || !params) return niv_fail(NIV_ERR_ARG, "handle or params is NULL");
     if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
     if (n == 0) return NIV_OK;
     if (!pos || !nrm || !out_E) return niv_fail(NIV_ERR_ARG, "NULL record pointer");
+    if ((dtype_in != NIV_F32 && dtype_in != NIV_F16) || (dtype_out != NIV_F32 && dtype_out != NIV_F16))
+        return niv_fail(NIV_ERR_ARG, "record dtype must be NIV_F32 or NIV_F16");
+    if (params->image_width < 0) return niv_fail(NIV_ERR_ARG, "image_width < 0");
     int rc = check_device(h);
     if (rc) return rc;
-    const size_t in_b = (size_t)n * (dtype_in == NIV_F16 ? 8 : 16);
-    const size_t out_b = (size_t)n * (dtype_out == NIV_F16 ? 8 : 16);
-    const size_t a_in = (in_b + 255) & ~(size_t)255, need = 2 * a_in + out_b;
     cudaStream_t s = (cudaStream_t)stream;
+    // NIV_HOST_MODE: 0 (default) direct where possible, 1 always the chunked pipeline
+    if (niv_env_int("NIV_HOST_MODE", 0) == 0) {
+        const void* dpos = mapped_host(pos);
+        const void* dnrm = mapped_host(nrm);
+        void* dout = mapped_host(out_E);
+        if (dpos && dnrm && dout && aligned16(dpos) && aligned16(dnrm) && aligned16(dout)) {
+            rc = niv_query(h, dpos, dnrm, n, dtype_in, params, dout, dtype_out, precision, stream);
+            if (rc) {
+                cudaStreamSynchronize(s);
+                return rc;
+            }
+            NIV_CUDA(cudaStreamSynchronize(s));
+            return NIV_OK;
+        }
+    }
+    const size_t rin = dtype_in == NIV_F16 ? 8 : 16, rout = dtype_out == NIV_F16 ? 8 : 16;
+    const size_t a_in = ((size_t)n * rin + 255) & ~(size_t)255, need = 2 * a_in + (size_t)n * rout;
     if (h->stage_bytes < need) {
         NIV_CUDA(cudaStreamSynchronize(s));
         cudaFree(h->stage);
@@ -378,12 +501,15 @@ int niv_query_host(niv_handle h, const void* pos, const void* nrm, int64_t n, in
         NIV_CUDA(cudaMalloc(&h->stage, need));
         h->stage_bytes = need;
     }
-    char* base = (char*)h->stage;
-    NIV_CUDA(cudaMemcpyAsync(base, pos, in_b, cudaMemcpyHostToDevice, s));
-    NIV_CUDA(cudaMemcpyAsync(base + a_in, nrm, in_b, cudaMemcpyHostToDevice, s));
-    rc = niv_query(h, base, base + a_in, n, dtype_in, params, base + 2 * a_in, dtype_out, precision, stream);
+    rc = host_pipe_init(h);
     if (rc) return rc;
-    NIV_CUDA(cudaMemcpyAsync(out_E, base + 2 * a_in, out_b, cudaMemcpyDeviceToHost, s));
+    rc = host_pipeline(h, pos, nrm, n, dtype_in, params, out_E, dtype_out, precision, s,
+                       host_chunks(n, params->image_width));
+    if (rc) {
+        for (int i = 0; i < 2; ++i) cudaStreamSynchronize(h->host_copy[i]);
+        cudaStreamSynchronize(s);
+        return rc;
+    }
     NIV_CUDA(cudaStreamSynchronize(s));
     return NIV_OK;
 }
@@ -780,3 +906,4 @@ int niv_shade(const void* albedo, const void* direct, const void* E, int64_t n, 
 }
 
 }  // extern "C"
+

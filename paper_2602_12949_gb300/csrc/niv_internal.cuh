@@ -15,6 +15,9 @@
 #include "niv.h"
 #include "encoding.cuh"
 
+// Most chunks niv_query_host splits a call into.
+#define NIV_HOST_CHUNKS_MAX 32
+
 struct niv_model {
     niv_model_desc d;
     int device;
@@ -53,6 +56,12 @@ struct niv_model {
     // Host staging for niv_query_host.
     void* stage;
     size_t stage_bytes;
+    // Copy streams (host->device, device->host), per-chunk events (inputs landed, outputs
+    // written) and join events of the pipelined niv_query_host, created on first use.
+    cudaStream_t host_copy[2];
+    cudaEvent_t host_ev[2][NIV_HOST_CHUNKS_MAX];
+    cudaEvent_t host_join[2];
+    int host_pipe;
 };
 
 // ---- error reporting (thread-local message) ----

@@ -28,6 +28,7 @@
 #include <cuda_fp8.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "niv_internal.cuh"
@@ -177,6 +178,7 @@ __device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const TabT* __r
 
 __device__ __forceinline__ void group_sync(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory"); }
 
+
 // kWG independent warpgroups per CTA; each owns a 128-row tile pipeline (activation tile,
 // mbarrier, named barrier, 64 TMEM columns) and all share the weights in shared memory.
 // LV > 0: the level count is a compile-time constant, so the level loop unrolls fully and
@@ -233,7 +235,6 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         const bool valid = r < io.n;
         const int64_t rr = valid ? walk.source(r, io) : 0;
         const float4 p = niv_load_rec(io.pos, rr, io.in_f16);
-        const float4 nv = niv_load_rec(io.nrm, rr, io.in_f16);
         float u[4];
         u[0] = niv_unit(p.x, g.aabb_min[0], g.inv_ext[0]);
         u[1] = niv_unit(p.y, g.aabb_min[1], g.inv_ext[1]);
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         // ---- 1. encoding -> FP16 input row, one 16-byte chunk per G levels ----
         if (PE != 0) {
             encode_pe<PE>(g, u, s_act, tid, K1);
-        } else if (LV > 0) {
+        } else if constexpr (LV > 0) {
 #pragma unroll
             for (int l0 = 0; l0 < LV; l0 += G)
                 *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, LV, u);
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             for (int l0 = 0; l0 < L; l0 += G)
                 *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, L, u);
         }
+        const float4 nv = niv_load_rec(io.nrm, rr, io.in_f16);  // read late: not live during the encoding
         int tail = 8;  // columns written from col_extra on
         if (g.t_bands == 0) {  // [n.x, n.y, n.z, (t), 1, 0, ...]: the 1 multiplies the first layer's bias column
             const bool has_t = g.n_in > (PE != 0 ? 0 : L * F) + 6 * g.pe_bands + 3;
@@ -392,38 +394,59 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
     auto kern = query_tc_f16_kernel<DIMS, F, LV, PE, __half>;
     const __half* grid = m->grid_f16;
     const size_t smem = tc_smem_bytes(*lay);
-    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0;
+    int dev = 0;
     NIV_CUDA(cudaGetDevice(&dev));
-    NIV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // Residency from the register and shared-memory budgets (the occupancy API reports a
-    // single CTA per SM for kernels that allocate tensor memory).
-    cudaFuncAttributes fa;
-    NIV_CUDA(cudaFuncGetAttributes(&fa, kern));
-    int smem_per_sm = 0, regs_per_sm = 0;
-    NIV_CUDA(cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    NIV_CUDA(cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
-    const int by_smem = smem_per_sm / (int)(smem + 1024);  // 1 KB per CTA reserved by the driver
-    const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 1;
-    const int by_regs = regs_per_sm / (kT * kWG * regs);
-    int per_sm = by_smem < by_regs ? by_smem : by_regs;
-    // TMEM is allocated in powers of two from 32 to 512 columns: round the CTA's need up.
-    uint32_t cols = 32u;
-    while (cols < (lay->W <= 32 ? 32u : 64u) * (uint32_t)kWG) cols <<= 1;
-    if (cols > 512u) return niv_fail(NIV_ERR_UNSUPPORTED, "too many warpgroups for tensor memory");
-    const int forced = niv_env_int("NIV_TC_BLOCKS_PER_SM", 0);
-    if (forced > 0) per_sm = forced;
-    if (per_sm > (int)(512 / cols)) per_sm = (int)(512 / cols);  // never oversubscribe TMEM
-    if (per_sm < 1) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core query kernel does not fit on an SM");
-    // Ask for just the shared memory the resident CTAs need: the rest of the SM's unified
-    // L1 / shared storage then serves as L1 cache for the feature gathers.
-    int carve = (int)((100 * (int64_t)per_sm * (int64_t)(smem + 1024) + smem_per_sm - 1) / smem_per_sm);
-    carve = niv_env_int("NIV_TC_CARVEOUT", carve);
-    if (carve > 100) carve = 100;
-    NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
-    if (niv_env_int("NIV_VERBOSE", 0))
-        fprintf(stderr, "niv: fp16 query: smem %zu B, regs %d, smem %d/SM, regs %d/SM, launching %d/SM, carveout %d%%\n",
-                smem, fa.numRegs, by_smem, by_regs, per_sm, carve);
+    if (dev < 0 || dev >= 64) return niv_fail(NIV_ERR_UNSUPPORTED, "device ordinal above 63");
+    // The launch configuration of this kernel instance on a device depends only on its
+    // shared-memory size: it is worked out with a dozen runtime queries on first use and
+    // reused after (the tuning variables NIV_TC_BLOCKS_PER_SM, NIV_TC_CARVEOUT and
+    // NIV_VERBOSE are read then).
+    static std::mutex mu;
+    static struct { size_t smem; int sms, per_sm; uint32_t cols; } conf[64];
+    int sms = 0, per_sm = 0;
+    uint32_t cols = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (conf[dev].smem != smem) {
+            NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            NIV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            // Residency from the register and shared-memory budgets (the occupancy API reports a
+            // single CTA per SM for kernels that allocate tensor memory).
+            cudaFuncAttributes fa;
+            NIV_CUDA(cudaFuncGetAttributes(&fa, kern));
+            int smem_per_sm = 0, regs_per_sm = 0;
+            NIV_CUDA(cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+            NIV_CUDA(cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+            const int by_smem = smem_per_sm / (int)(smem + 1024);  // 1 KB per CTA reserved by the driver
+            const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 1;
+            const int by_regs = regs_per_sm / (kT * kWG * regs);
+            per_sm = by_smem < by_regs ? by_smem : by_regs;
+            // TMEM is allocated in powers of two from 32 to 512 columns: round the CTA's need up.
+            cols = 32u;
+            while (cols < (lay->W <= 32 ? 32u : 64u) * (uint32_t)kWG) cols <<= 1;
+            if (cols > 512u) return niv_fail(NIV_ERR_UNSUPPORTED, "too many warpgroups for tensor memory");
+            const int forced = niv_env_int("NIV_TC_BLOCKS_PER_SM", 0);
+            if (forced > 0) per_sm = forced;
+            if (per_sm > (int)(512 / cols)) per_sm = (int)(512 / cols);  // never oversubscribe TMEM
+            if (per_sm < 1) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core query kernel does not fit on an SM");
+            // Ask for just the shared memory the resident CTAs need: the rest of the SM's unified
+            // L1 / shared storage then serves as L1 cache for the feature gathers.
+            int carve = (int)((100 * (int64_t)per_sm * (int64_t)(smem + 1024) + smem_per_sm - 1) / smem_per_sm);
+            carve = niv_env_int("NIV_TC_CARVEOUT", carve);
+            if (carve > 100) carve = 100;
+            NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+            if (niv_env_int("NIV_VERBOSE", 0))
+                fprintf(stderr, "niv: fp16 query: smem %zu B, regs %d, smem %d/SM, regs %d/SM, launching %d/SM, carveout %d%%\n",
+                        smem, fa.numRegs, by_smem, by_regs, per_sm, carve);
+            conf[dev].sms = sms;
+            conf[dev].per_sm = per_sm;
+            conf[dev].cols = cols;
+            conf[dev].smem = smem;
+        }
+        sms = conf[dev].sms;
+        per_sm = conf[dev].per_sm;
+        cols = conf[dev].cols;
+    }
     if (!status) status = niv_status_word();
     if (!status) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
     const int64_t tiles = niv_tile_count_host(io.n, io.image_width);

@@ -157,6 +157,62 @@ def test_query_host_matches_device_query(niv):
     m.close()
 
 
+@pytest.mark.parametrize("width,rows,n_extra,precision,rec", [(1000, 537, 0, "fp16", np.float16),
+                                                              (0, 0, 300001, "fp32", np.float32),
+                                                              (1920, 1080, 0, "fp16", np.float32)])
+def test_chunked_host_query_matches_device_query(niv, width, rows, n_extra, precision, rec):
+    # large calls are split into chunks of whole 8-row bands (or 128-record tiles) whose
+    # copies overlap the queries of their neighbours: the result must not change by a bit
+    m, params, om = make(niv, MODEL_C1, seed=4)
+    n = width * rows + n_extra
+    pos, nrm = uniform_queries(n, seed=5)
+    pos, nrm = pos.astype(rec), nrm.astype(rec)
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, image_width=width)
+    out_dt = torch.float16 if rec == np.float16 else torch.float32
+    dev = m.query(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda(), precision=precision, out_dtype=out_dt,
+                  **kw).cpu().numpy()
+    host = m.query_host(pos, nrm, precision=precision, **kw)
+    np.testing.assert_array_equal(host, dev)
+    m.close()
+
+
+@pytest.mark.parametrize("mode", ["0", "1"])
+def test_pinned_host_query_follows_buffer_contents_and_arguments(niv, mode, monkeypatch):
+    # page-locked buffers: mode 0 lets one query read and write host memory directly; mode 1
+    # stages them through device memory in overlapped chunks.  Each call must read the
+    # buffers' current contents, and new arguments (another output buffer, new parameters,
+    # another precision) must take effect.
+    monkeypatch.setenv("NIV_HOST_MODE", mode)
+    m, params, om = make(niv, MODEL_C1, seed=6)
+    W, H = 640, 360
+    n = W * H
+    pos, nrm = uniform_queries(n, seed=7)
+    hp = torch.from_numpy(pos.astype(np.float16)).pin_memory()
+    hn = torch.from_numpy(nrm.astype(np.float16)).pin_memory()
+    ho = torch.empty((n, 4), dtype=torch.float16).pin_memory()
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, image_width=W)
+
+    def device(**extra):
+        return m.query(hp.cuda(), hn.cuda(), precision="fp16", out_dtype=torch.float16, **dict(kw, **extra)).cpu()
+
+    for call in range(5):
+        if call == 3:  # new contents in the same buffers
+            hp.copy_(torch.from_numpy(uniform_queries(n, seed=8)[0].astype(np.float16)))
+        m.query_host(hp.numpy(), hn.numpy(), out=ho.numpy(), precision="fp16", **kw)
+        assert torch.equal(ho, device()), call
+    ho2 = torch.empty_like(ho).pin_memory()
+    m.query_host(hp.numpy(), hn.numpy(), out=ho2.numpy(), precision="fp16", **kw)
+    assert torch.equal(ho2, device())
+    g, _ = m.param_count()
+    m.set_params(init_params(g, m.layer_shapes(), seed=9))
+    for call in range(3):
+        m.query_host(hp.numpy(), hn.numpy(), out=ho.numpy(), precision="fp16", **kw)
+        assert torch.equal(ho, device()), call
+    m.query_host(hp.numpy(), hn.numpy(), out=ho.numpy(), precision="fp32", **kw)
+    assert torch.equal(ho, m.query(hp.cuda(), hn.cuda(), precision="fp32", out_dtype=torch.float16, **kw).cpu())
+    m.close()
+
+
 def test_shade_matches_oracle(niv):
     rng = np.random.default_rng(0)
     n = 100000 + 3
