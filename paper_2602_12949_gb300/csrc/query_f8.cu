@@ -37,6 +37,11 @@ struct F8Layout {
     uint32_t w1, wh, wo, scal, total;    // byte offsets; scal = FP32 block [c | qmul | biases | cq | bq]
 };
 
+// Float offset of b / s_a' inside the FP32 block at `scal`: after c (nh+1), 1/s_a (nh+1),
+// the biases (nh W + 3, padded to + 4) and c / s_a' (nh), rounded up to a multiple of 4 so
+// that the hidden epilogue loads it in 16-byte pieces.
+__host__ __device__ __forceinline__ int f8_bq_offset(int nh, int W) { return (2 * (nh + 1) + nh * W + 4 + nh + 3) & ~3; }
+
 // E4M3 codes of max(lo, 0) (low byte) and max(hi, 0) (high byte), rounded to nearest with
 // saturation to +-448.
 __device__ __forceinline__ uint32_t e4m3x2_relu(float lo, float hi) {
@@ -100,7 +105,8 @@ __device__ __forceinline__ uint4 encode_chunk8(const GridArgs& g, const __half* 
         if (F == 1) {
             wd[q >> 2] |= (e4m3x2(acc[0] * q0, 0.0f) & 0xFFu) << (8 * (q & 3));
         } else if (F == 2) {
-            const uint32_t h = e4m3x2(acc[0] * q0, acc[1 % F] * q0);
+            const float2 a = __fmul2_rn(make_float2(acc[0], acc[1 % F]), make_float2(q0, q0));
+            const uint32_t h = e4m3x2(a.x, a.y);
             wd[(q >> 1) & 3] |= (q & 1) ? (h << 16) : h;
         } else {
             wd[q & 3] = e4m3x2(acc[0] * q0, acc[1 % F] * q0) | (e4m3x2(acc[2 % F] * q0, acc[3 % F] * q0) << 16);
@@ -158,7 +164,7 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
     const float* s_q = s_c + (nh + 1);                                   // 1 / s_a per matrix input
     const float* s_b = s_q + (nh + 1);                                   // biases
     const float* s_cq = s_b + nh * W + 4;                                // hidden layers: c / s_a'
-    const float* s_bq = s_cq + nh;                                       // hidden layers: b / s_a'
+    const float* s_bq = s_c + f8_bq_offset(nh, W);                       // hidden layers: b / s_a'
     const int L = LV > 0 ? LV : g.levels, LF = L * F;
     constexpr int G = 16 / F;  // levels per 16-byte chunk of E4M3 inputs
     uint32_t phase = 0;
@@ -219,7 +225,12 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
                 float v[16];
                 tc::tmem_ld16(tmem_row + (uint32_t)(ch * 16), v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = fmaf(v[j], cq, bq[ch * 16 + j]);
+                for (int j = 0; j < 8; ++j) {  // packed pairs: each lane is the FMA fma(acc, c / s_a', b / s_a')
+                    const float2 r = __ffma2_rn(make_float2(v[2 * j], v[2 * j + 1]), make_float2(cq, cq),
+                                                reinterpret_cast<const float2*>(bq + ch * 16)[j]);
+                    v[2 * j] = r.x;
+                    v[2 * j + 1] = r.y;
+                }
                 *reinterpret_cast<uint4*>(s_act + core_off8(tid, ch * 16, W)) = e4m3x16_relu(v);
             }
             tc::fence_async_smem();
@@ -383,8 +394,8 @@ int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s) {
     lay.wh = up(lay.w1 + (uint32_t)(W * lay.K1));
     lay.wo = up(lay.wh + (uint32_t)((nh - 1) * W * W));
     lay.scal = up(lay.wo + (uint32_t)(kNO * W));
-    // [c (nh+1) | 1/s_a (nh+1) | biases (nh W + 3, padded to + 4) | c / s_a' (nh) | b / s_a' (nh W)]
-    lay.total = up(lay.scal + (uint32_t)((2 * (nh + 1) + nh * W + 4 + nh + nh * W) * 4));
+    // [c (nh+1) | 1/s_a (nh+1) | biases (nh W + 3, padded to + 4) | c / s_a' (nh) | pad | b / s_a' (nh W)]
+    lay.total = up(lay.scal + (uint32_t)((f8_bq_offset(nh, W) + nh * W) * 4));
     static_assert(sizeof(F8Layout) <= sizeof(((niv_model*)0)->f8_layout), "layout slot too small");
     std::vector<uint8_t> buf(lay.total, 0);
     float* c = reinterpret_cast<float*>(&buf[lay.scal]);
@@ -418,7 +429,7 @@ int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s) {
     // power of two, so c / s_a' and b / s_a' are exact and fma(acc, c / s_a', b / s_a') equals
     // the rounded (acc c + b) scaled
     float* cq = bias + nh * W + 4;
-    float* bq = cq + nh;
+    float* bq = c + f8_bq_offset(nh, W);
     for (int l = 0; l < nh; ++l) {
         cq[l] = c[l] * qm[l + 1];
         for (int r = 0; r < W; ++r) bq[l * W + r] = bias[l * W + r] * qm[l + 1];
