@@ -124,8 +124,9 @@ __device__ __forceinline__ void group_sync8(int wg) { asm volatile("bar.sync %0,
 
 // kWG warpgroups per CTA, persistent over 128-record tiles; each warpgroup owns an activation
 // tile, an mbarrier, a named barrier and its TMEM columns.  LV > 0: level count fixed at
-// compile time (the level loop unrolls).
-template <int DIMS, int F, int LV>
+// compile time (the level loop unrolls).  WT, KT, NHT > 0: network width, first-layer input
+// width and hidden-layer count fixed at compile time (layer and column loops unroll).
+template <int DIMS, int F, int LV, int WT = 0, int KT = 0, int NHT = 0>
 __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArgs io, const __half* __restrict__ grid16,
                                                                 const uint8_t* __restrict__ packed, F8Layout lay,
                                                                 int out_act, int64_t n_tiles, uint32_t tmem_cols,
@@ -134,7 +135,8 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);  // one per warpgroup
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + 64);
     uint8_t* s_net = smem + kHdr;
-    const int K1 = lay.K1, W = lay.W, nh = lay.n_hidden;
+    const int K1 = KT > 0 ? KT : lay.K1, W = WT > 0 ? WT : lay.W, nh = NHT > 0 ? NHT : lay.n_hidden;
+    const int col_extra = LV > 0 ? ((LV * F + 15) & ~15) : lay.col_extra;  // column of n.x
     const uint32_t act_bytes = (uint32_t)kT * (uint32_t)(K1 > W ? K1 : W);
     const int wg = threadIdx.x / kT, tid = threadIdx.x % kT, warp = tid >> 5;
     uint8_t* s_act = s_net + ((lay.total + 127u) & ~127u) + wg * act_bytes;
@@ -196,10 +198,10 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
         }
         {
             const float tv = g.n_in > LF + 3 ? u[3] : 0.0f;
-            *reinterpret_cast<uint4*>(s_act + core_off8(tid, lay.col_extra, K1)) =
+            *reinterpret_cast<uint4*>(s_act + core_off8(tid, col_extra, K1)) =
                 make_uint4(e4m3x2(nv.x * q0, nv.y * q0) | (e4m3x2(nv.z * q0, tv * q0) << 16), 0u, 0u, 0u);
         }
-        for (int k = lay.col_extra + 16; k < K1; k += 16)
+        for (int k = col_extra + 16; k < K1; k += 16)
             *reinterpret_cast<uint4*>(s_act + core_off8(tid, k, K1)) = make_uint4(0u, 0u, 0u, 0u);
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -207,6 +209,7 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
 
         // ---- hidden layers ----
         uint32_t K = (uint32_t)K1, w_off = lay.w1;
+#pragma unroll
         for (int layer = 0; layer < nh && ok; ++layer) {
             if (tid == 0) {
                 tc::fence_after_sync();
@@ -221,6 +224,7 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
             tc::fence_after_sync();
             const float cq = s_cq[layer];
             const float* bq = s_bq + layer * W;
+#pragma unroll
             for (int ch = 0; ch < W / 16; ++ch) {
                 float v[16];
                 tc::tmem_ld16(tmem_row + (uint32_t)(ch * 16), v);
@@ -272,10 +276,12 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
     if (threadIdx.x < 32) tc::tmem_dealloc(*s_tmem, tmem_cols);
 }
 
-template <int DIMS, int F, int LV>
+template <int DIMS, int F, int LV, int WT = 0, int KT = 0, int NHT = 0>
 int launch8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
     const F8Layout* lay = reinterpret_cast<const F8Layout*>(m->f8_layout);
-    auto kern = query_f8_kernel<DIMS, F, LV>;
+    if ((WT > 0 && lay->W != WT) || (KT > 0 && lay->K1 != KT) || (NHT > 0 && lay->n_hidden != NHT))
+        return niv_fail(NIV_ERR_UNSUPPORTED, "network shape differs from the kernel's");
+    auto kern = query_f8_kernel<DIMS, F, LV, WT, KT, NHT>;
     const int kmax = lay->K1 > lay->W ? lay->K1 : lay->W;
     const size_t smem = (size_t)kHdr + ((lay->total + 127u) & ~127u) + (size_t)kWG * kT * kmax;
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -497,7 +503,11 @@ int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io,
     if (lay->K1 > 128) return niv_fail(NIV_ERR_UNSUPPORTED, "FP8 path needs a network input of <= 112 values");
     // fully unrolled encoders for 16 levels of 2 features (configs 1, 3, 4), a runtime loop otherwise
     const bool l16 = g.levels == 16 && m->d.feat == 2;
+    // fixed shapes: width 64, 64 input columns, 2 (3-D) or 3 (4-D) hidden layers
+    const bool fixed2 = lay->W == 64 && lay->K1 == 64 && lay->n_hidden == 2;
+    const bool fixed3 = lay->W == 64 && lay->K1 == 64 && lay->n_hidden == 3;
     if (m->d.dims == 4) {
+        if (l16 && fixed3) return launch8<4, 2, 16, 64, 64, 3>(m, g, io, s);
         if (l16) return launch8<4, 2, 16>(m, g, io, s);
         switch (m->d.feat) {
             case 1: return launch8<4, 1, 0>(m, g, io, s);
@@ -505,6 +515,7 @@ int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io,
             default: return launch8<4, 4, 0>(m, g, io, s);
         }
     }
+    if (l16 && fixed2) return launch8<3, 2, 16, 64, 64, 2>(m, g, io, s);
     if (l16) return launch8<3, 2, 16>(m, g, io, s);
     switch (m->d.feat) {
         case 1: return launch8<3, 1, 0>(m, g, io, s);

@@ -45,6 +45,9 @@ namespace {
 #ifndef NIV_TC_MINB
 #define NIV_TC_MINB 1
 #endif
+#ifndef NIV_TC_FIXW
+#define NIV_TC_FIXW 1
+#endif
 
 constexpr int kT = 128;          // rows per tile = threads per warpgroup
 constexpr int kWG = NIV_TC_WG;   // warpgroups (independent tile pipelines) per CTA
@@ -184,7 +187,9 @@ __device__ __forceinline__ void group_sync(int wg) { asm volatile("bar.sync %0, 
 // LV > 0: the level count is a compile-time constant, so the level loop unrolls fully and
 // every per-level constant (resolution, table offset, dense flag) is an immediate operand.
 // PE != 0: frequency-encoded model without grid (PE > 0: that many bands, fixed at compile time).
-template <int DIMS, int F, int LV, int PE, typename TabT>
+// WT, KT, NHT > 0: network width, first-layer input width and hidden-layer count fixed at
+// compile time (loops over layers and tile columns unroll with constant offsets).
+template <int DIMS, int F, int LV, int PE, typename TabT, int WT = 0, int KT = 0, int NHT = 0>
 __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(GridArgs g, IoArgs io,
                                                                 const TabT* __restrict__ grid,
                                                                 const uint8_t* __restrict__ packed, TcLayout lay,
@@ -198,7 +203,9 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
 
     const int wg = threadIdx.x / kT, tid = threadIdx.x % kT, warp = tid >> 5;
     uint8_t* s_act = s_net + ((lay.total + 127u) & ~127u) + wg * act_bytes;
-    const int K1 = lay.K1, W = lay.W;
+    const int K1 = KT > 0 ? KT : lay.K1, W = WT > 0 ? WT : lay.W, NH = NHT > 0 ? NHT : lay.n_hidden;
+    // column of n.x: the features end before it (round_up(L F, 8) for grid models)
+    const int col_extra = (LV > 0 && PE == 0) ? ((LV * F + 7) & ~7) : lay.col_extra;
 
     for (uint32_t i = threadIdx.x; i < lay.total / 16; i += kT * kWG)
         reinterpret_cast<uint4*>(s_net)[i] = __ldg(reinterpret_cast<const uint4*>(packed) + i);
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             const uint32_t one = (uint32_t)__half_as_ushort(__float2half_rn(1.0f));
             uint4 c = make_uint4(pack_half2(nv.x, nv.y), has_t ? pack_half2(nv.z, u[3]) : (pack_half2(nv.z, 0.0f) & 0xFFFFu) | (one << 16), 0u, 0u);
             if (has_t) c.z = one;
-            *reinterpret_cast<uint4*>(s_act + core_off(tid, lay.col_extra, K1)) = c;
+            *reinterpret_cast<uint4*>(s_act + core_off(tid, col_extra, K1)) = c;
         } else {  // Sec. 6: [n.x, n.y, n.z, sin, cos of 2^b pi t (b < t_bands <= 6), 1, 0, ...]
             float v[16];
 #pragma unroll
@@ -273,16 +280,16 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
 #pragma unroll
             for (int i = 3; i < 16; ++i)
                 if (i == 3 + 2 * g.t_bands) v[i] = 1.0f;
-            *reinterpret_cast<uint4*>(s_act + core_off(tid, lay.col_extra, K1)) =
+            *reinterpret_cast<uint4*>(s_act + core_off(tid, col_extra, K1)) =
                 make_uint4(pack_half2(v[0], v[1]), pack_half2(v[2], v[3]), pack_half2(v[4], v[5]), pack_half2(v[6], v[7]));
             if (4 + 2 * g.t_bands > 8) {
-                *reinterpret_cast<uint4*>(s_act + core_off(tid, lay.col_extra + 8, K1)) =
+                *reinterpret_cast<uint4*>(s_act + core_off(tid, col_extra + 8, K1)) =
                     make_uint4(pack_half2(v[8], v[9]), pack_half2(v[10], v[11]), pack_half2(v[12], v[13]),
                                pack_half2(v[14], v[15]));
                 tail = 16;
             }
         }
-        for (int k = lay.col_extra + tail; k < K1; k += 8)
+        for (int k = col_extra + tail; k < K1; k += 8)
             *reinterpret_cast<uint4*>(s_act + core_off(tid, k, K1)) = make_uint4(0u, 0u, 0u, 0u);
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -291,7 +298,8 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         // ---- 2, 3. hidden layers (the last one feeds the output layer) ----
         uint32_t K = (uint32_t)K1, w_off = lay.w1;
         float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
-        for (int layer = 0; layer < lay.n_hidden && ok; ++layer) {
+#pragma unroll
+        for (int layer = 0; layer < NH && ok; ++layer) {
             if (tid == 0) {
                 tc::fence_after_sync();
                 issue_layer(tmem, act_a, net_a + w_off, K, idesc_h, bar);
@@ -304,12 +312,13 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             phase ^= 1u;
             tc::fence_after_sync();
             const float* bias = s_bias + (layer - 1) * W;  // layer 0's bias came through the MMA
-            const bool last = layer == lay.n_hidden - 1;
+            const bool last = layer == NH - 1;
             if (kOutFma && last) {
-                z0 = s_bias[(lay.n_hidden - 1) * W + 0];
-                z1 = s_bias[(lay.n_hidden - 1) * W + 1];
-                z2 = s_bias[(lay.n_hidden - 1) * W + 2];
+                z0 = s_bias[(NH - 1) * W + 0];
+                z1 = s_bias[(NH - 1) * W + 1];
+                z2 = s_bias[(NH - 1) * W + 2];
             }
+#pragma unroll
             for (int c = 0; c < W / 16; ++c) {
                 float v[16];
                 tc::tmem_ld16(tmem_row + (uint32_t)(c * 16), v);
@@ -364,7 +373,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             tc::fence_after_sync();
             float z[4];
             tmem_ld4(tmem_row, z);
-            const float* bo = s_bias + (lay.n_hidden - 1) * W;
+            const float* bo = s_bias + (NH - 1) * W;
             z0 = z[0] + bo[0];
             z1 = z[1] + bo[1];
             z2 = z[2] + bo[2];
@@ -388,10 +397,12 @@ size_t tc_smem_bytes(const TcLayout& lay) {
     return (size_t)kHdr + ((lay.total + 127u) & ~127u) + (size_t)kWG * kT * kmax * 2;
 }
 
-template <int DIMS, int F, int LV, int PE = 0>
+template <int DIMS, int F, int LV, int PE = 0, int WT = 0, int KT = 0, int NHT = 0>
 int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s, int* status) {
     const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
-    auto kern = query_tc_f16_kernel<DIMS, F, LV, PE, __half>;
+    if ((WT > 0 && lay->W != WT) || (KT > 0 && lay->K1 != KT) || (NHT > 0 && lay->n_hidden != NHT))
+        return niv_fail(NIV_ERR_UNSUPPORTED, "network shape differs from the kernel's");
+    auto kern = query_tc_f16_kernel<DIMS, F, LV, PE, __half, WT, KT, NHT>;
     const __half* grid = m->grid_f16;
     const size_t smem = tc_smem_bytes(*lay);
     int dev = 0;
@@ -472,7 +483,16 @@ int by_feat(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_
     switch (m->d.feat) {
         case 1: return launch<DIMS, 1, 0>(m, g, io, s, status);
         case 2:
-            if (g.levels == 16) return launch<DIMS, 2, 16>(m, g, io, s, status);
+            if (g.levels == 16) {
+                // fixed shapes of the 16-level models: width 64, 48 input columns, 2 or 3 hidden layers
+                const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
+                if (NIV_TC_FIXW && lay->W == 64 && lay->K1 == 48 && lay->n_hidden == 2)
+                    return launch<DIMS, 2, 16, 0, 64, 48, 2>(m, g, io, s, status);
+                if (NIV_TC_FIXW && lay->W == 64 && lay->K1 == 48 && lay->n_hidden == 3)
+                    return launch<DIMS, 2, 16, 0, 64, 48, 3>(m, g, io, s, status);
+                if (NIV_TC_FIXW && lay->W == 64) return launch<DIMS, 2, 16, 0, 64>(m, g, io, s, status);
+                return launch<DIMS, 2, 16>(m, g, io, s, status);
+            }
             if (g.levels == 8) return launch<DIMS, 2, 8>(m, g, io, s, status);
             return launch<DIMS, 2, 0>(m, g, io, s, status);
         case 4:
