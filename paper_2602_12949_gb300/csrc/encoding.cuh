@@ -30,6 +30,13 @@ struct GridArgs {
     float t;
     int32_t res[NIV_MAX_LEVELS];
     uint32_t offset[NIV_MAX_LEVELS];  // first entry of each level
+    // per-level constants in the form the encoders use them (read as kernel-argument
+    // operands, so no tile recomputes them): N and N - 1 as floats (exact), and for dense
+    // levels the entry strides N + 1 and (N + 1)^2
+    float res_f[NIV_MAX_LEVELS];
+    float resm1_f[NIV_MAX_LEVELS];
+    uint32_t stride1[NIV_MAX_LEVELS];
+    uint32_t stride2[NIV_MAX_LEVELS];
 };
 
 // Where a kernel finds its records and how it walks them.
@@ -131,12 +138,12 @@ __device__ __forceinline__ void niv_level_weights(const float* w1, float* wc) {
 // Corner entries of level l at normalised coordinate u and the per-axis fractions w1
 // (Sec. 4.1), with the per-corner work factored: one cell per axis, per-axis index terms
 // (dense strides or hash products) combined per corner.  Corner c has offset bit d along
-// dimension d.
-template <int DIMS>
+// dimension d.  ND >= 0: the dense levels are exactly levels 0 .. ND-1, known at compile
+// time (with the level unrolled, the dense / hashed choice then costs no branch).
+template <int DIMS, int ND = -1>
 __device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, const float* u, uint32_t* e, float* w1) {
     constexpr int NC = 1 << DIMS;
-    const int32_t N = g.res[l];
-    const float fN = (float)N, fmax = (float)(N - 1);
+    const float fN = g.res_f[l], fmax = g.resm1_f[l];
     uint32_t ci[DIMS];
 #pragma unroll
     for (int d = 0; d < DIMS; ++d) {
@@ -145,8 +152,8 @@ __device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, cons
         ci[d] = (uint32_t)(int)fl;
         w1[d] = __fsub_rn(s, fl);
     }
-    if ((g.dense_mask >> l) & 1u) {
-        const uint32_t S = (uint32_t)N + 1u, S2 = S * S;
+    if (ND >= 0 ? l < ND : ((g.dense_mask >> l) & 1u) != 0u) {
+        const uint32_t S = g.stride1[l], S2 = g.stride2[l];
         uint32_t base = ci[2] * S2 + ci[1] * S + ci[0];
         if (DIMS == 4) base += ci[DIMS - 1] * S2 * S;
         uint32_t oh[NC / 2];
@@ -189,11 +196,11 @@ __device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, cons
 }
 
 // Corner entries and multilinear weights of level l at normalised coordinate u.
-template <int DIMS>
+template <int DIMS, int ND = -1>
 __device__ __forceinline__ void niv_level_corners(const GridArgs& g, int l, const float* u, uint32_t* e,
                                                   float* wc) {
     float w1[DIMS];
-    niv_level_entries<DIMS>(g, l, u, e, w1);
+    niv_level_entries<DIMS, ND>(g, l, u, e, w1);
     niv_level_weights<DIMS>(w1, wc);
 }
 

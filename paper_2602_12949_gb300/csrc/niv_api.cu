@@ -176,6 +176,10 @@ GridArgs niv_grid_args(const niv_model* m, const niv_query_params* p) {
     for (int l = 0; l < m->d.levels; ++l) {
         g.res[l] = m->res[l];
         g.offset[l] = (uint32_t)m->offset[l];
+        g.res_f[l] = (float)m->res[l];
+        g.resm1_f[l] = (float)(m->res[l] - 1);
+        g.stride1[l] = (uint32_t)m->res[l] + 1u;
+        g.stride2[l] = g.stride1[l] * g.stride1[l];
         if (m->dense[l]) g.dense_mask |= 1u << l;
     }
     for (int k = 0; k < 3; ++k) {

@@ -86,7 +86,7 @@ __device__ __forceinline__ uint32_t e4m3x2(float a, float b) {
 
 // Encode levels [l0, l0 + 16/F) of one record into one 16-byte chunk of E4M3 inputs (value
 // times q0, the inverse input scale), each level converted as soon as it is blended.
-template <int DIMS, int F>
+template <int DIMS, int F, int ND = -1>
 __device__ __forceinline__ uint4 encode_chunk8(const GridArgs& g, const __half* __restrict__ grid16, int l0, int L,
                                                const float* u, float q0) {
     constexpr int NC = 1 << DIMS, G = 16 / F;
@@ -98,7 +98,7 @@ __device__ __forceinline__ uint4 encode_chunk8(const GridArgs& g, const __half* 
         uint32_t e[NC];
         float wc[NC];
         R raw[NC];
-        niv_level_corners<DIMS>(g, l0 + q, u, e, wc);
+        niv_level_corners<DIMS, ND>(g, l0 + q, u, e, wc);
         niv_level_gather<NC, F, __half>(grid16 + (size_t)g.offset[l0 + q] * F, e, raw);
         float acc[F];
         niv_level_blend<NC, F>(raw, wc, acc);
@@ -115,6 +115,9 @@ __device__ __forceinline__ uint4 encode_chunk8(const GridArgs& g, const __half* 
     return make_uint4(wd[0], wd[1], wd[2], wd[3]);
 }
 
+#ifndef NIV_TC_ND
+#define NIV_TC_ND 1
+#endif
 #ifndef NIV_F8_WG
 #define NIV_F8_WG 8
 #endif
@@ -125,8 +128,9 @@ __device__ __forceinline__ void group_sync8(int wg) { asm volatile("bar.sync %0,
 // kWG warpgroups per CTA, persistent over 128-record tiles; each warpgroup owns an activation
 // tile, an mbarrier, a named barrier and its TMEM columns.  LV > 0: level count fixed at
 // compile time (the level loop unrolls).  WT, KT, NHT > 0: network width, first-layer input
-// width and hidden-layer count fixed at compile time (layer and column loops unroll).
-template <int DIMS, int F, int LV, int WT = 0, int KT = 0, int NHT = 0>
+// width and hidden-layer count fixed at compile time (layer and column loops unroll).  ND >= 0:
+// levels 0 .. ND-1 are the dense ones.
+template <int DIMS, int F, int LV, int WT = 0, int KT = 0, int NHT = 0, int ND = -1>
 __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArgs io, const __half* __restrict__ grid16,
                                                                 const uint8_t* __restrict__ packed, F8Layout lay,
                                                                 int out_act, int64_t n_tiles, uint32_t tmem_cols,
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
         if (LV > 0) {
 #pragma unroll
             for (int l0 = 0; l0 < LV; l0 += G)
-                *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K1)) = encode_chunk8<DIMS, F>(g, grid16, l0, LV, u, q0);
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K1)) = encode_chunk8<DIMS, F, ND>(g, grid16, l0, LV, u, q0);
         } else {
             for (int l0 = 0; l0 < L; l0 += G)
                 *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K1)) = encode_chunk8<DIMS, F>(g, grid16, l0, L, u, q0);
@@ -276,12 +280,14 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
     if (threadIdx.x < 32) tc::tmem_dealloc(*s_tmem, tmem_cols);
 }
 
-template <int DIMS, int F, int LV, int WT = 0, int KT = 0, int NHT = 0>
+template <int DIMS, int F, int LV, int WT = 0, int KT = 0, int NHT = 0, int ND = -1>
 int launch8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s) {
     const F8Layout* lay = reinterpret_cast<const F8Layout*>(m->f8_layout);
     if ((WT > 0 && lay->W != WT) || (KT > 0 && lay->K1 != KT) || (NHT > 0 && lay->n_hidden != NHT))
         return niv_fail(NIV_ERR_UNSUPPORTED, "network shape differs from the kernel's");
-    auto kern = query_f8_kernel<DIMS, F, LV, WT, KT, NHT>;
+    if (ND >= 0 && g.dense_mask != (ND >= 32 ? ~0u : ((1u << ND) - 1u)))
+        return niv_fail(NIV_ERR_UNSUPPORTED, "dense levels differ from the kernel's");
+    auto kern = query_f8_kernel<DIMS, F, LV, WT, KT, NHT, ND>;
     const int kmax = lay->K1 > lay->W ? lay->K1 : lay->W;
     const size_t smem = (size_t)kHdr + ((lay->total + 127u) & ~127u) + (size_t)kWG * kT * kmax;
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -507,6 +513,7 @@ int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io,
     const bool fixed2 = lay->W == 64 && lay->K1 == 64 && lay->n_hidden == 2;
     const bool fixed3 = lay->W == 64 && lay->K1 == 64 && lay->n_hidden == 3;
     if (m->d.dims == 4) {
+        if (NIV_TC_ND && l16 && fixed3 && g.dense_mask == 0x3u) return launch8<4, 2, 16, 64, 64, 3, 2>(m, g, io, s);
         if (l16 && fixed3) return launch8<4, 2, 16, 64, 64, 3>(m, g, io, s);
         if (l16) return launch8<4, 2, 16>(m, g, io, s);
         switch (m->d.feat) {
@@ -515,6 +522,7 @@ int niv_launch_query_f8(const niv_model* m, const GridArgs& g, const IoArgs& io,
             default: return launch8<4, 4, 0>(m, g, io, s);
         }
     }
+    if (NIV_TC_ND && l16 && fixed2 && g.dense_mask == 0xFu) return launch8<3, 2, 16, 64, 64, 2, 4>(m, g, io, s);
     if (l16 && fixed2) return launch8<3, 2, 16, 64, 64, 2>(m, g, io, s);
     if (l16) return launch8<3, 2, 16>(m, g, io, s);
     switch (m->d.feat) {

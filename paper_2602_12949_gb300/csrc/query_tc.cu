@@ -48,6 +48,9 @@ namespace {
 #ifndef NIV_TC_FIXW
 #define NIV_TC_FIXW 1
 #endif
+#ifndef NIV_TC_ND
+#define NIV_TC_ND 1
+#endif
 
 constexpr int kT = 128;          // rows per tile = threads per warpgroup
 constexpr int kWG = NIV_TC_WG;   // warpgroups (independent tile pipelines) per CTA
@@ -142,7 +145,7 @@ __device__ __forceinline__ void encode_pe(const GridArgs& g, const float* u, uin
 
 // Encode levels [l0, l0 + G) of one record into one 16-byte chunk of FP16 features,
 // kILP levels' gathers in flight at a time.
-template <int DIMS, int F, typename TabT>
+template <int DIMS, int F, typename TabT, int ND = -1>
 __device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const TabT* __restrict__ grid, int l0, int L,
                                               const float* u) {
     constexpr int NC = 1 << DIMS, G = 8 / F;
@@ -155,8 +158,8 @@ __device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const TabT* __r
         uint32_t ea[NC], eb[NC];
         float wa[NC], wb[NC];
         R ra[NC], rb[NC];
-        if (has_a) niv_level_corners<DIMS>(g, la, u, ea, wa);
-        if (has_b) niv_level_corners<DIMS>(g, lb, u, eb, wb);
+        if (has_a) niv_level_corners<DIMS, ND>(g, la, u, ea, wa);
+        if (has_b) niv_level_corners<DIMS, ND>(g, lb, u, eb, wb);
         if (has_a) niv_level_gather<NC, F, TabT>(grid + (size_t)g.offset[la] * F, ea, ra);
         if (has_b) niv_level_gather<NC, F, TabT>(grid + (size_t)g.offset[lb] * F, eb, rb);
         float acc[F];
@@ -188,8 +191,9 @@ __device__ __forceinline__ void group_sync(int wg) { asm volatile("bar.sync %0, 
 // every per-level constant (resolution, table offset, dense flag) is an immediate operand.
 // PE != 0: frequency-encoded model without grid (PE > 0: that many bands, fixed at compile time).
 // WT, KT, NHT > 0: network width, first-layer input width and hidden-layer count fixed at
-// compile time (loops over layers and tile columns unroll with constant offsets).
-template <int DIMS, int F, int LV, int PE, typename TabT, int WT = 0, int KT = 0, int NHT = 0>
+// compile time (loops over layers and tile columns unroll with constant offsets).  ND >= 0:
+// levels 0 .. ND-1 are the dense ones.
+template <int DIMS, int F, int LV, int PE, typename TabT, int WT = 0, int KT = 0, int NHT = 0, int ND = -1>
 __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(GridArgs g, IoArgs io,
                                                                 const TabT* __restrict__ grid,
                                                                 const uint8_t* __restrict__ packed, TcLayout lay,
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         } else if constexpr (LV > 0) {
 #pragma unroll
             for (int l0 = 0; l0 < LV; l0 += G)
-                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, LV, u);
+                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F, TabT, ND>(g, grid, l0, LV, u);
         } else {
             for (int l0 = 0; l0 < L; l0 += G)
                 *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, L, u);
@@ -397,12 +401,14 @@ size_t tc_smem_bytes(const TcLayout& lay) {
     return (size_t)kHdr + ((lay.total + 127u) & ~127u) + (size_t)kWG * kT * kmax * 2;
 }
 
-template <int DIMS, int F, int LV, int PE = 0, int WT = 0, int KT = 0, int NHT = 0>
+template <int DIMS, int F, int LV, int PE = 0, int WT = 0, int KT = 0, int NHT = 0, int ND = -1>
 int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t s, int* status) {
     const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
     if ((WT > 0 && lay->W != WT) || (KT > 0 && lay->K1 != KT) || (NHT > 0 && lay->n_hidden != NHT))
         return niv_fail(NIV_ERR_UNSUPPORTED, "network shape differs from the kernel's");
-    auto kern = query_tc_f16_kernel<DIMS, F, LV, PE, __half, WT, KT, NHT>;
+    if (ND >= 0 && g.dense_mask != (ND >= 32 ? ~0u : ((1u << ND) - 1u)))
+        return niv_fail(NIV_ERR_UNSUPPORTED, "dense levels differ from the kernel's");
+    auto kern = query_tc_f16_kernel<DIMS, F, LV, PE, __half, WT, KT, NHT, ND>;
     const __half* grid = m->grid_f16;
     const size_t smem = tc_smem_bytes(*lay);
     int dev = 0;
@@ -486,10 +492,18 @@ int by_feat(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_
             if (g.levels == 16) {
                 // fixed shapes of the 16-level models: width 64, 48 input columns, 2 or 3 hidden layers
                 const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
-                if (NIV_TC_FIXW && lay->W == 64 && lay->K1 == 48 && lay->n_hidden == 2)
-                    return launch<DIMS, 2, 16, 0, 64, 48, 2>(m, g, io, s, status);
-                if (NIV_TC_FIXW && lay->W == 64 && lay->K1 == 48 && lay->n_hidden == 3)
-                    return launch<DIMS, 2, 16, 0, 64, 48, 3>(m, g, io, s, status);
+                // and, when the dense levels are the first 2, 4 or 5 (configs 3, 1, 4), that count
+                const bool f2 = NIV_TC_FIXW && lay->W == 64 && lay->K1 == 48 && lay->n_hidden == 2;
+                const bool f3 = NIV_TC_FIXW && lay->W == 64 && lay->K1 == 48 && lay->n_hidden == 3;
+                const uint32_t dm = NIV_TC_ND ? g.dense_mask : 0xFFFFFFFFu;
+                if constexpr (DIMS == 3) {
+                    if (f2 && dm == 0xFu) return launch<DIMS, 2, 16, 0, 64, 48, 2, 4>(m, g, io, s, status);
+                    if (f2 && dm == 0x1Fu) return launch<DIMS, 2, 16, 0, 64, 48, 2, 5>(m, g, io, s, status);
+                } else {
+                    if (f3 && dm == 0x3u) return launch<DIMS, 2, 16, 0, 64, 48, 3, 2>(m, g, io, s, status);
+                }
+                if (f2) return launch<DIMS, 2, 16, 0, 64, 48, 2>(m, g, io, s, status);
+                if (f3) return launch<DIMS, 2, 16, 0, 64, 48, 3>(m, g, io, s, status);
                 if (NIV_TC_FIXW && lay->W == 64) return launch<DIMS, 2, 16, 0, 64>(m, g, io, s, status);
                 return launch<DIMS, 2, 16>(m, g, io, s, status);
             }
