@@ -242,8 +242,27 @@ __device__ __forceinline__ void niv_unpack(float4 r, float* f) {
     f[3] = r.w;
 }
 
+#ifndef NIV_BLEND_PAIRS
+#define NIV_BLEND_PAIRS 1
+#endif
+// Two FP16 features per entry: both features of a corner in one packed FP32 FMA, each
+// lane the scalar FMA of its feature in the same corner order.
+template <int NC>
+__device__ __forceinline__ void niv_level_blend2(const uint32_t* raw, const float* wc, float* acc) {
+    float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+        a = __ffma2_rn(make_float2(wc[c], wc[c]), __half22float2(*reinterpret_cast<const __half2*>(&raw[c])), a);
+    acc[0] = a.x;
+    acc[1] = a.y;
+}
+
 template <int NC, int F, typename R>
 __device__ __forceinline__ void niv_level_blend(const R* raw, const float* wc, float* acc) {
+    if constexpr (NIV_BLEND_PAIRS && F == 2 && std::is_same<R, uint32_t>::value) {
+        niv_level_blend2<NC>(raw, wc, acc);
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < F; ++j) acc[j] = 0.0f;
 #pragma unroll

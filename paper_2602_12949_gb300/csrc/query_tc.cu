@@ -328,11 +328,14 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                 tc::tmem_ld16(tmem_row + (uint32_t)(c * 16), v);
                 if (layer > 0) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float2 b = reinterpret_cast<const float2*>(bias + c * 16)[j];
-                        const float2 sum = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]), b);
-                        v[2 * j] = sum.x;
-                        v[2 * j + 1] = sum.y;
+                    for (int j = 0; j < 4; ++j) {  // biases 16-byte aligned: one load per four
+                        const float4 b = reinterpret_cast<const float4*>(bias + c * 16)[j];
+                        const float2 lo = __fadd2_rn(make_float2(v[4 * j], v[4 * j + 1]), make_float2(b.x, b.y));
+                        const float2 hi = __fadd2_rn(make_float2(v[4 * j + 2], v[4 * j + 3]), make_float2(b.z, b.w));
+                        v[4 * j] = lo.x;
+                        v[4 * j + 1] = lo.y;
+                        v[4 * j + 2] = hi.x;
+                        v[4 * j + 3] = hi.y;
                     }
                 }
                 if (kOutFma && last) {
