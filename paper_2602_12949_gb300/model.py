@@ -164,7 +164,8 @@ class NIVModel:
 
     def query_host(self, pos, nrm, out=None, precision="fp16", aabb_min=(0.0, 0.0, 0.0),
                    aabb_max=(1.0, 1.0, 1.0), t=0.0, image_width=0, stream=None):
-        """Same as query for host arrays (numpy or CPU tensors); copies in and out inside the call."""
+        """Same as query for host arrays (numpy or CPU tensors), copied or read in place inside
+        the call (page-locked buffers are read and written by the kernel directly)."""
         to_np = (lambda a: a.numpy()) if isinstance(pos, torch.Tensor) else (lambda a: a)
         p, n = np.ascontiguousarray(to_np(pos)), np.ascontiguousarray(to_np(nrm))
         if p.ndim != 2 or p.shape[1] != 4 or p.shape != n.shape or p.dtype != n.dtype:
@@ -173,10 +174,19 @@ class NIVModel:
         if out is None:
             out = np.empty(p.shape, p.dtype)
         o = to_np(out) if isinstance(out, torch.Tensor) else out
+        if not (o.flags["C_CONTIGUOUS"] and o.shape == p.shape):
+            raise ValueError("out must be a contiguous [n][4] array")
         odt = _lib.NIV_F16 if o.dtype == np.float16 else _lib.NIV_F32
-        qp = self.query_params(aabb_min, aabb_max, t, image_width)
-        check(lib().niv_query_host(self._h, ctypes.c_void_p(p.ctypes.data), ctypes.c_void_p(n.ctypes.data),
-                                   p.shape[0], dt, ctypes.byref(qp), ctypes.c_void_p(o.ctypes.data), odt,
+        # a per-frame call: the parameter block is cached and the pointers are passed as ints
+        key = (tuple(aabb_min), tuple(aabb_max), float(t), int(image_width))
+        cache = self.__dict__.setdefault("_qp_cache", {})
+        qp = cache.get(key)
+        if qp is None:
+            if len(cache) >= 64:
+                cache.clear()
+            qp = cache[key] = self.query_params(*key)
+        check(lib().niv_query_host(self._h, p.__array_interface__["data"][0], n.__array_interface__["data"][0],
+                                   p.shape[0], dt, ctypes.byref(qp), o.__array_interface__["data"][0], odt,
                                    PRECISIONS[precision], _stream(stream)))
         return out
 
