@@ -12,9 +12,11 @@
 // hierarchy on the host: binned surface-area-heuristic splits of the centroids (16 bins per
 // axis), leaves of at most 4 triangles or where no split pays (up to 16), nodes in
 // depth-first order (left child next to its parent), bounds
-// padded by 1e-5 of the scene's extent.  One thread per record traverses it with a stack,
-// the child on the ray's side of the split first (any hit ends the ray); records whose ray
-// origin lies farther than R from every depth-3 node box skip the rays (AO = 1).
+// padded by 1e-5 of the scene's extent.  On the device every inner node holds the boxes of
+// both its children, so one step tests two boxes; one thread per record traverses it with a
+// stack, leaves of hit children first, then the hit inner child that the ray enters first
+// (any hit ends the ray); records whose ray origin lies farther than R from every depth-3
+// node box skip the rays (AO = 1).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -26,9 +28,10 @@ constexpr int kCullBoxes = 8;  // node boxes at depth 3: a record traces rays on
 
 struct niv_dyn {
     int device;
-    int64_t n_tris, n_nodes;
-    // per node: (lo.xyz, a), (hi.xyz, b); leaf: a = first triangle, b = count > 0;
-    // inner: a = right child (the left child follows its parent), b = -(split axis + 1)
+    int64_t n_tris, n_nodes;  // n_nodes: nodes of the binary hierarchy
+    // per inner node, for each of its two children: (lo.xyz, ref), (hi.xyz, count);
+    // count > 0: a leaf of `count` triangles from `ref`; 0: the inner node `ref`;
+    // < 0: no child (a leaf root's second slot)
     float4* nodes;
     float4* tris;  // per triangle: v0, e1 = v1 - v0, e2 = v2 - v0
     int n_cull;
@@ -184,17 +187,6 @@ void collect_cull(const std::vector<HostNode>& nodes, int32_t i, int depth, std:
 constexpr int kStack = 64;
 constexpr float kRayBias = 0.01f;
 
-// Slab test of the ray o + t d, t in [0, tmax], against a node box (inv: finite reciprocals of d,
-// oi = o * inv).  The box bounds are padded, so the FMA's rounding cannot lose a hit.
-__device__ __forceinline__ bool box_hit(const float4& lo, const float4& hi, float3 oi, float3 inv, float tmax) {
-    const float tx0 = fmaf(lo.x, inv.x, -oi.x), tx1 = fmaf(hi.x, inv.x, -oi.x);
-    const float ty0 = fmaf(lo.y, inv.y, -oi.y), ty1 = fmaf(hi.y, inv.y, -oi.y);
-    const float tz0 = fmaf(lo.z, inv.z, -oi.z), tz1 = fmaf(hi.z, inv.z, -oi.z);
-    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-    return tn <= tf;
-}
-
 // Moeller-Trumbore: hit at 0 < t <= tmax inside the triangle (v0, e1, e2).
 __device__ __forceinline__ bool tri_hit(const float4& v0, const float4& e1, const float4& e2, float3 o, float3 d,
                                         float tmax) {
@@ -212,6 +204,26 @@ __device__ __forceinline__ bool tri_hit(const float4& v0, const float4& e1, cons
     return t > 0.0f && t <= tmax;
 }
 
+// Entry distance of the ray o + t d, t in [0, tmax], into a node box (inv: finite
+// reciprocals of d, oi = o * inv); false when it misses.  The box bounds are padded, so
+// the FMA's rounding cannot lose a hit.
+__device__ __forceinline__ bool box_enter(const float4& lo, const float4& hi, float3 oi, float3 inv, float tmax,
+                                          float& tn) {
+    const float tx0 = fmaf(lo.x, inv.x, -oi.x), tx1 = fmaf(hi.x, inv.x, -oi.x);
+    const float ty0 = fmaf(lo.y, inv.y, -oi.y), ty1 = fmaf(hi.y, inv.y, -oi.y);
+    const float tz0 = fmaf(lo.z, inv.z, -oi.z), tz1 = fmaf(hi.z, inv.z, -oi.z);
+    tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    return tn <= tf;
+}
+
+__device__ __forceinline__ bool leaf_hit(const float4* __restrict__ tris, int first, int count, float3 o, float3 d,
+                                         float tmax) {
+    for (int i = first; i < first + count; ++i)
+        if (tri_hit(__ldg(tris + 3 * i), __ldg(tris + 3 * i + 1), __ldg(tris + 3 * i + 2), o, d, tmax)) return true;
+    return false;
+}
+
 __device__ bool any_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, float3 o, float3 d,
                         float tmax) {
     const float3 inv = make_float3(1.0f / (fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x)),
@@ -221,25 +233,28 @@ __device__ bool any_hit(const float4* __restrict__ nodes, const float4* __restri
     int stack[kStack];
     int sp = 0, node = 0;
     while (true) {
-        const float4 lo = __ldg(nodes + 2 * node), hi = __ldg(nodes + 2 * node + 1);
-        if (box_hit(lo, hi, oi, inv, tmax)) {
-            const int a = __float_as_int(lo.w), b = __float_as_int(hi.w);
-            if (b > 0) {
-                for (int i = a; i < a + b; ++i)
-                    if (tri_hit(__ldg(tris + 3 * i), __ldg(tris + 3 * i + 1), __ldg(tris + 3 * i + 2), o, d, tmax))
-                        return true;
-            } else {
-                // the child on the ray's side of the split first: an occluded ray meets its hit sooner
-                const int axis = -b - 1;
-                const float dir = axis == 0 ? d.x : (axis == 1 ? d.y : d.z);
-                const int near = dir >= 0.0f ? node + 1 : a, far = dir >= 0.0f ? a : node + 1;
-                if (sp < kStack) stack[sp++] = far;  // the builder caps the depth at 60
-                node = near;
-                continue;
-            }
+        const float4 l0 = __ldg(nodes + 4 * node), h0 = __ldg(nodes + 4 * node + 1);
+        const float4 l1 = __ldg(nodes + 4 * node + 2), h1 = __ldg(nodes + 4 * node + 3);
+        const int r0 = __float_as_int(l0.w), c0 = __float_as_int(h0.w);
+        const int r1 = __float_as_int(l1.w), c1 = __float_as_int(h1.w);
+        float t0, t1;
+        const bool in0 = c0 >= 0 && box_enter(l0, h0, oi, inv, tmax, t0);
+        const bool in1 = c1 >= 0 && box_enter(l1, h1, oi, inv, tmax, t1);
+        if (in0 && c0 > 0 && leaf_hit(tris, r0, c0, o, d, tmax)) return true;
+        if (in1 && c1 > 0 && leaf_hit(tris, r1, c1, o, d, tmax)) return true;
+        const bool go0 = in0 && c0 == 0, go1 = in1 && c1 == 0;
+        if (go0 && go1) {
+            const bool first0 = t0 <= t1;
+            if (sp < kStack) stack[sp++] = first0 ? r1 : r0;  // the builder caps the depth at 60
+            node = first0 ? r0 : r1;
+        } else if (go0) {
+            node = r0;
+        } else if (go1) {
+            node = r1;
+        } else {
+            if (sp == 0) return false;
+            node = stack[--sp];
         }
-        if (sp == 0) return false;
-        node = stack[--sp];
     }
 }
 
@@ -311,14 +326,34 @@ int niv_dyn_build(const float* tri9, int64_t n_tris, niv_dyn** out) {
     for (int k = 0; k < 3; ++k) ext = std::max(ext, hi[k] - lo[k]);
     B.pad = 1e-5f * std::max(ext, 1e-3f);
     B.build(0, (int32_t)n_tris, 0);
-    std::vector<float4> nodes(2 * B.nodes.size()), tris(3 * (size_t)n_tris);
-    for (size_t i = 0; i < B.nodes.size(); ++i) {
-        const HostNode& h = B.nodes[i];
-        float a, b;
-        memcpy(&a, &h.a, 4);
-        memcpy(&b, &h.b, 4);
-        nodes[2 * i] = make_float4(h.lo[0], h.lo[1], h.lo[2], a);
-        nodes[2 * i + 1] = make_float4(h.hi[0], h.hi[1], h.hi[2], b);
+    // device nodes: one per inner node of the binary hierarchy (a leaf root gets one with a
+    // single child), each holding both children's boxes
+    std::vector<int32_t> wide_of(B.nodes.size(), -1);
+    int32_t n_wide = 0;
+    for (size_t i = 0; i < B.nodes.size(); ++i)
+        if (B.nodes[i].b <= 0) wide_of[i] = n_wide++;
+    auto as_float = [](int32_t v) {
+        float f;
+        memcpy(&f, &v, 4);
+        return f;
+    };
+    auto put_child = [&](float4* slot, int32_t c) {
+        const HostNode& h = B.nodes[(size_t)c];
+        const bool leaf = h.b > 0;
+        slot[0] = make_float4(h.lo[0], h.lo[1], h.lo[2], as_float(leaf ? h.a : wide_of[(size_t)c]));
+        slot[1] = make_float4(h.hi[0], h.hi[1], h.hi[2], as_float(leaf ? h.b : 0));
+    };
+    std::vector<float4> nodes(4 * (size_t)std::max(n_wide, 1)), tris(3 * (size_t)n_tris);
+    if (n_wide == 0) {
+        put_child(&nodes[0], 0);
+        nodes[2] = make_float4(0.0f, 0.0f, 0.0f, as_float(0));
+        nodes[3] = make_float4(0.0f, 0.0f, 0.0f, as_float(-1));
+    } else {
+        for (size_t i = 0; i < B.nodes.size(); ++i) {
+            if (wide_of[i] < 0) continue;
+            put_child(&nodes[4 * (size_t)wide_of[i]], (int32_t)i + 1);
+            put_child(&nodes[4 * (size_t)wide_of[i] + 2], B.nodes[i].a);
+        }
     }
     for (int64_t i = 0; i < n_tris; ++i) {
         const float* t = tri9 + 9 * (int64_t)B.order[(size_t)i];

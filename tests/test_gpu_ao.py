@@ -77,6 +77,32 @@ def test_far_records_are_unoccluded(niv):
     dyn.close()
 
 
+@pytest.mark.parametrize("n_tris", [1, 2, 7])
+def test_small_hierarchies_match_oracle(niv, n_tris):
+    # a hierarchy that is a single leaf (1 or 2 triangles) or one split: squares above a
+    # floor of records, counts equal to the oracle's on every clear record
+    rng = np.random.default_rng(n_tris)
+    tris = []
+    for i in range(n_tris):
+        z, half = 0.2 + 0.1 * i, 0.3
+        cx, cy = rng.uniform(-0.3, 0.3, 2)
+        a, b, c = (cx - half, cy - half, z), (cx + half, cy - half, z), (cx + half, cy + half, z)
+        tris.append(a + b + c)
+    tri9 = np.array(tris, np.float32)
+    x4 = np.zeros((4096, 4), np.float32)
+    x4[:, :2] = rng.uniform(-0.6, 0.6, (4096, 2))
+    n4 = np.zeros((4096, 4), np.float32)
+    n4[:, 2] = 1.0
+    dyn = niv.DynamicGeometry(tri9)
+    ao = dyn.ao(torch.from_numpy(x4).cuda(), torch.from_numpy(n4).cuda(), rays=16, radius=1.0, seed=5).cpu().numpy()
+    _, blocked, amb = oracle.dyn_ao(tri9, x4, n4, 16, 1.0, seed=5)
+    got = np.rint((1.0 - ao) * 16).astype(np.int32)
+    clear = ~amb
+    assert np.array_equal(got[clear], blocked[clear])
+    assert amb.mean() < 0.01 and np.count_nonzero(blocked) > 100
+    dyn.close()
+
+
 def test_bad_arguments_rejected(niv):
     with pytest.raises(niv.NivError):
         niv.DynamicGeometry(np.zeros((0, 9), np.float32))
