@@ -89,9 +89,8 @@ __global__ void __launch_bounds__(128) probe_query_kernel(const uint2* __restric
                 const float dist = sqrtf(dot3(dv, dv));
                 bool visible = true;
                 if (dist > 0.0f) {
-                    Hit h;
                     const float3 d = make_float3(dv.x / dist, dv.y / dist, dv.z / dist);
-                    visible = !(S.intersect(o, d, h) && h.t < dist - kRayEnd);
+                    visible = !S.occluded(o, d, dist - kRayEnd);
                 }
                 w = fmaxf(visible ? w : 0.0f, 1e-6f);
             } else {

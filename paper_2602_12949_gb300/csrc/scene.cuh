@@ -63,6 +63,56 @@ struct SceneView {
         return e[0] > 0.0f || e[1] > 0.0f || e[2] > 0.0f;
     }
 
+    // Whether the ray o + t d hits anything before tmax, for shadow rays: each object's hit
+    // distance is the one intersect takes (the sphere's first root beyond kTEps, the box's
+    // entry or exit beyond kTEps, the room's first wall unless it is the open skylight), so
+    // the answer is intersect's closest hit t < tmax; the search stops at the first such hit.
+    // The slab distances use the ray's reciprocal directions instead of divisions.
+    __device__ bool occluded(float3 o, float3 d, float tmax) const {
+        for (int i = 0; i < ns; ++i) {
+            const float r = sph[kSph * i + 3];
+            const float3 ci = centre(i);
+            const float3 oc = make_float3(o.x - ci.x, o.y - ci.y, o.z - ci.z);
+            const float b = dot3(oc, d), disc = b * b - (dot3(oc, oc) - r * r);
+            if (disc < 0.0f) continue;
+            const float sq = sqrtf(disc);
+            float t = -b - sq;
+            if (t <= kTEps) t = -b + sq;
+            if (t > kTEps && t < tmax) return true;
+        }
+        const float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+        for (int i = 0; i < nb; ++i) {
+            const float* B = box + kBox * i;
+            const float tx1 = (B[0] - o.x) * inv.x, tx2 = (B[3] - o.x) * inv.x;
+            const float ty1 = (B[1] - o.y) * inv.y, ty2 = (B[4] - o.y) * inv.y;
+            const float tz1 = (B[2] - o.z) * inv.z, tz2 = (B[5] - o.z) * inv.z;
+            const float tn = fmaxf(fmaxf(fminf(tx1, tx2), fminf(ty1, ty2)), fminf(tz1, tz2));
+            const float tf = fminf(fminf(fmaxf(tx1, tx2), fmaxf(ty1, ty2)), fmaxf(tz1, tz2));
+            if (tf < tn) continue;
+            const float t = tn > kTEps ? tn : tf;
+            if (t > kTEps && t < tmax) return true;
+        }
+        if (room) {
+            float tw = INFINITY;
+            int wall = -1;
+            for (int k = 0; k < 3; ++k) {
+                const float dk = comp(d, k), ok = comp(o, k);
+                float t;
+                if (dk > 0.0f) t = (h[7 + k] - ok) * comp(inv, k);
+                else if (dk < 0.0f) t = (h[4 + k] - ok) * comp(inv, k);
+                else continue;
+                if (t < tw) { tw = t; wall = 2 * k + (dk > 0.0f); }
+            }
+            if (wall >= 0 && tw < tmax) {
+                const float px = o.x + tw * d.x, pz = o.z + tw * d.z;
+                const float* sk = h + 13;
+                const bool open = wall == 3 && sk[0] < sk[1] && px >= sk[0] && px <= sk[1] && pz >= sk[2] && pz <= sk[3];
+                if (!open) return true;
+            }
+        }
+        return false;
+    }
+
     __device__ bool intersect(float3 o, float3 d, Hit& hit) const {
         hit.kind = 0;
         hit.t = INFINITY;
