@@ -131,12 +131,13 @@ struct SceneView {
                 hit.id = i;
             }
         }
+        const float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);  // slab distances by multiplication
         for (int i = 0; i < nb; ++i) {
             const float* B = box + kBox * i;
             float tn = -INFINITY, tf = INFINITY;
             int an = 0, af = 0;
             for (int k = 0; k < 3; ++k) {
-                const float t1 = (B[k] - comp(o, k)) / comp(d, k), t2 = (B[3 + k] - comp(o, k)) / comp(d, k);
+                const float t1 = (B[k] - comp(o, k)) * comp(inv, k), t2 = (B[3 + k] - comp(o, k)) * comp(inv, k);
                 const float lo = fminf(t1, t2), hi = fmaxf(t1, t2);
                 if (lo > tn) { tn = lo; an = k; }
                 if (hi < tf) { tf = hi; af = k; }
@@ -159,8 +160,8 @@ struct SceneView {
             for (int k = 0; k < 3; ++k) {
                 const float dk = comp(d, k), ok = comp(o, k);
                 float t;
-                if (dk > 0.0f) t = (h[7 + k] - ok) / dk;
-                else if (dk < 0.0f) t = (h[4 + k] - ok) / dk;
+                if (dk > 0.0f) t = (h[7 + k] - ok) * comp(inv, k);
+                else if (dk < 0.0f) t = (h[4 + k] - ok) * comp(inv, k);
                 else continue;
                 if (t < tw) { tw = t; wall = 2 * k + (dk > 0.0f); }
             }
