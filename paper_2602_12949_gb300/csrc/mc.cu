@@ -85,8 +85,19 @@ __device__ float3 path_radiance(const SceneView& S, const Rng& rng, uint32_t j, 
                                           cs * tt.z + sn * bb.z + ct * w.z);
             const float cosl = dot3(nf, wl);
             if (cosl <= 0.0f) continue;
-            Hit hs;
-            if (!S.intersect(p, wl, hs) || hs.kind != 1 || hs.id != e) continue;
+            // the shadow ray counts when its closest hit is the emitter: the emitter's own hit
+            // distance (as intersect computes it) with nothing hit before it
+            float te;
+            {
+                const float3 oc = make_float3(p.x - c.x, p.y - c.y, p.z - c.z);
+                const float b = dot3(oc, wl), disc = b * b - (dot3(oc, oc) - r * r);
+                if (disc < 0.0f) continue;
+                const float sq = sqrtf(disc);
+                te = -b - sq;
+                if (te <= kTEps) te = -b + sq;
+                if (!(te > kTEps)) continue;
+            }
+            if (S.occluded(p, wl, te)) continue;
             const float pdf_inv = 6.283185307179586f * (1.0f - cmax);
             const float* Ee = S.sph + kSph * e + 7;
             const float f = cosl * pdf_inv * 0.3183098861837907f;
