@@ -84,6 +84,12 @@ def _run(niv, spec, pos, nrm, kw, seed=0, bias_std=0.0, cal=None):
     (MODEL_C0, {}),
     (dict(MODEL_C0, width=32, n_hidden=1), {}),
     (MODEL_C3, dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=0.4)),
+    # 16-level models: the config-1 grid (4 dense levels, a compiled shape), 5 and 3 dense
+    # levels, and a 4-D grid without dense levels (the shape-only kernels)
+    (dict(MODEL_C3, dims=3, in_extra=3, n_hidden=2, log2_T=17), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
+    (dict(MODEL_C3, dims=3, in_extra=3, n_hidden=2), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
+    (dict(MODEL_C3, dims=3, in_extra=3, n_hidden=2, log2_T=15), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
+    (dict(MODEL_C3, log2_T=15), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=0.6)),
 ])
 def test_fp8_matches_fp8_oracle(niv, spec, kw):
     lo, hi = kw.get("aabb_min", (0, 0, 0)), kw.get("aabb_max", (1, 1, 1))

@@ -106,6 +106,11 @@ def test_fp16_ragged_sizes_and_biases(niv, n):
     (MODEL_P, dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
     (MODEL_C3, dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=0.71)),
     (dict(MODEL_C0, feat=1, levels=16), {}),
+    # 16-level models beside the compiled shapes: 3 dense levels, 4 hidden layers, width 32
+    (dict(MODEL_C1, log2_T=15), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
+    (dict(MODEL_C1, n_hidden=4), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
+    (dict(MODEL_C1, width=32), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
+    (dict(MODEL_C3, log2_T=17), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=0.3)),
 ])
 def test_fp16_other_shapes(niv, spec, kw):
     m, params, om = make(niv, spec, seed=9, bias_std=0.1)
