@@ -120,22 +120,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_code_hash(paths):
+    """First 16 hex digits of the SHA-256 of C/C++/CUDA sources with their comments removed
+    and every run of whitespace collapsed to one space: the code, not its comments or layout."""
+    import hashlib
+    import re
+    tok = re.compile(r'"(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\'|//[^\n]*|/\*.*?\*/', re.S)
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p) as fh:
+            text = fh.read()
+        code = tok.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", text)
+        h.update(" ".join(code.split()).encode())
+        h.update(b"\0")
+    return h.hexdigest()[:16]
+
+
 def _profiled_record():
     """DRAM bytes and warp instructions per launch of the fused kernel from the committed ncu
-    summary, if the kernel sources are unchanged since that capture; else None."""
-    import hashlib
+    summary, if the kernel's code is unchanged since that capture; else None."""
     path = os.path.join(ROOT, "profiles", "niv_query_fp16_1080p.md")
     srcs = ["query_tc.cu", "encoding.cuh", "tc_ptx.cuh"]  # the kernel and every device helper it includes
     try:
         text = open(path).read()
         rec = dict(l.split(":", 1) for l in text.splitlines()
-                   if l.startswith(("traffic_bytes_per_launch:", "source_sha256_16:",
+                   if l.startswith(("traffic_bytes_per_launch:", "code_sha256_16:",
                                     "warp_instructions_per_launch:")))
-        h = hashlib.sha256()
-        for f in srcs:
-            with open(os.path.join(ROOT, "paper_2602_12949_gb300", "csrc", f), "rb") as fh:
-                h.update(fh.read())
-        if h.hexdigest()[:16] != rec["source_sha256_16"].strip():
+        digest = kernel_code_hash([os.path.join(ROOT, "paper_2602_12949_gb300", "csrc", f) for f in srcs])
+        if digest != rec["code_sha256_16"].strip():
             return None
         return {"traffic": int(rec["traffic_bytes_per_launch"].strip()),
                 "instructions": int(rec["warp_instructions_per_launch"].strip())}

@@ -24,7 +24,11 @@
 //
 // Tuning knobs (compile-time): NIV_TC_WG warpgroups per CTA sharing one copy of the
 // weights, NIV_TC_ILP levels whose gathers are in flight together, NIV_TC_MINB the
-// launch-bounds residency target, NIV_TC_OUT_FMA output layer on the CUDA cores.
+// launch-bounds residency target, NIV_TC_OUT_FMA output layer on the CUDA cores,
+// NIV_TC_FIXW kernels compiled for the 16-level models' network shapes (width 64, 48
+// input columns, 2 or 3 hidden layers), NIV_TC_ND those kernels also compiled for their
+// dense-level counts (NIV_BLEND_PAIRS in encoding.cuh: a corner's two features blended as
+// one packed FP32 pair).
 #include <cuda_fp8.h>
 #include <string.h>
 

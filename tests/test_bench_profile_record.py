@@ -1,6 +1,6 @@
 """bench.py reports the ncu traffic and instruction count of the fused kernel from the
-committed profile summary only while the kernel sources hash to the value recorded there:
-a changed source must drop both (host logic, no GPU)."""
+committed profile summary only while the kernel's code hashes to the value recorded there:
+a code change must drop both, a comment or layout change must not (host logic, no GPU)."""
 import os
 import shutil
 
@@ -23,9 +23,21 @@ def test_record_follows_the_source_hash(tmp_path, monkeypatch):
     if rec is None:  # the committed summary predates the current sources: nothing to report
         return
     assert rec["traffic"] > 0 and rec["instructions"] > 0
-    with open(root / "paper_2602_12949_gb300" / "csrc" / "query_tc.cu", "a") as f:
-        f.write("\n// edited\n")
+    src = root / "paper_2602_12949_gb300" / "csrc" / "query_tc.cu"
+    text = src.read_text()
+    src.write_text("// a new comment line\n/* and a block\n   comment */\n" + text.replace("\n", "\n\n", 3) + "\n// end\n")
+    assert bench._profiled_record() == rec
+    src.write_text(text + "\nstatic const int edited_code = 1;\n")
     assert bench._profiled_record() is None
+
+
+def test_code_hash_keeps_strings_and_drops_comments(tmp_path):
+    a, b, c = tmp_path / "a.cu", tmp_path / "b.cu", tmp_path / "c.cu"
+    a.write_text('asm("ld.x [%0]; // not a comment");  // a comment\nint x = 1;\n')
+    b.write_text('asm("ld.x [%0]; // not a comment");\n\n   int x = 1; /* another */\n')
+    c.write_text('asm("ld.x [%0]; // changed");\nint x = 1;\n')
+    assert bench.kernel_code_hash([a]) == bench.kernel_code_hash([b])
+    assert bench.kernel_code_hash([a]) != bench.kernel_code_hash([c])
 
 
 def test_missing_or_garbled_summary_gives_none(tmp_path, monkeypatch):
