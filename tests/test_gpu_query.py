@@ -176,8 +176,8 @@ def test_chunked_host_query_matches_device_query(niv, width, rows, n_extra, prec
     m.close()
 
 
-@pytest.mark.parametrize("mode", ["0", "1"])
-def test_pinned_host_query_follows_buffer_contents_and_arguments(niv, mode, monkeypatch):
+@pytest.mark.parametrize("mode,rec", [("0", np.float16), ("1", np.float16), ("0", np.float32)])
+def test_pinned_host_query_follows_buffer_contents_and_arguments(niv, mode, rec, monkeypatch):
     # page-locked buffers: mode 0 lets one query read and write host memory directly; mode 1
     # stages them through device memory in overlapped chunks.  Each call must read the
     # buffers' current contents, and new arguments (another output buffer, new parameters,
@@ -187,17 +187,18 @@ def test_pinned_host_query_follows_buffer_contents_and_arguments(niv, mode, monk
     W, H = 640, 360
     n = W * H
     pos, nrm = uniform_queries(n, seed=7)
-    hp = torch.from_numpy(pos.astype(np.float16)).pin_memory()
-    hn = torch.from_numpy(nrm.astype(np.float16)).pin_memory()
-    ho = torch.empty((n, 4), dtype=torch.float16).pin_memory()
+    tdt = torch.float16 if rec == np.float16 else torch.float32
+    hp = torch.from_numpy(pos.astype(rec)).pin_memory()
+    hn = torch.from_numpy(nrm.astype(rec)).pin_memory()
+    ho = torch.empty((n, 4), dtype=tdt).pin_memory()
     kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, image_width=W)
 
     def device(**extra):
-        return m.query(hp.cuda(), hn.cuda(), precision="fp16", out_dtype=torch.float16, **dict(kw, **extra)).cpu()
+        return m.query(hp.cuda(), hn.cuda(), precision="fp16", out_dtype=tdt, **dict(kw, **extra)).cpu()
 
     for call in range(5):
         if call == 3:  # new contents in the same buffers
-            hp.copy_(torch.from_numpy(uniform_queries(n, seed=8)[0].astype(np.float16)))
+            hp.copy_(torch.from_numpy(uniform_queries(n, seed=8)[0].astype(rec)))
         m.query_host(hp.numpy(), hn.numpy(), out=ho.numpy(), precision="fp16", **kw)
         assert torch.equal(ho, device()), call
     ho2 = torch.empty_like(ho).pin_memory()
@@ -209,7 +210,7 @@ def test_pinned_host_query_follows_buffer_contents_and_arguments(niv, mode, monk
         m.query_host(hp.numpy(), hn.numpy(), out=ho.numpy(), precision="fp16", **kw)
         assert torch.equal(ho, device()), call
     m.query_host(hp.numpy(), hn.numpy(), out=ho.numpy(), precision="fp32", **kw)
-    assert torch.equal(ho, m.query(hp.cuda(), hn.cuda(), precision="fp32", out_dtype=torch.float16, **kw).cpu())
+    assert torch.equal(ho, m.query(hp.cuda(), hn.cuda(), precision="fp32", out_dtype=tdt, **kw).cpu())
     m.close()
 
 
