@@ -162,6 +162,24 @@ NIV_API int niv_set_params(niv_handle h, const float* params, int64_t n, niv_str
 NIV_API int niv_get_params(niv_handle h, float* out, int64_t n, niv_stream stream);
 
 /*
+ * Save a model to a file, and load one into a new handle on the current device.  The
+ * file holds, little-endian: the 4 bytes "NIVM", uint32 format version 1; the model
+ * description field by field in the order of niv_model_desc (int32 dims, levels, feat,
+ * log2_T; float64 base, growth; int32 n_hidden, width, in_extra, out_dim, out_act;
+ * uint32 prime_t; int32 pe_bands, t_bands); int64 n; then the n FP32 master parameters in
+ * the order of niv_set_params.  The Adam state is not saved (a loaded model starts a new
+ * optimisation).
+ *  - niv_save synchronises `stream` (the parameters are read from the device).
+ *  - niv_load reads and checks the header before it touches the device: a missing file,
+ *    another magic or version, or a description that niv_create refuses is NIV_ERR_ARG
+ *    with a message.  A parameter count that differs from the description's, or a short
+ *    file, is NIV_ERR_ARG too (the model created for it is released again).  On any
+ *    error *out is unchanged.
+ */
+NIV_API int niv_save(niv_handle h, const char* path, niv_stream stream);
+NIV_API int niv_load(const char* path, niv_handle* out);
+
+/*
  * The per-pixel query (Sec. 4.4): E = net(encode(u(p)), n, t) for n records.
  * pos, nrm: device [n][4] records of type dtype_in (NIV_F32 / NIV_F16);
  * out_E: device [n][4] records of type dtype_out holding E.rgb and 0.

@@ -331,6 +331,96 @@ int niv_get_params(niv_handle h, float* out, int64_t n, niv_stream stream) {
     return NIV_OK;
 }
 
+namespace {
+// Model files (little-endian hosts): "NIVM", version, the description field by field, the
+// parameter count, the FP32 parameters.
+constexpr char kFileMagic[4] = {'N', 'I', 'V', 'M'};
+constexpr uint32_t kFileVersion = 1;
+
+bool put_bytes(FILE* f, const void* v, size_t n) { return fwrite(v, n, 1, f) == 1; }
+bool get_bytes(FILE* f, void* v, size_t n) { return fread(v, n, 1, f) == 1; }
+#define put(f, v) put_bytes((f), &(v), sizeof(v))
+#define get(f, v) get_bytes((f), &(v), sizeof(v))
+
+bool put_desc(FILE* f, const niv_model_desc& d) {
+    return put(f, d.dims) && put(f, d.levels) && put(f, d.feat) && put(f, d.log2_T) && put(f, d.base) &&
+           put(f, d.growth) && put(f, d.n_hidden) && put(f, d.width) && put(f, d.in_extra) && put(f, d.out_dim) &&
+           put(f, d.out_act) && put(f, d.prime_t) && put(f, d.pe_bands) && put(f, d.t_bands);
+}
+bool get_desc(FILE* f, niv_model_desc& d) {
+    return get(f, d.dims) && get(f, d.levels) && get(f, d.feat) && get(f, d.log2_T) && get(f, d.base) &&
+           get(f, d.growth) && get(f, d.n_hidden) && get(f, d.width) && get(f, d.in_extra) && get(f, d.out_dim) &&
+           get(f, d.out_act) && get(f, d.prime_t) && get(f, d.pe_bands) && get(f, d.t_bands);
+}
+}  // namespace
+
+int niv_save(niv_handle h, const char* path, niv_stream stream) {
+    if (!h || !path) return niv_fail(NIV_ERR_ARG, "handle or path is NULL");
+    const int64_t n = h->n_grid + h->n_mlp;
+    std::vector<float> params((size_t)n);
+    int rc = niv_get_params(h, params.data(), n, stream);
+    if (rc) return rc;
+    FILE* f = fopen(path, "wb");
+    if (!f) return niv_fail(NIV_ERR_ARG, std::string("cannot open for writing: ") + path);
+    bool ok = fwrite(kFileMagic, 1, 4, f) == 4 && put(f, kFileVersion) && put_desc(f, h->d) && put(f, n) &&
+              fwrite(params.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return niv_fail(NIV_ERR_ARG, std::string("write failed: ") + path);
+    return NIV_OK;
+}
+
+int niv_load(const char* path, niv_handle* out) {
+    if (!path || !out) return niv_fail(NIV_ERR_ARG, "path or out is NULL");
+    FILE* f = fopen(path, "rb");
+    if (!f) return niv_fail(NIV_ERR_ARG, std::string("cannot open: ") + path);
+    char magic[4];
+    uint32_t version = 0;
+    niv_model_desc d;
+    memset(&d, 0, sizeof d);
+    int64_t n = 0;
+    if (fread(magic, 1, 4, f) != 4 || memcmp(magic, kFileMagic, 4) != 0 || !get(f, version)) {
+        fclose(f);
+        return niv_fail(NIV_ERR_ARG, "not a model file (magic)");
+    }
+    if (version != kFileVersion || !get_desc(f, d) || !get(f, n)) {
+        fclose(f);
+        return niv_fail(NIV_ERR_ARG, "unsupported model file version or truncated header");
+    }
+    int rc = validate_desc(&d);
+    if (rc) {
+        fclose(f);
+        return rc;
+    }
+    niv_handle h = nullptr;
+    rc = niv_create(&d, &h);
+    if (rc) {
+        fclose(f);
+        return rc;
+    }
+    if (n != h->n_grid + h->n_mlp) {
+        fclose(f);
+        niv_destroy(h);
+        return niv_fail(NIV_ERR_ARG, "parameter count differs from the description's");
+    }
+    std::vector<float> params((size_t)n);
+    const bool full = fread(params.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+    fclose(f);
+    if (!full) {
+        niv_destroy(h);
+        return niv_fail(NIV_ERR_ARG, "model file truncated");
+    }
+    rc = niv_set_params(h, params.data(), n, nullptr);
+    if (rc) {
+        niv_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return NIV_OK;
+}
+
+#undef put
+#undef get
+
 int niv_query(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
               const niv_query_params* params, void* out_E, int32_t dtype_out, int32_t precision,
               niv_stream stream) {

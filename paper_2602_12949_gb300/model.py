@@ -4,6 +4,8 @@ Tensors are plain containers here (device memory and streams); every step of
 the query, shading, training and Monte Carlo paths runs in libniv's kernels.
 """
 import ctypes
+import os
+import struct
 
 import numpy as np
 import torch
@@ -46,6 +48,26 @@ class NIVModel:
         h = ctypes.c_void_p()
         check(lib().niv_create(ctypes.byref(self.desc), ctypes.byref(h)))
         self._h = h
+
+    # model files: "NIVM", version 1, the description field by field, the count, the FP32 parameters
+    _FILE_HEAD = struct.Struct("<4sI4i2d5iI2iq")
+
+    def save(self, path, stream=None):
+        """Write the description and the FP32 master parameters to `path` (niv_save)."""
+        check(lib().niv_save(self._h, os.fsencode(path), _stream(stream)))
+
+    @classmethod
+    def load(cls, path):
+        """A model read from a file written by save (niv_load), on the current device."""
+        with open(path, "rb") as f:
+            head = f.read(cls._FILE_HEAD.size)
+        h = ctypes.c_void_p()
+        check(lib().niv_load(os.fsencode(path), ctypes.byref(h)))  # checks the header itself
+        fields = cls._FILE_HEAD.unpack(head)[2:16]
+        self = cls.__new__(cls)
+        self.desc = ModelDesc(*fields)
+        self._h = h
+        return self
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -70,3 +70,28 @@ def test_null_handles_are_rejected(libniv):
     assert libniv.niv_param_count(None, None, None) == NIV_ERR_ARG
     assert libniv.niv_shade(None, None, None, 4, None, None) == NIV_ERR_ARG
     assert libniv.niv_destroy(None) == 0
+
+
+def test_model_files_are_checked_before_the_device(libniv, tmp_path):
+    # niv_load refuses a missing file, a foreign file, another format version and a bad
+    # description on the host, leaving *out unchanged
+    import struct
+    from paper_2602_12949_gb300._lib import NIV_ERR_ARG
+    h = ctypes.c_void_p(1234)
+    assert libniv.niv_load(str(tmp_path / "missing.niv").encode(), ctypes.byref(h)) == NIV_ERR_ARG
+    foreign = tmp_path / "foreign.niv"
+    foreign.write_bytes(b"PK\x03\x04" + bytes(100))
+    assert libniv.niv_load(str(foreign).encode(), ctypes.byref(h)) == NIV_ERR_ARG
+    assert b"magic" in libniv.niv_last_error()
+    head = struct.Struct("<4sI4i2d5iI2iq")
+    newer = tmp_path / "newer.niv"
+    newer.write_bytes(head.pack(b"NIVM", 2, 3, 8, 2, 14, 4.0, 1.5, 2, 64, 3, 3, 1, 1, 0, 0, 10))
+    assert libniv.niv_load(str(newer).encode(), ctypes.byref(h)) == NIV_ERR_ARG
+    bad_desc = tmp_path / "bad.niv"
+    bad_desc.write_bytes(head.pack(b"NIVM", 1, 5, 8, 2, 14, 4.0, 1.5, 2, 64, 3, 3, 1, 1, 0, 0, 10))  # dims 5
+    assert libniv.niv_load(str(bad_desc).encode(), ctypes.byref(h)) == NIV_ERR_ARG
+    short = tmp_path / "short.niv"
+    short.write_bytes(b"NIVM\x01\x00\x00\x00" + bytes(6))
+    assert libniv.niv_load(str(short).encode(), ctypes.byref(h)) == NIV_ERR_ARG
+    assert h.value == 1234
+    assert libniv.niv_save(None, b"x", None) == NIV_ERR_ARG

@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 from niv_inputs import init_params, uniform_queries
-from niv_inputs.configs import MODEL_C0, MODEL_C1, MODEL_C3, ROOM_MIN, ROOM_MAX, room_gbuffer
+from niv_inputs.configs import MODEL_C0, MODEL_C1, MODEL_C3, MODEL_PE16, ROOM_MIN, ROOM_MAX, room_gbuffer
 
 pytestmark = pytest.mark.gpu
 
@@ -212,6 +212,24 @@ def test_pinned_host_query_follows_buffer_contents_and_arguments(niv, mode, rec,
     m.query_host(hp.numpy(), hn.numpy(), out=ho.numpy(), precision="fp32", **kw)
     assert torch.equal(ho, m.query(hp.cuda(), hn.cuda(), precision="fp32", out_dtype=tdt, **kw).cpu())
     m.close()
+
+
+def test_save_and_load_round_trip(niv, tmp_path):
+    # the file keeps the description and the FP32 master parameters bit for bit; a model
+    # loaded from it answers queries exactly as the saved one
+    for spec in (MODEL_C1, MODEL_C3, MODEL_PE16):
+        m, params, om = make(niv, spec, seed=11, bias_std=0.1)
+        path = tmp_path / "model.niv"
+        m.save(path)
+        m2 = niv.NIVModel.load(path)
+        assert m2.param_count() == m.param_count()
+        np.testing.assert_array_equal(m2.get_params(), m.get_params())
+        pos, nrm = uniform_queries(4096 + 5, seed=12)
+        dp, dn = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+        for prec in ("fp32", "fp16"):
+            assert torch.equal(m2.query(dp, dn, precision=prec, t=0.3), m.query(dp, dn, precision=prec, t=0.3))
+        m.close()
+        m2.close()
 
 
 def test_shade_matches_oracle(niv):
