@@ -47,7 +47,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison and error checks")
     ap.add_argument("--workload", default="config1",
-                    choices=["config1", "config3", "half", "sweep", "train", "time", "config2"],
+                    choices=["config1", "config3", "half", "sweep", "train", "time", "config2", "peaks"],
                     help="config1: the headline (config-1 model on the room frame); config3: the 4-D model at "
                          "--res with t from the seed; half: quarter-pixel query + upsampling and shading; "
                          "sweep: memory-error trade-off (hash table sizes against probes of equal memory); "
@@ -67,6 +67,21 @@ def _peaks():
         return {"hbm": p["hbm_gbs"], "tensor": p["bf16_tflops"], "src": "measured"}
     except Exception:
         return {"hbm": 6800.0, "tensor": 1900.0, "src": "fallback"}
+
+
+def _extra_peaks():
+    """FP32 FMA, FP8 tensor and L2 read rates measured by `bench.py --workload peaks` on this
+    GPU model and recorded in profiles/measured_peaks_gb300.md; {} when absent."""
+    out = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", "measured_peaks_gb300.md")) as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("fp32_ffma_tflops", "fp8_tflops", "l2_read_gbs"):
+                    out[k.strip()] = float(v.strip())
+    except (OSError, ValueError):
+        pass
+    return out
 
 
 class ClockSampler:
@@ -381,6 +396,57 @@ def _table1_and_half(dev, flush, stream, dpos, dnrm, steps, warmup):
     return {"table1_1080p_fp16": rows, "half_1080p_config1": half}
 
 
+def run_peaks(a):
+    """Rates the roofline of the other paths needs, measured on this GPU: FP32 FMA (the
+    library's probe kernel, independent FMA chains on every thread), FP8 dense tensor
+    (torch._scaled_mm, E4M3 8192^3) and L2 read bandwidth (torch sum over a 64 MiB tensor,
+    L2-resident after the first pass).  Best of the timed repetitions, CUDA events."""
+    import ctypes
+    import torch
+    from paper_2602_12949_gb300._lib import check, lib
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+
+    def best(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            fn()
+            e0.record(stream)
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(e0))
+        return min(ts)  # ms
+
+    res = {}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = sms * 8 * 4, 8192
+    buf = torch.zeros(blocks, device=dev)
+    ms = best(lambda: check(lib().niv_peak_ffma(ctypes.c_void_p(buf.data_ptr()), blocks, iters,
+                                                ctypes.c_void_p(stream.cuda_stream))), 10)
+    res["fp32_ffma_tflops"] = 2.0 * 8 * iters * 256 * blocks / (ms * 1e-3) / 1e12
+    try:
+        n = 8192
+        a8 = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn)
+        b8 = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device=dev)
+        ms = best(lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16), 10)
+        res["fp8_tflops"] = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+    except Exception as e:  # FP8 GEMM not offered by this torch build
+        res["fp8_tflops"] = None
+        res["fp8_error"] = str(e)[:200]
+    x = torch.ones(16 << 20, device=dev)  # 64 MiB of FP32
+    ms = best(lambda: x.sum(), 50)
+    res["l2_read_gbs"] = x.numel() * 4 / (ms * 1e-3) / 1e9
+    line = {"metric": "measured peaks for the rooflines beside the tensor one", "value": res["fp32_ffma_tflops"],
+            "unit": "TFLOP/s (FP32 FMA)", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "peaks": res, "gpu": torch.cuda.get_device_name(dev), "sms": sms}
+    print(json.dumps(line), flush=True)
+
+
 def run_sweep(a):
     """Memory-error trade-off on the seeded room: NIV (config-1 shape) trained at hash table
     sizes 2^13 .. 2^19 against the SH probe grid of the same memory, with and without
@@ -545,6 +611,9 @@ def run_workload(a):
     if a.workload == "sweep":
         run_sweep(a)
         return
+    if a.workload == "peaks":
+        run_peaks(a)
+        return
     if a.workload == "train":
         run_train(a)
         return
@@ -565,6 +634,7 @@ def run_workload(a):
     stream = torch.cuda.current_stream()
     peaks = _peaks()
     kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)
+    fp8_measured = None
     if a.workload == "config3":
         pos, nrm, _ = room_gbuffer(W, H)
         dp, dn = torch.from_numpy(pos).to(dev), torch.from_numpy(nrm).to(dev)
@@ -577,7 +647,9 @@ def run_workload(a):
         out = torch.empty((npx, 4), dtype=torch.float32 if a.precision == "fp32" else torch.float16, device=dev)
         step = lambda: m.query(dp, dn, out=out, precision=a.precision, t=t, image_width=W, **kw)
         flop = 2 * (36 * 64 + 2 * 64 * 64 + 64 * 3)  # 21,376 per query
-        tensor_peak = peaks["tensor"] * (2.0 if a.precision == "fp8" else 1.0)  # FP8 dense rate = 2x BF16
+        fp8_measured = _extra_peaks().get("fp8_tflops") if a.precision == "fp8" else None
+        # FP8: the measured E4M3 rate, else the nominal 2x of the measured BF16 one
+        tensor_peak = fp8_measured or peaks["tensor"] * (2.0 if a.precision == "fp8" else 1.0)
         config = {"workload": "config3-%s: 4-D model (16 levels x 2 features, T=2^19, 36-64-64-64-3) on the "
                               "%dx%d room frame, t=%.4f" % (a.res, W, H, t), "pixels": npx, "precision": a.precision}
         unit_per_step = npx
@@ -621,8 +693,10 @@ def run_workload(a):
             "config": dict(config, l2="flushed between steps (256 MB write)", parallelism="single"),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": tensor_peak, "unit": "TFLOP/s",
                          "frac": achieved / tensor_peak, "traffic": None,
-                         "peak_source": "%s bf16 burst%s" % (peaks["src"], " x 2 (FP8 dense rate)"
-                                                            if a.precision == "fp8" else "")},
+                         "peak_source": ("measured E4M3 dense rate (profiles/measured_peaks_gb300.md)"
+                                         if fp8_measured else
+                                         "%s bf16 burst%s" % (peaks["src"], " x 2 (FP8 dense rate)"
+                                                              if a.precision == "fp8" else ""))},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     m.close()
@@ -692,6 +766,12 @@ def main():
         ms32 = timed("fp32", out32, max(5, a.steps // 2), 3)
         extra["fp32_plain"] = {"ms_per_frame": statistics.mean(ms32),
                                "gqueries_per_s": npx / (statistics.mean(ms32) * 1e-3) / 1e9}
+        ffma = _extra_peaks().get("fp32_ffma_tflops")
+        if ffma:  # the plain path's network on the FP32 FMA pipes (SURVEY's FP32-plain bound)
+            ach = FLOP_PER_QUERY["c1"] * npx / (statistics.mean(ms32) * 1e-3) / 1e12
+            extra["fp32_plain"]["roofline"] = {"bound": "ffma", "achieved": ach, "peak": ffma, "unit": "TFLOP/s",
+                                               "frac": ach / ffma,
+                                               "peak_source": "measured (profiles/measured_peaks_gb300.md)"}
         extra["more"] = _more_workloads(a, dev, flush, stream)
 
     # e2e: page-locked host buffers through niv_query_host, which lets the query kernel read
@@ -751,7 +831,20 @@ def main():
         dt = time.perf_counter() - t0
         cpu = {"value": sample / dt / 1e9, "unit": "Gqueries/s", "cores": _oracle_threads(), "kind": "oracle",
                "sample": "%d random pixels of the frame, FP64 C oracle (OpenMP)" % sample,
-               "ms_per_frame_extrapolated": 1e3 * dt * npx / sample}
+               "ms_per_frame_extrapolated": 1e3 * dt * npx / sample,
+               "ms_per_4k_frame_extrapolated": 4e3 * dt * npx / sample}
+        # the same oracle on one host core, over a sixteenth of the sample
+        all_cores = _oracle_threads()
+        oracle.lib().orc_set_num_threads(1)
+        try:
+            s1 = sample // 16
+            t0 = time.perf_counter()
+            oracle.query(om, params, p32[:s1], n32[:s1], ROOM_MIN, ROOM_MAX)
+            dt1 = time.perf_counter() - t0
+        finally:
+            oracle.lib().orc_set_num_threads(all_cores)
+        cpu["one_core"] = {"value": s1 / dt1 / 1e9, "unit": "Gqueries/s", "cores": 1,
+                           "sample": "%d of those pixels" % s1, "ms_per_frame_extrapolated": 1e3 * dt1 * npx / s1}
         got = out[pick, :3].double().cpu().numpy()
         den = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
         errs[a.precision] = {"max_rel": float(np.max(np.abs(got - ref) / den)),

@@ -96,6 +96,8 @@ def lib():
         vp = ctypes.c_void_p
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_num_threads.argtypes = []
+        L.orc_set_num_threads.restype = None
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
         L.orc_layout.restype = i64
         L.orc_layout.argtypes = [P(Desc), vp, vp, vp, vp]
         L.orc_mlp_param_count.restype = i64

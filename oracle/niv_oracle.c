@@ -85,6 +85,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the following parallel loops (timing on a given number of host cores). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 static const uint32_t ORC_PI[3] = {1u, 2654435761u, 805459861u};
 
 /* ---- FP32 operations emulated in FP64 (exact: operands are floats) ---- */
