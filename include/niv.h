@@ -387,6 +387,12 @@ NIV_API int niv_probe_query_rt(const void* coef16, const int32_t* P, const float
  *    capture begins.
  *  - Every call shares the one array, which keeps the last call's contents; calls
  *    whose work overlaps on the GPU race with each other, so serialise them.
+ *  - The model's parameters must have been set (niv_set_params or niv_load):
+ *    otherwise NIV_ERR_ARG.  After training steps the call first rebuilds the
+ *    model's inference copies in place, as niv_query does (no allocation).
+ *  - The array's address is cached per device ordinal for the life of the
+ *    process: do not reset a device (cudaDeviceReset) while this library is
+ *    loaded.  The library's device status word is cached the same way.
  */
 NIV_API int niv_query_host_noalloc(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
                                    const niv_query_params* params, void* out_E, int32_t dtype_out,

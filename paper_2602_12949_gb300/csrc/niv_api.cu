@@ -134,6 +134,8 @@ int ensure_training_state(niv_model* h) {
 
 }  // namespace
 
+int niv_refresh_inference(niv_model* m, cudaStream_t s) { return refresh_inference(m, s); }
+
 int niv_env_int(const char* name, int dflt) {
     const char* v = getenv(name);
     return (v && *v) ? atoi(v) : dflt;
@@ -478,12 +480,12 @@ struct HostChunks {
     int count;
 };
 
-// Chunks of whole tiles (whole 8-row bands of 16 x 8-pixel tiles for images) of about two
+// Chunks of whole tiles (whole bands of NIV_TILE_ROWS rows of tiles for images) of about two
 // waves of the tensor-core kernel (8 warpgroups on every SM), at least 65,536 records
 // each and at most NIV_HOST_CHUNKS_MAX of them; NIV_HOST_CHUNKS sets the count instead.
 HostChunks host_chunks(int64_t n, int64_t W) {
-    const int64_t granule = W > 0 ? 8 * W : 128;  // records of one band / one tile
-    const int64_t granule_tiles = W > 0 ? (W + 15) / 16 : 1;
+    const int64_t granule = W > 0 ? NIV_TILE_ROWS * W : 128;  // records of one band / one tile
+    const int64_t granule_tiles = W > 0 ? (W + kTileW - 1) / kTileW : 1;
     const int64_t granules = (n + granule - 1) / granule;
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

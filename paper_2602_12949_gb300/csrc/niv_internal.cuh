@@ -79,6 +79,10 @@ int* niv_status_word();
 
 GridArgs niv_grid_args(const niv_model* m, const niv_query_params* p);
 
+// Rebuild the FP16 grid and the packed networks from the FP32 master parameters (after
+// training steps).  Allocates device memory only when no network was packed before.
+int niv_refresh_inference(niv_model* m, cudaStream_t s);
+
 // Integer value of an environment variable (tuning and diagnostics), or dflt.
 int niv_env_int(const char* name, int dflt);
 

@@ -68,8 +68,18 @@ extern "C" int niv_query_host_noalloc(niv_handle h, const void* pos, const void*
     NIV_CUDA(cudaGetDevice(&dev));
     if (dev != h->device) return niv_fail(NIV_ERR_ARG, "current device differs from the model's device");
 
+    // The inference copies must exist already (refreshing them then allocates nothing): a
+    // model straight from niv_create has no packed network.
+    if (!h->mlp_tc) return niv_fail(NIV_ERR_ARG, "parameters not set: call niv_set_params or niv_load first");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = 0;
+    if (h->infer_dirty) {  // trained since the inference copies were built
+        rc = niv_refresh_inference(h, s);
+        if (rc) return rc;
+    }
+
     unsigned char* base = nullptr;
-    int rc = scratch_address(&base);
+    rc = scratch_address(&base);
     if (rc) return rc;
     int* status = reinterpret_cast<int*>(base);
     unsigned char* d_pos = base + kStatusBytes;
@@ -77,7 +87,6 @@ extern "C" int niv_query_host_noalloc(niv_handle h, const void* pos, const void*
     unsigned char* d_out = d_nrm + kArea;
     const size_t in_b = (size_t)n * (dtype_in == NIV_F16 ? 8 : 16);
     const size_t out_b = (size_t)n * (dtype_out == NIV_F16 ? 8 : 16);
-    cudaStream_t s = (cudaStream_t)stream;
 
     NIV_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));  // the array keeps the last call's status
     NIV_CUDA(cudaMemcpyAsync(d_pos, pos, in_b, cudaMemcpyHostToDevice, s));
@@ -92,7 +101,10 @@ extern "C" int niv_query_host_noalloc(niv_handle h, const void* pos, const void*
     io.in_f16 = dtype_in == NIV_F16;
     io.out_f16 = dtype_out == NIV_F16;
     rc = precision == NIV_FP32 ? niv_launch_query_fp32(h, g, io, s) : niv_launch_query_tc(h, g, io, precision, s, status);
-    if (rc) return rc;
+    if (rc) {
+        cudaStreamSynchronize(s);  // the queued copies may still read the caller's buffers
+        return rc;
+    }
     NIV_CUDA(cudaMemcpyAsync(out_E, d_out, out_b, cudaMemcpyDeviceToHost, s));
     int st = 0;
     NIV_CUDA(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s));

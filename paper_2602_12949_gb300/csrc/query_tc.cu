@@ -594,6 +594,9 @@ int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s) {
 int niv_launch_query_tc(const niv_model* m, const GridArgs& g, const IoArgs& io, int precision, cudaStream_t s,
                         int* status) {
     if (precision != NIV_FP16) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core path: precision not supported");
+    // niv_create leaves the packed network unset (a zero layout would pass the shape checks
+    // below and launch the kernel on a null weight pointer)
+    if (!m->mlp_tc) return niv_fail(NIV_ERR_ARG, "parameters not set: call niv_set_params or niv_load first");
     const TcLayout* lay = reinterpret_cast<const TcLayout*>(m->tc_layout);
     if (lay->K1 > 128) return niv_fail(NIV_ERR_UNSUPPORTED, "tensor-core path needs a network input of <= 120 values");
     return m->d.dims == 4 ? by_feat<4>(m, g, io, s, status) : by_feat<3>(m, g, io, s, status);

@@ -243,3 +243,18 @@ def test_shade_matches_oracle(niv):
     # one FP16 rounding of the result: half an ulp, 2^-11 relative
     np.testing.assert_allclose(out[:, :3].astype(np.float64), ref, rtol=2.0 ** -11, atol=1e-7)
     assert np.all(out[:, 3] == 1.0)
+
+
+def test_fp16_query_before_parameters_are_set_is_refused(niv):
+    """A model straight from niv_create has no packed network: the tensor-core query returns
+    NIV_ERR_ARG on the host and launches nothing; the FP32 path runs on the zero network."""
+    m = niv.NIVModel(**MODEL_C0)
+    pos, nrm = uniform_queries(1000, seed=5)
+    dpos, dnrm = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+    with pytest.raises(niv.NivError) as ei:
+        m.query(dpos, dnrm, precision="fp16", out_dtype=torch.float32)
+    assert ei.value.code == -1 and "parameters not set" in str(ei.value)
+    E = m.query(dpos, dnrm, precision="fp32", out_dtype=torch.float32)
+    niv.sync_status()
+    np.testing.assert_allclose(E[:, :3].cpu().numpy(), np.log(2.0), rtol=1e-6)  # softplus(0)
+    m.close()

@@ -70,3 +70,33 @@ def test_noalloc_rejects_more_than_its_capacity(niv):
     assert rc == -1
     assert b"NIV_NOALLOC_MAX_RECORDS" in niv.lib().niv_last_error()
     m.close()
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp32"])
+def test_noalloc_query_after_a_training_step_uses_the_trained_parameters(niv, precision):
+    """An Adam step changes the FP32 master parameters on the device; the allocation-free
+    call must rebuild the inference copies first, as niv_query does, so both agree."""
+    m = niv.NIVModel(**MODEL_C1)
+    g, _ = m.param_count()
+    m.set_params(init_params(g, m.layer_shapes(), seed=12, bias_std=0.1))
+    tpos, tnrm = uniform_queries(8192, seed=7, lo=ROOM_MIN, hi=ROOM_MAX, dtype=np.float32)
+    target = np.zeros_like(tpos)
+    target[:, :3] = np.random.default_rng(8).uniform(0.1, 2.0, (len(tpos), 3))
+    m.fit(torch.from_numpy(tpos).cuda(), torch.from_numpy(tnrm).cuda(), torch.from_numpy(target).cuda(),
+          aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, lr=1e-2)
+    pos, nrm = uniform_queries(30000 + 5, seed=9, lo=ROOM_MIN, hi=ROOM_MAX, dtype=np.float16)
+    qp = m.query_params(ROOM_MIN, ROOM_MAX, 0.0, 0)
+    rc, out = _noalloc(niv, m, pos, nrm, precision, qp)  # first: the call that must refresh
+    assert rc == 0, niv.lib().niv_last_error()
+    ref = m.query_host(pos, nrm, precision=precision, aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)
+    np.testing.assert_array_equal(out, ref)
+    m.close()
+
+
+def test_noalloc_refuses_a_model_without_parameters(niv):
+    m = niv.NIVModel(**MODEL_C1)
+    pos, nrm = uniform_queries(100, seed=2, dtype=np.float16)
+    rc, _ = _noalloc(niv, m, pos, nrm, "fp16", m.query_params(ROOM_MIN, ROOM_MAX, 0.0, 0))
+    assert rc == -1
+    assert b"parameters not set" in niv.lib().niv_last_error()
+    m.close()
