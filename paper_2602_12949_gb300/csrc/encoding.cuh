@@ -287,15 +287,37 @@ __device__ __forceinline__ void niv_encode_level(const GridArgs& g, const TabT* 
     niv_level_blend<NC, F>(raw, wc, acc);
 }
 
+// Image tiles: NIV_TILE_W x (128 / NIV_TILE_W) pixels, each warp of a tile an NIV_WARP_W x
+// (32 / NIV_WARP_W) block, the warps row-major in the tile.
+#ifndef NIV_TILE_W
+#define NIV_TILE_W 16
+#endif
+#ifndef NIV_WARP_W
+#define NIV_WARP_W 8
+#endif
+constexpr int kTileW = NIV_TILE_W, kTileH = 128 / NIV_TILE_W;
+constexpr int kWarpW = NIV_WARP_W, kWarpH = 32 / NIV_WARP_W;
+static_assert(kTileW * kTileH == 128 && kWarpW * kWarpH == 32 && kTileW % kWarpW == 0 && kTileH % kWarpH == 0,
+              "tile and warp shapes must tile 128 and 32 records");
+// Rows of a whole band of tiles (host-side chunking works in whole bands).
+#define NIV_TILE_ROWS (128 / NIV_TILE_W)
+
+// Pixel offset (x, y) of thread slot k inside its tile.
+__host__ __device__ __forceinline__ int niv_slot_x(int k) {
+    return ((k >> 5) % (kTileW / kWarpW)) * kWarpW + (k & 31) % kWarpW;
+}
+__host__ __device__ __forceinline__ int niv_slot_y(int k) {
+    return ((k >> 5) / (kTileW / kWarpW)) * kWarpH + (k & 31) / kWarpW;
+}
+
 // Linear record index of thread slot `k` of tile `tile` (128-record tiles).  For images a tile
-// is a 16 x 8 pixel block and each warp of it an 8 x 4 sub-block, so the 32 queries of a warp
-// are as compact on screen (and so in the scene) as possible.
+// is a kTileW x kTileH pixel block and each warp of it a kWarpW x kWarpH sub-block, so the 32
+// queries of a warp are close on screen (and so in the scene).
 __device__ __forceinline__ int64_t niv_record_of(int64_t tile, int k, int64_t n, int32_t width) {
     if (width <= 0) return tile * 128 + k;
-    int64_t tiles_x = (width + 15) / 16;
+    int64_t tiles_x = (width + kTileW - 1) / kTileW;
     int64_t ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    const int w = k >> 5, lane = k & 31;
-    int64_t px = tx * 16 + (w & 1) * 8 + (lane & 7), py = ty * 8 + (w >> 1) * 4 + (lane >> 3);
+    int64_t px = tx * kTileW + niv_slot_x(k), py = ty * kTileH + niv_slot_y(k);
     if (px >= width) return n;  // outside the image: no record
     return py * width + px;
 }
@@ -310,10 +332,9 @@ struct NivTileWalk {
     __device__ __forceinline__ void init(int64_t first, int64_t step, int k, int32_t width) {
         tile = first;
         stride = step;
-        const int w = k >> 5, lane = k & 31;
-        ox = (w & 1) * 8 + (lane & 7);
-        oy = (w >> 1) * 4 + (lane >> 3);
-        tiles_x = width > 0 ? (width + 15) / 16 : 1;
+        ox = niv_slot_x(k);
+        oy = niv_slot_y(k);
+        tiles_x = width > 0 ? (width + kTileW - 1) / kTileW : 1;
         ty = first / tiles_x;
         tx = (int32_t)(first - ty * tiles_x);
         sy = step / tiles_x;
@@ -331,28 +352,24 @@ struct NivTileWalk {
     // Record of thread slot k (n: outside the image).
     __device__ __forceinline__ int64_t record(int k, int64_t n, int32_t width) const {
         if (width <= 0) return tile * 128 + k;
-        const int32_t px = tx * 16 + ox;
+        const int32_t px = tx * kTileW + ox;
         if (px >= width) return n;
-        return (ty * 8 + oy) * (int64_t)width + px;
+        return (ty * kTileH + oy) * (int64_t)width + px;
     }
     // G-buffer record of this thread's output record r (see IoArgs::sub).
     __device__ __forceinline__ int64_t source(int64_t r, const IoArgs& io) const {
         if (io.sub <= 1) return r;
-        return (ty * 8 + oy) * io.sub * (int64_t)io.src_width + (int64_t)(tx * 16 + ox) * io.sub;
+        return (ty * kTileH + oy) * io.sub * (int64_t)io.src_width + (int64_t)(tx * kTileW + ox) * io.sub;
     }
 };
 
-__device__ __forceinline__ int64_t niv_tile_count(int64_t n, int32_t width) {
+__host__ __device__ __forceinline__ int64_t niv_tile_count(int64_t n, int32_t width) {
     if (width <= 0) return (n + 127) / 128;
     int64_t rows = (n + width - 1) / width;
-    return ((width + 15) / 16) * ((rows + 7) / 8);
+    return ((width + kTileW - 1) / kTileW) * ((rows + kTileH - 1) / kTileH);
 }
 
-__host__ __forceinline__ int64_t niv_tile_count_host(int64_t n, int32_t width) {
-    if (width <= 0) return (n + 127) / 128;
-    int64_t rows = (n + width - 1) / width;
-    return ((width + 15) / 16) * ((rows + 7) / 8);
-}
+__host__ __forceinline__ int64_t niv_tile_count_host(int64_t n, int32_t width) { return niv_tile_count(n, width); }
 
 // Load one [4] record (FP16 or FP32) as float4.
 __device__ __forceinline__ float4 niv_load_rec(const void* base, int64_t i, bool f16) {
