@@ -301,7 +301,8 @@ def fp8_act_amax(model, params, pos4, nrm4, aabb_min=(0, 0, 0), aabb_max=(1, 1, 
 
 
 def query_fp8(model, params, s_act, pos4, nrm4, aabb_min=(0, 0, 0), aabb_max=(1, 1, 1), t=0.0):
-    """E(x, n) of the E4M3 network path with activation scales s_act (one per matrix product)."""
+    """E(x, n) of the E4M3 network path with activation scales s_act (one per matrix product):
+    every scaled weight and input carried as two E4M3 codes h = e4m3(v), l = e4m3(v - h)."""
     pos4, nrm4 = _f32(pos4), _f32(nrm4)
     E = np.zeros((len(pos4), model.out_dim))
     rc = lib().orc_query_fp8(ctypes.byref(model.cdesc()), _p(_f64(params)), _p(_f64(s_act)), _p(pos4), _p(nrm4),

@@ -614,9 +614,14 @@ int orc_query_f16(const orc_desc* d, const double* params, const float* pos4, co
  *   s = 2^ceil(log2(amax / 448)),
  * so that scaling is exact.  Weights: s_w from amax|W| of the layer.
  * Activations: s_a from the amax of the layer's FP32 input over a calibration
- * batch (the unquantised network).  Layer l computes
- *   z = (sum_i e4m3(W/s_w)[o][i] * e4m3(a/s_a)[i]) * s_w * s_a + b,
- * ReLU on hidden layers, softplus on the output.  Biases stay in FP32.
+ * batch (the unquantised network).  One E4M3 code keeps 3 mantissa bits, which
+ * moves E of He-initialised networks by 3-5% of its range; so each scaled value
+ * v is carried as two E4M3 codes at the same scale, h = e4m3(v) and
+ * l = e4m3(v - h), whose sum keeps about 8 bits.  Layer l computes
+ *   z = (sum_i hW*ha + hW*la + lW*ha) * s_w * s_a + b
+ * with (hW, lW) the pair of W[o][i]/s_w and (ha, la) that of a[i]/s_a (the
+ * product lW*la lies below both codes' resolution and is left out), ReLU on
+ * hidden layers, softplus on the output.  Biases stay in FP32.
  * ------------------------------------------------------------------------ */
 
 /* 2^ceil(log2(amax / 448)) (1 when amax is 0) */
@@ -689,6 +694,7 @@ int orc_query_fp8(const orc_desc* d, const double* params, const double* s_act, 
     for (int64_t q = 0; q < n; ++q) {
         float u[ORC_MAX_DIMS];
         double enc[ORC_MAX_ENC], a[ORC_MAX_WIDTH + ORC_MAX_ENC], z[ORC_MAX_WIDTH];
+        double ah[ORC_MAX_WIDTH + ORC_MAX_ENC], al[ORC_MAX_WIDTH + ORC_MAX_ENC];
         normalise(d, pos4 + 4 * q, aabb_min, aabb_max, t, u);
         encode_point(d, &L, params, u, enc, NULL, NULL);
         net_input(d, enc, nrm4 + 4 * q, t, a);
@@ -698,10 +704,18 @@ int orc_query_fp8(const orc_desc* d, const double* params, const double* s_act, 
             int last = l == layers - 1, n_out = last ? d->out_dim : d->width;
             const double* W = p;
             const double* b = p + (int64_t)n_out * k_in;
+            for (int i = 0; i < k_in; ++i) {  /* the two codes of each scaled input */
+                double v = a[i] / s_act[l];
+                ah[i] = orc_e4m3(v);
+                al[i] = orc_e4m3(v - ah[i]);
+            }
             for (int o = 0; o < n_out; ++o) {
                 double acc = 0.0;
-                for (int i = 0; i < k_in; ++i)
-                    acc += orc_e4m3(W[(int64_t)o * k_in + i] / s_w[l]) * orc_e4m3(a[i] / s_act[l]);
+                for (int i = 0; i < k_in; ++i) {
+                    double v = W[(int64_t)o * k_in + i] / s_w[l];
+                    double wh = orc_e4m3(v), wl = orc_e4m3(v - wh);
+                    acc += wh * ah[i] + wh * al[i] + wl * ah[i];
+                }
                 z[o] = acc * s_w[l] * s_act[l] + b[o];
             }
             for (int o = 0; o < n_out; ++o) {

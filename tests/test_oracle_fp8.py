@@ -1,4 +1,8 @@
-"""Pins of the oracle's E4M3 network path against numpy + torch's float8_e4m3fn rounding."""
+"""Pins of the oracle's E4M3 network path against numpy + torch's float8_e4m3fn rounding.
+
+The path carries every scaled weight and input v as two E4M3 codes h = e4m3(v),
+l = e4m3(v - h) and forms each product as hW*ha + hW*la + lW*ha.
+"""
 import numpy as np
 import pytest
 
@@ -44,9 +48,29 @@ def test_calibration_amax_matches_numpy_forward():
     np.testing.assert_allclose(amax, ref, rtol=1e-12)
 
 
+def _pair(v):
+    h = _e4m3(v)
+    return h, _e4m3(v - h)
+
+
+def test_two_code_pair_keeps_eight_bits():
+    """|h + l - v| <= 2^-4 |v - h| <= 2^-8 |v| for v in E4M3's normal range (each code rounds
+    to 3 mantissa bits); below it the subnormal step 2^-9 bounds l's rounding."""
+    v = np.random.default_rng(0).uniform(-448.0, 448.0, 200000)
+    v = np.concatenate([v, v * 2.0 ** -8, [0.0, 2.0 ** -6, 448.0, -448.0]])
+    h = oracle.e4m3(v)
+    l = oracle.e4m3(v - h)
+    err = np.abs(h + l - v)
+    assert np.all(err <= np.maximum(2.0 ** -8 * np.abs(v), 2.0 ** -10) * (1 + 1e-12))
+    assert np.all(np.abs(h - v) <= np.maximum(2.0 ** -4 * np.abs(v), 2.0 ** -10) * (1 + 1e-12))
+    # and the single code alone does not (the second code matters)
+    assert np.max(np.abs(h - v) / np.maximum(np.abs(v), 1.0)) > 2.0 ** -6
+
+
 @pytest.mark.parametrize("n_hidden", [2, 3])
 def test_fp8_forward_matches_numpy_with_torch_quantiser(n_hidden):
-    """Quantise W/s_w and a/s_a with torch's E4M3 cast, multiply in FP64, rescale: same E as the oracle."""
+    """Split W/s_w and a/s_a into two codes with torch's E4M3 cast, form hW ha + hW la + lW ha in
+    FP64, rescale: same E as the oracle."""
     m = oracle.Model(n_hidden=n_hidden)
     L = oracle.layout(m)
     params = init_params(L["total"] * m.feat, oracle.layer_shapes(m), seed=5, bias_std=0.1).astype(np.float64)
@@ -59,13 +83,16 @@ def test_fp8_forward_matches_numpy_with_torch_quantiser(n_hidden):
     layers = _layers(m, params[L["total"] * m.feat:])
     for li, (W, b) in enumerate(layers):
         s_w = 2.0 ** np.ceil(np.log2(np.abs(W).max() / 448.0))
-        z = (_e4m3(a / s_act[li]) @ _e4m3(W / s_w).T) * (s_w * s_act[li]) + b
+        ah, al = _pair(a / s_act[li])
+        wh, wl = _pair(W / s_w)
+        z = (ah @ wh.T + al @ wh.T + ah @ wl.T) * (s_w * s_act[li]) + b
         a = np.maximum(z, 0.0) if li < len(layers) - 1 else np.logaddexp(0.0, z)
     np.testing.assert_allclose(got, a, rtol=1e-12, atol=1e-14)
 
 
 def test_fp8_is_close_to_full_precision():
-    """E4M3 keeps 3 mantissa bits: outputs stay within a few percent of the FP64 network."""
+    """Two E4M3 codes keep about 8 bits: outputs stay within the FP8 bar (2e-2 of the range) of
+    the FP64 network, yet are visibly quantised."""
     m = oracle.Model()
     L = oracle.layout(m)
     params = init_params(L["total"] * m.feat, oracle.layer_shapes(m), seed=7).astype(np.float64)
@@ -74,4 +101,4 @@ def test_fp8_is_close_to_full_precision():
     E8 = oracle.query_fp8(m, params, s_act, pos, nrm)
     E = oracle.query(m, params, pos, nrm)
     err = np.abs(E8 - E).max() / np.abs(E).max()
-    assert 1e-4 < err < 0.1
+    assert 1e-5 < err < 2e-2
