@@ -5,9 +5,13 @@
 // interpolation), writes the network input as E4M3 bytes into its K-major shared-memory
 // tile, and every layer runs as tcgen05.mma of
 // kind::f8f6f4 (E4M3 x E4M3, K = 32 per instruction) into an FP32 TMEM accumulator.
-// Per-layer power-of-two scales (the FP8 reading of the design notes): weights
-// e4m3(W / s_w), inputs e4m3(a / s_a), and the epilogue forms
-//   z = acc * (s_w * s_a) + b,  ReLU,  then e4m3(z / s_a') for the next layer;
+// Per-layer power-of-two scales: v = W / s_w and v = a / s_a.  One E4M3 code keeps only 3
+// mantissa bits, so every scaled value is carried as two codes at the same scale,
+// h = e4m3(v) and l = e4m3(v - h) (about 8 bits together), stored side by side: a tile of
+// K inputs is K columns of h codes followed by K columns of l codes.  A layer is the MMA
+// chain  acc = H Wh^T + L Wh^T + H Wl^T  (the L Wl^T term lies below both codes'
+// resolution), and the epilogue forms
+//   z = acc * (s_w * s_a) + b,  ReLU,  then the two codes of z / s_a' for the next layer;
 // the output layer finishes with softplus in FP32.  s_a comes from niv_fp8_calibrate
 // (amax of each layer's FP32 input over a calibration batch), s_w from amax|W|.
 #include <cuda_fp8.h>
@@ -33,7 +37,9 @@ __host__ __device__ __forceinline__ uint32_t core_off8(int r, int k, int K) {
 }
 
 struct F8Layout {
-    int32_t K1, W, n_hidden, col_extra;  // col_extra: tile column of n.x (features end before it)
+    // K1: network inputs per code tile (h and l tiles each K1 columns wide); col_extra: column
+    // of n.x (the features end before it)
+    int32_t K1, W, n_hidden, col_extra;
     uint32_t w1, wh, wo, scal, total;    // byte offsets; scal = FP32 block [c | qmul | biases | cq | bq]
 };
 
@@ -42,20 +48,33 @@ struct F8Layout {
 // that the hidden epilogue loads it in 16-byte pieces.
 __host__ __device__ __forceinline__ int f8_bq_offset(int nh, int W) { return (2 * (nh + 1) + nh * W + 4 + nh + 3) & ~3; }
 
-// E4M3 codes of max(lo, 0) (low byte) and max(hi, 0) (high byte), rounded to nearest with
-// saturation to +-448.
-__device__ __forceinline__ uint32_t e4m3x2_relu(float lo, float hi) {
-    uint16_t r;
-    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
-    return r;
+// The two E4M3 codes of a pair of values (a in the low, b in the high byte of each code
+// pair): h = e4m3(v) and l = e4m3(v - h), both rounded to nearest with saturation to +-448.
+// v is first rounded to FP16 (2^-11 relative, far below l's resolution of about 2^-8), so
+// that v - h is one exact FP16 subtraction (h lies within a factor of two of v).  RELU: v is
+// max(v, 0).  Returns h in the low and l in the high 16 bits.
+template <bool RELU>
+__device__ __forceinline__ uint32_t e4m3_pair2(float a, float b) {
+    uint32_t v, hf, r;
+    uint16_t h, l;
+    if (RELU) asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(v) : "f"(b), "f"(a));
+    else asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(v) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(h) : "r"(v));
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(hf) : "h"(h));
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(hf));
+    asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(l) : "r"(r));
+    return (uint32_t)h | ((uint32_t)l << 16);
 }
 
-// The same for 16 values, in order.
-__device__ __forceinline__ uint4 e4m3x16_relu(const float* v) {
-    return make_uint4(e4m3x2_relu(v[0], v[1]) | (e4m3x2_relu(v[2], v[3]) << 16),
-                      e4m3x2_relu(v[4], v[5]) | (e4m3x2_relu(v[6], v[7]) << 16),
-                      e4m3x2_relu(v[8], v[9]) | (e4m3x2_relu(v[10], v[11]) << 16),
-                      e4m3x2_relu(v[12], v[13]) | (e4m3x2_relu(v[14], v[15]) << 16));
+// The codes of 16 values (max(v, 0)), in order: h codes to hi, l codes to lo.
+__device__ __forceinline__ void e4m3_pairs16_relu(const float* v, uint4& hi, uint4& lo) {
+    uint32_t p[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) p[j] = e4m3_pair2<true>(v[2 * j], v[2 * j + 1]);
+    hi = make_uint4((p[0] & 0xFFFFu) | (p[1] << 16), (p[2] & 0xFFFFu) | (p[3] << 16), (p[4] & 0xFFFFu) | (p[5] << 16),
+                    (p[6] & 0xFFFFu) | (p[7] << 16));
+    lo = make_uint4((p[0] >> 16) | (p[1] & 0xFFFF0000u), (p[2] >> 16) | (p[3] & 0xFFFF0000u),
+                    (p[4] >> 16) | (p[5] & 0xFFFF0000u), (p[6] >> 16) | (p[7] & 0xFFFF0000u));
 }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
@@ -70,28 +89,33 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
     for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// One layer over K inputs: the tiles at act ([H | L], 2K columns) and w ([Wh | Wl], 2K
+// columns) give acc = H Wh^T + L Wh^T + H Wl^T, then `bar` is signalled.
 __device__ __forceinline__ void issue_layer8(uint32_t tmem, uint32_t act, uint32_t w, uint32_t K, uint32_t idesc,
                                              uint32_t bar) {
-    const uint32_t sbo = (K >> 4) * 128u;
+    const uint32_t sbo = (2u * K >> 4) * 128u;  // 8-row groups of a 2K-column tile
+    const uint32_t lo = (K >> 4) * 128u;        // first core matrix of the l codes
     for (uint32_t ks = 0; ks < K / 32; ++ks)
         tc::mma_e4m3(tmem, tc::smem_desc(act + ks * 256u, 128u, sbo), tc::smem_desc(w + ks * 256u, 128u, sbo), idesc,
                      ks > 0 ? 1u : 0u);
+    for (uint32_t ks = 0; ks < K / 32; ++ks)
+        tc::mma_e4m3(tmem, tc::smem_desc(act + lo + ks * 256u, 128u, sbo), tc::smem_desc(w + ks * 256u, 128u, sbo),
+                     idesc, 1u);
+    for (uint32_t ks = 0; ks < K / 32; ++ks)
+        tc::mma_e4m3(tmem, tc::smem_desc(act + ks * 256u, 128u, sbo), tc::smem_desc(w + lo + ks * 256u, 128u, sbo),
+                     idesc, 1u);
     tc::mma_commit(bar);
 }
 
-// One E4M3 byte pair (a, b), rounded to nearest with saturation, in the low 16 bits.
-__device__ __forceinline__ uint32_t e4m3x2(float a, float b) {
-    return __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3) & 0xFFFFu;
-}
-
-// Encode levels [l0, l0 + 16/F) of one record into one 16-byte chunk of E4M3 inputs (value
-// times q0, the inverse input scale), each level converted as soon as it is blended.
+// Encode levels [l0, l0 + 16/F) of one record into one 16-byte chunk of h codes (hi) and one
+// of l codes (lo) of the E4M3 inputs (value times q0, the inverse input scale), each level
+// converted as soon as it is blended.
 template <int DIMS, int F, int ND = -1>
-__device__ __forceinline__ uint4 encode_chunk8(const GridArgs& g, const __half* __restrict__ grid16, int l0, int L,
-                                               const float* u, float q0) {
+__device__ __forceinline__ void encode_chunk8(const GridArgs& g, const __half* __restrict__ grid16, int l0, int L,
+                                              const float* u, float q0, uint4& hi, uint4& lo) {
     constexpr int NC = 1 << DIMS, G = 16 / F;
     using R = typename NivRaw<F, __half>::T;
-    uint32_t wd[4] = {0u, 0u, 0u, 0u};
+    uint32_t wd[4] = {0u, 0u, 0u, 0u}, wl[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int q = 0; q < G; ++q) {
         if (l0 + q >= L) continue;
@@ -103,16 +127,23 @@ __device__ __forceinline__ uint4 encode_chunk8(const GridArgs& g, const __half* 
         float acc[F];
         niv_level_blend<NC, F>(raw, wc, acc);
         if (F == 1) {
-            wd[q >> 2] |= (e4m3x2(acc[0] * q0, 0.0f) & 0xFFu) << (8 * (q & 3));
+            const uint32_t p = e4m3_pair2<false>(acc[0] * q0, 0.0f);
+            wd[q >> 2] |= (p & 0xFFu) << (8 * (q & 3));
+            wl[q >> 2] |= ((p >> 16) & 0xFFu) << (8 * (q & 3));
         } else if (F == 2) {
             const float2 a = __fmul2_rn(make_float2(acc[0], acc[1 % F]), make_float2(q0, q0));
-            const uint32_t h = e4m3x2(a.x, a.y);
-            wd[(q >> 1) & 3] |= (q & 1) ? (h << 16) : h;
+            const uint32_t p = e4m3_pair2<false>(a.x, a.y);
+            wd[(q >> 1) & 3] |= (q & 1) ? (p << 16) : (p & 0xFFFFu);
+            wl[(q >> 1) & 3] |= (q & 1) ? (p & 0xFFFF0000u) : (p >> 16);
         } else {
-            wd[q & 3] = e4m3x2(acc[0] * q0, acc[1 % F] * q0) | (e4m3x2(acc[2 % F] * q0, acc[3 % F] * q0) << 16);
+            const uint32_t p0 = e4m3_pair2<false>(acc[0] * q0, acc[1 % F] * q0);
+            const uint32_t p1 = e4m3_pair2<false>(acc[2 % F] * q0, acc[3 % F] * q0);
+            wd[q & 3] = (p0 & 0xFFFFu) | (p1 << 16);
+            wl[q & 3] = (p0 >> 16) | (p1 & 0xFFFF0000u);
         }
     }
-    return make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    hi = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    lo = make_uint4(wl[0], wl[1], wl[2], wl[3]);
 }
 
 #ifndef NIV_TC_ND
@@ -141,7 +172,7 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
     uint8_t* s_net = smem + kHdr;
     const int K1 = KT > 0 ? KT : lay.K1, W = WT > 0 ? WT : lay.W, nh = NHT > 0 ? NHT : lay.n_hidden;
     const int col_extra = LV > 0 ? ((LV * F + 15) & ~15) : lay.col_extra;  // column of n.x
-    const uint32_t act_bytes = (uint32_t)kT * (uint32_t)(K1 > W ? K1 : W);
+    const uint32_t act_bytes = (uint32_t)kT * 2u * (uint32_t)(K1 > W ? K1 : W);  // h and l codes
     const int wg = threadIdx.x / kT, tid = threadIdx.x % kT, warp = tid >> 5;
     uint8_t* s_act = s_net + ((lay.total + 127u) & ~127u) + wg * act_bytes;
 
@@ -190,23 +221,37 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
         u[2] = niv_unit(p.z, g.aabb_min[2], g.inv_ext[2]);
         u[3] = fminf(fmaxf(g.t, 0.0f), 1.0f);
 
-        // ---- encoding -> E4M3 input row ----
+        // ---- encoding -> E4M3 input row: h codes in columns [0, K1), l codes in [K1, 2 K1) ----
         const float q0 = s_q[0];
+        const int K2 = 2 * K1;
         if (LV > 0) {
 #pragma unroll
-            for (int l0 = 0; l0 < LV; l0 += G)
-                *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K1)) = encode_chunk8<DIMS, F, ND>(g, grid16, l0, LV, u, q0);
+            for (int l0 = 0; l0 < LV; l0 += G) {
+                uint4 hi, lo;
+                encode_chunk8<DIMS, F, ND>(g, grid16, l0, LV, u, q0, hi, lo);
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K2)) = hi;
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, K1 + l0 * F, K2)) = lo;
+            }
         } else {
-            for (int l0 = 0; l0 < L; l0 += G)
-                *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K1)) = encode_chunk8<DIMS, F>(g, grid16, l0, L, u, q0);
+            for (int l0 = 0; l0 < L; l0 += G) {
+                uint4 hi, lo;
+                encode_chunk8<DIMS, F>(g, grid16, l0, L, u, q0, hi, lo);
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K2)) = hi;
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, K1 + l0 * F, K2)) = lo;
+            }
         }
         {
             const float tv = g.n_in > LF + 3 ? u[3] : 0.0f;
-            *reinterpret_cast<uint4*>(s_act + core_off8(tid, col_extra, K1)) =
-                make_uint4(e4m3x2(nv.x * q0, nv.y * q0) | (e4m3x2(nv.z * q0, tv * q0) << 16), 0u, 0u, 0u);
+            const uint32_t p0 = e4m3_pair2<false>(nv.x * q0, nv.y * q0), p1 = e4m3_pair2<false>(nv.z * q0, tv * q0);
+            *reinterpret_cast<uint4*>(s_act + core_off8(tid, col_extra, K2)) =
+                make_uint4((p0 & 0xFFFFu) | (p1 << 16), 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(s_act + core_off8(tid, K1 + col_extra, K2)) =
+                make_uint4((p0 >> 16) | (p1 & 0xFFFF0000u), 0u, 0u, 0u);
         }
-        for (int k = col_extra + 16; k < K1; k += 16)
-            *reinterpret_cast<uint4*>(s_act + core_off8(tid, k, K1)) = make_uint4(0u, 0u, 0u, 0u);
+        for (int k = col_extra + 16; k < K1; k += 16) {
+            *reinterpret_cast<uint4*>(s_act + core_off8(tid, k, K2)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(s_act + core_off8(tid, K1 + k, K2)) = make_uint4(0u, 0u, 0u, 0u);
+        }
         tc::fence_async_smem();
         tc::fence_before_sync();
         group_sync8(wg);
@@ -239,12 +284,15 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
                     v[2 * j] = r.x;
                     v[2 * j + 1] = r.y;
                 }
-                *reinterpret_cast<uint4*>(s_act + core_off8(tid, ch * 16, W)) = e4m3x16_relu(v);
+                uint4 hi, lo;
+                e4m3_pairs16_relu(v, hi, lo);
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, ch * 16, 2 * W)) = hi;
+                *reinterpret_cast<uint4*>(s_act + core_off8(tid, W + ch * 16, 2 * W)) = lo;
             }
             tc::fence_async_smem();
             tc::fence_before_sync();
             group_sync8(wg);
-            w_off = layer == 0 ? lay.wh : w_off + (uint32_t)(W * W);
+            w_off = layer == 0 ? lay.wh : w_off + (uint32_t)(2 * W * W);
             K = (uint32_t)W;
         }
         if (!ok) break;
@@ -289,7 +337,7 @@ int launch8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_
         return niv_fail(NIV_ERR_UNSUPPORTED, "dense levels differ from the kernel's");
     auto kern = query_f8_kernel<DIMS, F, LV, WT, KT, NHT, ND>;
     const int kmax = lay->K1 > lay->W ? lay->K1 : lay->W;
-    const size_t smem = (size_t)kHdr + ((lay->total + 127u) & ~127u) + (size_t)kWG * kT * kmax;
+    const size_t smem = (size_t)kHdr + ((lay->total + 127u) & ~127u) + (size_t)kWG * kT * 2 * kmax;
     NIV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, smem_per_sm = 0, regs_per_sm = 0;
     NIV_CUDA(cudaGetDevice(&dev));
@@ -389,10 +437,16 @@ double pow2_scale(double amax) {  // 2^ceil(log2(amax / 448)), 1 for amax = 0
 
 uint8_t to_e4m3(float v) { return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3); }
 
+float from_e4m3(uint8_t c) {
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)c, __NV_E4M3);
+    return __half2float(__half(h));
+}
+
 }  // namespace
 
 // Pack the E4M3 network from host FP32 parameters and the activation scales m->fp8_sact:
-// [W1 (W x K1) | hidden (W x W) ... | W_out (16 x W) bytes | c[nh+1] | qmul[nh+1] | biases].
+// [W1 (W x 2 K1) | hidden (W x 2 W) ... | W_out (16 x 2 W) bytes | c[nh+1] | qmul[nh+1] | biases],
+// each weight tile [Wh | Wl]: the h codes e4m3(W / s_w), then the l codes e4m3(W / s_w - h).
 int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s) {
     const int W = m->d.width, nh = m->d.n_hidden, n_in = m->n_in, LF = m->d.levels * m->d.feat;
     F8Layout lay;
@@ -403,9 +457,9 @@ int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s) {
     lay.n_hidden = nh;
     auto up = [](uint32_t x) { return (x + 127u) & ~127u; };
     lay.w1 = 0;
-    lay.wh = up(lay.w1 + (uint32_t)(W * lay.K1));
-    lay.wo = up(lay.wh + (uint32_t)((nh - 1) * W * W));
-    lay.scal = up(lay.wo + (uint32_t)(kNO * W));
+    lay.wh = up(lay.w1 + (uint32_t)(W * 2 * lay.K1));
+    lay.wo = up(lay.wh + (uint32_t)((nh - 1) * W * 2 * W));
+    lay.scal = up(lay.wo + (uint32_t)(kNO * 2 * W));
     // [c (nh+1) | 1/s_a (nh+1) | biases (nh W + 3, padded to + 4) | c / s_a' (nh) | pad | b / s_a' (nh W)]
     lay.total = up(lay.scal + (uint32_t)((f8_bq_offset(nh, W) + nh * W) * 4));
     static_assert(sizeof(F8Layout) <= sizeof(((niv_model*)0)->f8_layout), "layout slot too small");
@@ -423,12 +477,15 @@ int niv_pack_f8(niv_model* m, const float* mlp_host, cudaStream_t s) {
         const double sw = pow2_scale(amax);
         m->fp8_sw[l] = (float)sw;
         const float inv = (float)(1.0 / sw);  // exact: a power of two
-        const uint32_t base = l == 0 ? lay.w1 : last ? lay.wo : lay.wh + (uint32_t)((l - 1) * W * W);
+        const uint32_t base = l == 0 ? lay.w1 : last ? lay.wo : lay.wh + (uint32_t)((l - 1) * W * 2 * W);
         const int K = l == 0 ? lay.K1 : W;
         for (int r = 0; r < n_out; ++r)
             for (int i = 0; i < k_in; ++i) {
                 const int col = (l == 0 && i >= LF) ? lay.col_extra + (i - LF) : i;
-                buf[base + core_off8(r, col, K)] = to_e4m3(p[(size_t)r * k_in + i] * inv);
+                const float v = p[(size_t)r * k_in + i] * inv;  // exact: inv is a power of two
+                const uint8_t h = to_e4m3(v);
+                buf[base + core_off8(r, col, 2 * K)] = h;
+                buf[base + core_off8(r, K + col, 2 * K)] = to_e4m3(v - from_e4m3(h));  // v - h exact
             }
         p += (size_t)n_out * k_in;
         for (int r = 0; r < n_out; ++r) bias[l * W + r] = p[r];

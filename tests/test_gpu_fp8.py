@@ -1,16 +1,16 @@
-"""GPU parity of the E4M3 tensor-core query against the oracle's E4M3 network path.
+"""GPU parity of the E4M3 tensor-core query.
 
-The FP8 path quantises weights and every layer input to E4M3 with per-layer
-power-of-two scales and accumulates in FP32.  Parity is taken against the oracle's
-FP8 forward with the oracle's own calibration, so it measures the kernel; the
-departure of the FP8 format from the FP64 network is reported beside it.
+The FP8 path carries every weight and every layer input, divided by its per-layer
+power-of-two scale, as two E4M3 codes (h = e4m3(v), l = e4m3(v - h)) and accumulates
+the products hW ha + hW la + lW ha in FP32.  The bar is the FP8 tolerance against the
+unquantised FP64 oracle: max |E - E_fp64| / max E_fp64 <= FP8_BOUND = 2e-2, per result.
 
-Each E4M3 code is an integer decided by floating point: the kernel decides it from
-FP32 pre-activations, the oracle from FP64 ones, and where the two straddle a
-rounding point they pick neighbouring codes (one E4M3 step, 2^-3 relative, of one
-activation).  So the bar is: at least 98% of samples agree to 1e-5 of the frame's
-max irradiance (every decision identical), and every sample stays within
-FP8_FLIP_BOUND = 2e-2 + one flip's worth (4e-2 in all).
+Secondary check of the kernel: the oracle's own two-code E4M3 forward (grid values
+rounded to FP16 as the kernel stores them).  Each code is an integer decided by
+floating point (FP16 residuals on the GPU, FP64 in the oracle), so the two sides may
+pick neighbouring codes; either pair lies within 2^-8 |v| of v, so the two forwards
+differ by at most about twice the two-code form's own departure from the FP64 network
+(<= 1.7e-3 on these networks): FP8_ORACLE_BOUND = 5e-3.
 """
 import ctypes
 
@@ -24,15 +24,21 @@ from niv_inputs.configs import MODEL_C0, MODEL_C3, ROOM_MIN, ROOM_MAX, room_gbuf
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-FP8_AGREE = 1e-5        # normalised error of samples whose quantisation decisions all agree
-FP8_AGREE_FRAC = 0.98    # fraction of samples that must agree
-FP8_FLIP_BOUND = 4e-2    # any sample, isolated rounding-point flips included
+FP8_BOUND = 2e-2         # against the FP64 network, normalised by the frame's max E
+FP8_ORACLE_BOUND = 5e-3  # against the oracle's two-code E4M3 forward
 
 
-def fp8_parity(E, ref8):
-    """(max normalised error, fraction of samples within FP8_AGREE)."""
-    e = np.abs(E - ref8).max(axis=1) / np.abs(ref8).max()
-    return float(e.max()), float((e <= FP8_AGREE).mean())
+def norm_err(E, ref):
+    """max |E - ref| / max |ref| (abs error on irradiance normalised to [0, 1])."""
+    return float(np.max(np.abs(E - ref)) / np.abs(ref).max())
+
+
+def grid16(model, params):
+    """params with the grid values rounded to FP16, as the kernels store them."""
+    g = oracle.grid_value_count(model)
+    p = np.asarray(params, np.float64).copy()
+    p[:g] = p[:g].astype(np.float16).astype(np.float64)
+    return p
 
 
 @pytest.fixture(scope="module")
@@ -55,7 +61,7 @@ def test_fp8_tensor_core_layout_selftest(niv):
     np.testing.assert_array_equal(out.cpu().numpy(), ref)
 
 
-def _run(niv, spec, pos, nrm, kw, seed=0, bias_std=0.0, cal=None):
+def _run(niv, spec, pos, nrm, kw, seed=0, bias_std=0.0, cal=None, image_width=0):
     m = niv.NIVModel(**spec)
     g, _ = m.param_count()
     params = init_params(g, m.layer_shapes(), seed=seed, bias_std=bias_std)
@@ -69,15 +75,20 @@ def _run(niv, spec, pos, nrm, kw, seed=0, bias_std=0.0, cal=None):
     np.testing.assert_allclose(am, o_amax, rtol=1e-5)
     np.testing.assert_array_equal(sa, o_sact)  # power-of-two scales: the same decision on both sides
     E = m.query(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda(), precision="fp8",
-                out_dtype=torch.float32, **kw)[:, :3].cpu().numpy()
-    ref8 = oracle.query_fp8(om, params, o_sact, pos.astype(np.float32), nrm.astype(np.float32), **kw)
-    ref = oracle.query(om, params, pos.astype(np.float32), nrm.astype(np.float32), **kw)
-    e8, agree = fp8_parity(E, ref8)
-    e = np.max(np.abs(E - ref)) / np.abs(ref).max()
-    print("fp8: max abs err (normalised) %.3g vs FP8 oracle (%.4f of samples within %g), %.3g vs FP64 network"
-          % (e8, agree, FP8_AGREE, e))
+                out_dtype=torch.float32, image_width=image_width, **kw)[:, :3].cpu().numpy()
     m.close()
-    return e8, agree, e
+    return E, params, om, o_sact
+
+
+def _check(E, params, om, o_sact, pos, nrm, kw, label):
+    p32, n32 = pos.astype(np.float32), nrm.astype(np.float32)
+    ref = oracle.query(om, params, p32, n32, **kw)
+    ref8 = oracle.query_fp8(om, grid16(om, params), o_sact, p32, n32, **kw)
+    e, e8 = norm_err(E, ref), norm_err(E, ref8)
+    print("fp8 %s: max abs err (normalised) %.3g vs the FP64 network (bar %g), %.3g vs the oracle's E4M3 "
+          "forward (bound %g)" % (label, e, FP8_BOUND, e8, FP8_ORACLE_BOUND))
+    assert e <= FP8_BOUND
+    assert e8 <= FP8_ORACLE_BOUND
 
 
 @pytest.mark.parametrize("spec,kw", [
@@ -91,37 +102,23 @@ def _run(niv, spec, pos, nrm, kw, seed=0, bias_std=0.0, cal=None):
     (dict(MODEL_C3, dims=3, in_extra=3, n_hidden=2, log2_T=15), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
     (dict(MODEL_C3, log2_T=15), dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=0.6)),
 ])
-def test_fp8_matches_fp8_oracle(niv, spec, kw):
+def test_fp8_within_bar_of_fp64_oracle(niv, spec, kw):
     lo, hi = kw.get("aabb_min", (0, 0, 0)), kw.get("aabb_max", (1, 1, 1))
     pos, nrm = uniform_queries(8192 + 3, seed=21, lo=lo, hi=hi)
-    e8, agree, e = _run(niv, spec, pos, nrm, kw, seed=2, bias_std=0.1)
-    assert agree >= FP8_AGREE_FRAC
-    assert e8 <= FP8_FLIP_BOUND
-    assert e <= 0.1
+    E, params, om, o_sact = _run(niv, spec, pos, nrm, kw, seed=2, bias_std=0.1)
+    _check(E, params, om, o_sact, pos, nrm, kw, "random queries")
 
 
-def test_fp8_config3_model_on_room_frame(niv):
-    """The 4-D config-3 model on the full 1080p room G-buffer (image traversal), sampled pixels checked."""
+@pytest.mark.parametrize("t", [0.0, 0.25, 0.6369616873214543, 1.0])
+def test_fp8_config3_model_on_room_frame(niv, t):
+    """The 4-D config-3 model on the full 1080p room G-buffer (image traversal) at several
+    values of the scene parameter; sampled pixels checked against both oracles."""
     pos, nrm, _ = room_gbuffer(1920, 1080)
-    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=0.25)
-    pick = np.random.default_rng(3).choice(len(pos), 8192, replace=False)
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=t)
     cal = (pos[:: 31].copy(), nrm[:: 31].copy())  # calibration batch: every 31st pixel
-    m = niv.NIVModel(**MODEL_C3)
-    g, _ = m.param_count()
-    params = init_params(g, m.layer_shapes(), seed=0)
-    m.set_params(params)
-    m.fp8_calibrate(torch.from_numpy(cal[0]).cuda(), torch.from_numpy(cal[1]).cuda(), **kw)
-    E = m.query(torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda(), precision="fp8", image_width=1920,
-                out_dtype=torch.float32, **kw)[:, :3].cpu().numpy()
-    om = oracle.Model(**MODEL_C3)
-    o_sact = [oracle.fp8_scale(a) for a in oracle.fp8_act_amax(om, params, cal[0].astype(np.float32),
-                                                                cal[1].astype(np.float32), **kw)]
-    ref8 = oracle.query_fp8(om, params, o_sact, pos[pick].astype(np.float32), nrm[pick].astype(np.float32), **kw)
-    e8, agree = fp8_parity(E[pick], ref8)
-    print("fp8 config-3 frame: max %.3g, %.4f of samples within %g" % (e8, agree, FP8_AGREE))
-    assert agree >= FP8_AGREE_FRAC
-    assert e8 <= FP8_FLIP_BOUND
-    m.close()
+    E, params, om, o_sact = _run(niv, MODEL_C3, pos, nrm, kw, seed=0, cal=cal, image_width=1920)
+    pick = np.random.default_rng(3).choice(len(pos), 8192, replace=False)
+    _check(E[pick], params, om, o_sact, pos[pick], nrm[pick], kw, "config-3 frame, t=%g" % t)
 
 
 def test_fp8_requires_calibration(niv):
