@@ -508,6 +508,27 @@ NIV_API int niv_upsample_shade(const void* pos, const void* nrm, const void* alb
 NIV_API int niv_selftest_mma(int32_t mode, float* out, niv_stream stream);
 
 /*
+ * Diagnostic (no counterpart in the paper): makes the bounded wait that every
+ * tensor-core query kernel uses run out, without a fault.  One block allocates
+ * tensor memory as a query kernel does, issues no tensor-core operation, waits
+ * limit_us microseconds (1 .. 1000000, else NIV_ERR_ARG) on an mbarrier phase
+ * that nothing completes, latches failure code 3 in the device status word,
+ * frees its tensor memory and returns.  niv_sync_status() then reports
+ * NIV_ERR_DEVICE (and clears the word); the context stays usable.  Asynchronous.
+ */
+NIV_API int niv_selftest_wait_expiry(uint32_t limit_us, niv_stream stream);
+
+/*
+ * Diagnostic (no counterpart in the paper): the device counter-based generator
+ * that the Monte Carlo integrator, the probe bake and the ambient-occlusion pass
+ * draw from, Philox4x32-10 (Salmon et al., "Parallel Random Numbers: As Easy as
+ * 1, 2, 3", SC'11), applied to given inputs, so that it can be checked against
+ * the published known-answer vectors.  in6: device uint32 [n][6] = counter c0..c3,
+ * key k0, k1; out4: device uint32 [n][4].  Asynchronous.
+ */
+NIV_API int niv_selftest_philox(const uint32_t* in6, int64_t n, uint32_t* out4, niv_stream stream);
+
+/*
  * Diagnostic, no paper counterpart: the FP32 FMA rate of this GPU for the plain path's
  * roofline.  Launches `blocks` CTAs of 256 threads, each thread running 8 independent
  * FMA chains for `iters` steps (2 * 8 * iters FLOP per thread, 4096 * blocks * iters in

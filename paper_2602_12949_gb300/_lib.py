@@ -56,6 +56,7 @@ _lib = None
 
 # (name, restype, argtypes); pointer arguments are passed as integers (c_void_p).
 _VP, _I32, _I64, _F, _D, _U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double, ctypes.c_uint64
+_U32 = ctypes.c_uint32
 _SIGNATURES = [
     ("niv_version", ctypes.c_char_p, []),
     ("niv_last_error", ctypes.c_char_p, []),
@@ -88,6 +89,8 @@ _SIGNATURES = [
     ("niv_query_host_noalloc", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),
     ("niv_encode", ctypes.c_int, [_VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _VP, _VP]),
     ("niv_selftest_mma", ctypes.c_int, [_I32, _VP, _VP]),
+    ("niv_selftest_wait_expiry", ctypes.c_int, [_U32, _VP]),
+    ("niv_selftest_philox", ctypes.c_int, [_VP, _I64, _VP, _VP]),
     ("niv_shade", ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
     ("niv_dyn_create", ctypes.c_int, [_VP, _I64, ctypes.POINTER(_VP)]),
     ("niv_dyn_destroy", ctypes.c_int, [_VP]),

@@ -338,3 +338,28 @@ int niv_launch_compact(const float* x4, const float* n4, const float* t, const d
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }
+
+// ---- the device counter-based generator on given counters and keys ----
+namespace {
+__global__ void philox_selftest_kernel(const uint32_t* __restrict__ in6, int64_t n, uint32_t* __restrict__ out4) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t* p = in6 + 6 * i;
+    const uint4 r = philox4x32_10(make_uint4(p[0], p[1], p[2], p[3]), p[4], p[5]);
+    out4[4 * i] = r.x;
+    out4[4 * i + 1] = r.y;
+    out4[4 * i + 2] = r.z;
+    out4[4 * i + 3] = r.w;
+}
+}  // namespace
+
+extern "C" int niv_selftest_philox(const uint32_t* in6, int64_t n, uint32_t* out4, niv_stream stream) {
+    if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
+    if (n == 0) return NIV_OK;
+    if (!in6 || !out4) return niv_fail(NIV_ERR_ARG, "NULL pointer");
+    const int64_t blocks = (n + 127) / 128;
+    if (blocks > 0x7FFFFFFF) return niv_fail(NIV_ERR_ARG, "n too large");
+    philox_selftest_kernel<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(in6, n, out4);
+    NIV_CUDA(cudaGetLastError());
+    return NIV_OK;
+}

@@ -670,6 +670,44 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(int mode, float* __res
 }
 }  // namespace
 
+// ---- expiry of a bounded wait ----
+// The same bounded mbarrier wait the query kernels use, on a barrier whose phase nothing
+// completes: the kernel holds TMEM like a query kernel, issues no tensor-core operation (so
+// nothing is in flight when it gives up), waits limit_ns, latches failure code 3 in the
+// status word, frees its TMEM and returns.
+namespace {
+__global__ void __launch_bounds__(128) wait_expiry_kernel(uint64_t limit_ns, int* __restrict__ status) {
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&s_bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&s_tmem), 32);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const bool ok = tc::mbar_wait_bounded(tc::smem_u32(&s_bar), 0, limit_ns);  // no arrival will come
+    if (!ok && threadIdx.x == 0) atomicExch(status, 3);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(s_tmem, 32);
+}
+}  // namespace
+
+extern "C" int niv_selftest_wait_expiry(uint32_t limit_us, niv_stream stream) {
+    if (limit_us < 1 || limit_us > 1000000) return niv_fail(NIV_ERR_ARG, "limit_us must be in [1, 1000000]");
+    int* status = niv_status_word();
+    if (!status) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
+    wait_expiry_kernel<<<1, 128, 0, (cudaStream_t)stream>>>((uint64_t)limit_us * 1000ull, status);
+    NIV_CUDA(cudaGetLastError());
+    return NIV_OK;
+}
+
 extern "C" int niv_selftest_mma(int32_t mode, float* out, niv_stream stream) {
     if (!out) return niv_fail(NIV_ERR_ARG, "out is NULL");
     if (mode < 0 || mode > 2) return niv_fail(NIV_ERR_ARG, "mode must be 0, 1 or 2");
