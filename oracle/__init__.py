@@ -17,7 +17,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["niv_oracle.c", "oracle_mc.c", "oracle_sh.c", "oracle_ao.c"]
+_SOURCES = ["niv_oracle.c", "oracle_mc.c", "oracle_sh.c", "oracle_ao.c", "oracle_samples.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -125,9 +125,13 @@ def lib():
         L.orc_fp8_scale.restype = d
         L.orc_fp8_act_amax.argtypes = [P(Desc), vp, vp, vp, i64, vp, vp, f, vp]
         L.orc_query_fp8.argtypes = [P(Desc), vp, vp, vp, vp, i64, vp, vp, f, vp]
+        L.orc_training_samples.argtypes = [vp, i64, i64, f, ctypes.c_uint64, ctypes.c_uint64, vp, vp, vp, vp]
+        L.orc_training_samples.restype = ctypes.c_int
+        L.orc_sample_patch_table.argtypes = [vp, i64, vp, ctypes.c_int]
+        L.orc_sample_patch_table.restype = ctypes.c_int
         L.orc_philox4x32_10.argtypes = [vp, vp, vp]
         L.orc_philox4x32_10.restype = None
-        L.orc_mc_irradiance.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, u64, u64, ctypes.c_int, vp, vp]
+        L.orc_mc_irradiance.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, u64, u64, ctypes.c_int, vp, vp, vp]
         L.orc_mc_radiance.argtypes = [vp, vp, vp, i64, ctypes.c_int, u64, u64, ctypes.c_int, vp]
         L.orc_sh9.argtypes = [vp, vp]
         L.orc_sh9.restype = None
@@ -135,7 +139,7 @@ def lib():
         L.orc_sh_irradiance.restype = None
         L.orc_sh_project.argtypes = [vp, vp, i64, vp]
         L.orc_sh_project.restype = None
-        L.orc_probe_bake.argtypes = [vp, vp, vp, vp, ctypes.c_int, u64, u64, vp]
+        L.orc_probe_bake.argtypes = [vp, vp, vp, vp, ctypes.c_int, u64, u64, vp, vp]
         L.orc_probe_query.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         L.orc_probe_query_rt.argtypes = [vp, vp, vp, vp, vp, d, vp, vp, i64, vp, vp]
         L.orc_visible.argtypes = [vp, d, d, vp, vp, d]
@@ -312,6 +316,32 @@ def query_fp8(model, params, s_act, pos4, nrm4, aabb_min=(0, 0, 0), aabb_max=(1,
     return E
 
 
+def training_samples(blob, n, surface_frac=0.2, seed=0, index_base=0, with_t=False):
+    """Training-sample candidates of Sec. 4.5 / App. I (see oracle_samples.c):
+    (x4 float32 [n][4], n4 float32 [n][4], t float32 [n] or None, patch int32 [n], -1 = volume)."""
+    b = np.ascontiguousarray(blob, np.float32)
+    x4 = np.zeros((n, 4), np.float32)
+    n4 = np.zeros((n, 4), np.float32)
+    t = np.zeros(n, np.float32) if with_t else None
+    patch = np.zeros(n, np.int32)
+    k = lib().orc_training_samples(_p(b), b.size, n, float(surface_frac), int(seed), int(index_base), _p(x4), _p(n4),
+                                   _p(t) if t is not None else None, _p(patch))
+    if k < 0:
+        raise ValueError("bad scene description")
+    return x4, n4, t, patch
+
+
+def sample_patches(blob):
+    """The surfaces the samples are spread over, in order: float64 [K][13] rows of kind (0 rectangle,
+    1 sphere), axis, normal sign, plane, a0, a1, b0, b1, cx, cy, cz, r, area."""
+    b = np.ascontiguousarray(blob, np.float32)
+    out = np.zeros((512, 13))
+    k = lib().orc_sample_patch_table(_p(b), b.size, _p(out), 512)
+    if k < 0:
+        raise ValueError("bad scene description")
+    return out[:k]
+
+
 def philox(ctr, key):
     c = np.ascontiguousarray(ctr, np.uint32)
     k = np.ascontiguousarray(key, np.uint32)
@@ -320,16 +350,18 @@ def philox(ctr, key):
     return out
 
 
-def mc_irradiance(blob, x4, n4, spp, seed=0, mode=MC_INDIRECT, t=None, index_base=0):
-    """(E[m][3], keep[m]) by Monte Carlo on the scene blob."""
+def mc_irradiance(blob, x4, n4, spp, seed=0, mode=MC_INDIRECT, t=None, index_base=0, want_se=False):
+    """(E[m][3], keep[m]) by Monte Carlo on the scene blob; with want_se also the standard
+    error of each estimate ([m][3], from the sample variance of the path radiances)."""
     x4, n4 = _f32(x4), _f32(n4)
     m = len(x4)
     E = np.zeros((m, 3))
     keep = np.zeros(m, np.uint8)
+    se = np.zeros((m, 3)) if want_se else None
     tt = None if t is None else _f32(t)
     lib().orc_mc_irradiance(_p(_f32(blob)), _p(x4), _p(n4), _p(tt), m, int(spp), int(seed), int(index_base),
-                            int(mode), _p(E), _p(keep))
-    return E, keep
+                            int(mode), _p(E), _p(keep), _p(se))
+    return (E, keep, se) if want_se else (E, keep)
 
 
 def mc_radiance(blob, x4, d4, spp, seed=0, mode=MC_INDIRECT, index_base=0):
@@ -360,12 +392,15 @@ def sh_project(dirs, L):
     return c.reshape(9, 3)
 
 
-def probe_bake(blob, P, lo, hi, rays, seed=0, index_base=0):
+def probe_bake(blob, P, lo, hi, rays, seed=0, index_base=0, want_se=False):
+    """SH9 x RGB coefficients [probes][9][3]; with want_se also their standard errors (same shape,
+    from the sample variance of L Y over the rays)."""
     P = np.ascontiguousarray(P, np.int32)
     out = np.zeros((int(np.prod(P)), 9, 3))
+    se = np.zeros_like(out) if want_se else None
     lib().orc_probe_bake(_p(_f32(blob)), _p(P), _p(_f32(lo)), _p(_f32(hi)), int(rays), int(seed),
-                         int(index_base), _p(out))
-    return out
+                         int(index_base), _p(out), _p(se))
+    return (out, se) if want_se else out
 
 
 def probe_query(coef, P, lo, hi, x4, n4):

@@ -309,8 +309,12 @@ static void radiance(const scene_t* s, const rng_ctx* rng, uint32_t j, const dou
  * per-sample time of the rotating sphere.  Sample i uses rng stream i + index_base.
  * out_E: [m][3] doubles; out_keep (nullable): 1 keep / 0 discard.
  */
+/*
+ * out_se (nullable): per point and channel the standard error of the estimate,
+ * pi sqrt(s^2 / spp) with s^2 the sample variance of the spp path radiances.
+ */
 int orc_mc_irradiance(const float* blob, const float* x4, const float* n4, const float* t, int64_t m, int spp,
-                      uint64_t seed, uint64_t index_base, int mode, double* out_E, uint8_t* out_keep)
+                      uint64_t seed, uint64_t index_base, int mode, double* out_E, uint8_t* out_keep, double* out_se)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < m; ++i) {
@@ -321,7 +325,7 @@ int orc_mc_irradiance(const float* blob, const float* x4, const float* n4, const
         double n[3] = {n4[4 * i], n4[4 * i + 1], n4[4 * i + 2]};
         double nl = sqrt(dot3(n, n));
         for (int k = 0; k < 3; ++k) n[k] /= nl;
-        double acc[3] = {0.0, 0.0, 0.0};
+        double acc[3] = {0.0, 0.0, 0.0}, acc2[3] = {0.0, 0.0, 0.0};
         int hits = 0, back = 0;
         for (int j = 0; j < spp; ++j) {
             double u[4], w[3], L[3];
@@ -331,9 +335,17 @@ int orc_mc_irradiance(const float* blob, const float* x4, const float* n4, const
             radiance(&s, &rng, (uint32_t)j, x, w, mode, L, &fh, &fb);
             hits += fh;
             back += fb;
-            for (int k = 0; k < 3; ++k) acc[k] += L[k];
+            for (int k = 0; k < 3; ++k) {
+                acc[k] += L[k];
+                acc2[k] += L[k] * L[k];
+            }
         }
         for (int k = 0; k < 3; ++k) out_E[3 * i + k] = M_PI * acc[k] / (double)spp;
+        if (out_se)
+            for (int k = 0; k < 3; ++k) {
+                double var = spp > 1 ? (acc2[k] - acc[k] * acc[k] / spp) / (spp - 1) : 0.0;
+                out_se[3 * i + k] = M_PI * sqrt((var > 0.0 ? var : 0.0) / spp);
+            }
         if (out_keep) {
             int zero = out_E[3 * i] == 0.0 && out_E[3 * i + 1] == 0.0 && out_E[3 * i + 2] == 0.0;
             out_keep[i] = (uint8_t)(!(2 * back > spp) && !zero);

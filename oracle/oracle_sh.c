@@ -106,16 +106,20 @@ static void probe_pos(const int* P, const float* lo, const float* hi, int64_t p,
  * directions per probe, one indirect path each.  Probe p's paths use rng stream
  * index_base + p*rays + j.
  */
+/*
+ * out_se (nullable): per coefficient the standard error of the estimate,
+ * 4 pi sqrt(s^2 / rays) with s^2 the sample variance of L(w_j) Y(w_j) over the rays.
+ */
 int orc_probe_bake(const float* blob, const int* P, const float* lo, const float* hi, int rays, uint64_t seed,
-                   uint64_t index_base, double* out)
+                   uint64_t index_base, double* out, double* out_se)
 {
     int64_t np = (int64_t)P[0] * P[1] * P[2];
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t p = 0; p < np; ++p) {
         double x[3];
         probe_pos(P, lo, hi, p, x);
-        double c[27];
-        for (int i = 0; i < 27; ++i) c[i] = 0.0;
+        double c[27], c2[27];
+        for (int i = 0; i < 27; ++i) c[i] = c2[i] = 0.0;
         for (int j = 0; j < rays; ++j) {
             double w[3], L[3], Y[9];
             bake_dir(p, (uint32_t)j, seed, w);
@@ -124,9 +128,17 @@ int orc_probe_bake(const float* blob, const int* P, const float* lo, const float
             orc_mc_radiance(blob, x4, d4, 1, 1, seed, index_base + (uint64_t)p * rays + j, 1, L);
             orc_sh9(w, Y);
             for (int i = 0; i < 9; ++i)
-                for (int k = 0; k < 3; ++k) c[i * 3 + k] += L[k] * Y[i];
+                for (int k = 0; k < 3; ++k) {
+                    c[i * 3 + k] += L[k] * Y[i];
+                    c2[i * 3 + k] += L[k] * Y[i] * L[k] * Y[i];
+                }
         }
         for (int i = 0; i < 27; ++i) out[p * 27 + i] = c[i] * 4.0 * M_PI / (double)rays;
+        if (out_se)
+            for (int i = 0; i < 27; ++i) {
+                double var = rays > 1 ? (c2[i] - c[i] * c[i] / rays) / (rays - 1) : 0.0;
+                out_se[p * 27 + i] = 4.0 * M_PI * sqrt((var > 0.0 ? var : 0.0) / rays);
+            }
     }
     return 0;
 }

@@ -363,3 +363,178 @@ extern "C" int niv_selftest_philox(const uint32_t* in6, int64_t n, uint32_t* out
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }
+
+// ---- training-sample candidates (Sec. 4.5 / App. I) ----
+// A fraction surface_frac of the points lies on the scene's surfaces with the surface normal
+// as direction, spread over the surfaces in proportion to area; the rest is uniform in the
+// room with directions uniform on the sphere.  The surfaces ("patches"), in order: the room
+// walls (axis 0..2, the wall at room_min first, normals into the room; the ceiling cut into
+// the strips around the open skylight: x <= x0, x >= x1, (x0..x1, z <= z0), (x0..x1, z >= z1),
+// empty strips left out), the spheres that do not emit (rest position), then the box faces
+// (axis 0..2, the face at the low corner first, outward normals).  Sample j = index_base + i
+// draws Philox at counters (j lo, j hi, 0x53414D50, 0 and 1) with key (seed lo, seed hi).
+namespace {
+
+constexpr int kMaxPatches = 352;
+constexpr uint32_t kSampleTag = 0x53414D50u;
+
+struct SamplePatches {
+    int count;
+    float lo[3], hi[3];
+    float cdf[kMaxPatches];    // cumulative area fractions (FP64 sums rounded to FP32), last = 1
+    float4 geo0[kMaxPatches];  // rectangle: (0, axis, normal sign, plane); sphere: (1, 0, 0, 0)
+    float4 geo1[kMaxPatches];  // rectangle: (a0, a1, b0, b1) along the two other axes; sphere: (c, r)
+};
+
+// u in (0, 1) from 24 bits: float(x >> 8) 2^-24 + 2^-25, the product exact, one rounding.
+__device__ __forceinline__ float sample_u(uint32_t x) {
+    return __fadd_rn(__fmul_rn((float)(x >> 8), 1.0f / 16777216.0f), 1.0f / 33554432.0f);
+}
+
+// lo + (hi - lo) u in FP32, each operation rounded once.
+__device__ __forceinline__ float sample_span(float lo, float hi, float u) {
+    return __fadd_rn(lo, __fmul_rn(__fsub_rn(hi, lo), u));
+}
+
+// Uniform direction on the sphere: z = 1 - 2u, phi = 2 pi v.
+__device__ __forceinline__ float3 sample_sphere_dir(float u, float v) {
+    const float z = __fsub_rn(1.0f, __fmul_rn(2.0f, u));
+    const float s = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    float sp, cp;
+    sincospif(2.0f * v, &sp, &cp);
+    return make_float3(s * cp, s * sp, z);
+}
+
+__global__ void __launch_bounds__(128) training_samples_kernel(SamplePatches P, int64_t n, float surface_frac,
+                                                               uint64_t seed, uint64_t index_base, float4* __restrict__ x4,
+                                                               float4* __restrict__ n4, float* __restrict__ tout,
+                                                               int32_t* __restrict__ patch) {
+    __shared__ float s_cdf[kMaxPatches];
+    for (int k = threadIdx.x; k < P.count; k += blockDim.x) s_cdf[k] = P.cdf[k];
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t j = index_base + (uint64_t)i;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint4 ra = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)(j >> 32), kSampleTag, 0u), k0, k1);
+    const uint4 rb = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)(j >> 32), kSampleTag, 1u), k0, k1);
+    float3 p, q;
+    int which = -1;
+    if (P.count > 0 && sample_u(ra.x) < surface_frac) {
+        // first patch k with u < cdf[k] (the cdf does not decrease; the last entry is 1)
+        const float u = sample_u(ra.y);
+        int lo = 0, hi = P.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (u < s_cdf[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        which = lo;
+        const float4 g0 = P.geo0[lo], g1 = P.geo1[lo];
+        if (g0.x == 0.0f) {
+            const int axis = (int)g0.y;
+            const float a = sample_span(g1.x, g1.y, sample_u(ra.z)), b = sample_span(g1.z, g1.w, sample_u(ra.w));
+            // in-plane axes in increasing order
+            p = axis == 0 ? make_float3(g0.w, a, b) : (axis == 1 ? make_float3(a, g0.w, b) : make_float3(a, b, g0.w));
+            q = make_float3(axis == 0 ? g0.z : 0.0f, axis == 1 ? g0.z : 0.0f, axis == 2 ? g0.z : 0.0f);
+        } else {
+            q = sample_sphere_dir(sample_u(rb.x), sample_u(rb.y));
+            p = make_float3(g1.x + g1.w * q.x, g1.y + g1.w * q.y, g1.z + g1.w * q.z);
+        }
+    } else {
+        p = make_float3(sample_span(P.lo[0], P.hi[0], sample_u(ra.y)), sample_span(P.lo[1], P.hi[1], sample_u(ra.z)),
+                        sample_span(P.lo[2], P.hi[2], sample_u(ra.w)));
+        q = sample_sphere_dir(sample_u(rb.x), sample_u(rb.y));
+    }
+    x4[i] = make_float4(p.x, p.y, p.z, 0.0f);
+    n4[i] = make_float4(q.x, q.y, q.z, 0.0f);
+    if (tout) tout[i] = sample_u(rb.z);
+    if (patch) patch[i] = which;
+}
+
+// The patch table of a scene description (host); false if it does not fit.
+bool build_patches(const float* blob, SamplePatches& P) {
+    memset(&P, 0, sizeof P);
+    const int ns = (int)blob[0], nb = (int)blob[1];
+    double area[kMaxPatches];
+    int k = 0;
+    auto add_rect = [&](int axis, float sign, float plane, float a0, float a1, float b0, float b1) {
+        if (k >= kMaxPatches) return false;
+        P.geo0[k] = make_float4(0.0f, (float)axis, sign, plane);
+        P.geo1[k] = make_float4(a0, a1, b0, b1);
+        area[k] = ((double)a1 - (double)a0) * ((double)b1 - (double)b0);
+        ++k;
+        return true;
+    };
+    for (int d = 0; d < 3; ++d) {
+        P.lo[d] = blob[4 + d];
+        P.hi[d] = blob[7 + d];
+    }
+    if (blob[2] != 0.0f) {
+        const float sx0 = blob[13], sx1 = blob[14], sz0 = blob[15], sz1 = blob[16];
+        for (int axis = 0; axis < 3; ++axis) {
+            const int a = axis == 0 ? 1 : 0, b = axis == 2 ? 1 : 2;
+            if (!add_rect(axis, 1.0f, P.lo[axis], P.lo[a], P.hi[a], P.lo[b], P.hi[b])) return false;
+            if (axis == 1 && sx0 < sx1) {  // the ceiling around the skylight (a = x, b = z)
+                if (sx0 > P.lo[0] && !add_rect(1, -1.0f, P.hi[1], P.lo[0], sx0, P.lo[2], P.hi[2])) return false;
+                if (P.hi[0] > sx1 && !add_rect(1, -1.0f, P.hi[1], sx1, P.hi[0], P.lo[2], P.hi[2])) return false;
+                if (sz0 > P.lo[2] && !add_rect(1, -1.0f, P.hi[1], sx0, sx1, P.lo[2], sz0)) return false;
+                if (P.hi[2] > sz1 && !add_rect(1, -1.0f, P.hi[1], sx0, sx1, sz1, P.hi[2])) return false;
+            } else if (!add_rect(axis, -1.0f, P.hi[axis], P.lo[a], P.hi[a], P.lo[b], P.hi[b])) {
+                return false;
+            }
+        }
+    }
+    const float* sph = blob + kHdr;
+    for (int i = 0; i < ns; ++i) {
+        const float* s = sph + kSph * i;
+        if (s[7] > 0.0f || s[8] > 0.0f || s[9] > 0.0f) continue;  // emitters are not shaded
+        if (k >= kMaxPatches) return false;
+        P.geo0[k] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+        P.geo1[k] = make_float4(s[0], s[1], s[2], s[3]);
+        area[k] = 4.0 * 3.141592653589793 * (double)s[3] * (double)s[3];
+        ++k;
+    }
+    const float* box = sph + kSph * ns;
+    for (int i = 0; i < nb; ++i) {
+        const float* bl = box + kBox * i;
+        for (int axis = 0; axis < 3; ++axis) {
+            const int a = axis == 0 ? 1 : 0, b = axis == 2 ? 1 : 2;
+            if (!add_rect(axis, -1.0f, bl[axis], bl[a], bl[3 + a], bl[b], bl[3 + b])) return false;
+            if (!add_rect(axis, 1.0f, bl[3 + axis], bl[a], bl[3 + a], bl[b], bl[3 + b])) return false;
+        }
+    }
+    double total = 0.0, acc = 0.0;
+    for (int i = 0; i < k; ++i) total += area[i];
+    for (int i = 0; i < k; ++i) {
+        acc += area[i];
+        P.cdf[i] = (float)(acc / total);
+    }
+    if (k > 0) P.cdf[k - 1] = 1.0f;
+    P.count = k;
+    return true;
+}
+
+}  // namespace
+
+extern "C" int niv_training_samples(const float* scene, int64_t scene_len, int64_t n, float surface_frac,
+                                    uint64_t seed, uint64_t index_base, float* x4, float* n4, float* t,
+                                    int32_t* patch, niv_stream stream) {
+    if (!scene) return niv_fail(NIV_ERR_ARG, "scene is NULL");
+    if (n < 0) return niv_fail(NIV_ERR_ARG, "n < 0");
+    if (!(surface_frac >= 0.0f && surface_frac <= 1.0f)) return niv_fail(NIV_ERR_ARG, "surface_frac outside [0, 1]");
+    const int ns = (int)scene[0], nb = (int)scene[1];
+    if (ns < 0 || nb < 0 || ns + nb > kMaxObjects) return niv_fail(NIV_ERR_UNSUPPORTED, "at most 56 scene objects");
+    if (scene_len != kHdr + kSph * ns + kBox * nb) return niv_fail(NIV_ERR_ARG, "scene description length mismatch");
+    if (n == 0) return NIV_OK;
+    if (!x4 || !n4) return niv_fail(NIV_ERR_ARG, "NULL output");
+    if (((uintptr_t)x4 | (uintptr_t)n4) & 15u) return niv_fail(NIV_ERR_ALIGN, "records must be 16-byte aligned");
+    SamplePatches P;
+    if (!build_patches(scene, P)) return niv_fail(NIV_ERR_UNSUPPORTED, "more surface patches than the sampler holds");
+    const int64_t blocks = (n + 127) / 128;
+    if (blocks > 0x7FFFFFFF) return niv_fail(NIV_ERR_ARG, "n too large");
+    training_samples_kernel<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(
+        P, n, surface_frac, seed, index_base, reinterpret_cast<float4*>(x4), reinterpret_cast<float4*>(n4), t, patch);
+    NIV_CUDA(cudaGetLastError());
+    return NIV_OK;
+}

@@ -1,16 +1,19 @@
 """Training driver (Sec. 4.5): Monte Carlo targets -> culling -> Adam steps.
 
-Orchestration only: every numeric step runs in libniv's kernels (Monte Carlo
-irradiance, compaction of kept samples, forward/backward, Adam).  The candidate
-points come from niv_inputs.samples (the paper's sampling: uniform in the volume
-with uniform directions, 20% on surfaces with the surface normal).
+Orchestration only: every numeric step runs in libniv's kernels (candidate points,
+Monte Carlo irradiance, compaction of kept samples, forward/backward, Adam).  The
+candidates follow the paper's sampling (niv_training_samples: uniform in the volume
+with uniform directions, 20% on surfaces with the surface normal, by area).
 """
 import time
 
 import numpy as np
 import torch
 
-from .model import mc_irradiance, compact_targets
+from .model import mc_irradiance, compact_targets, training_samples
+
+# Counter ranges of the sample streams: training pools take [0, 2^40), held-out sets start at 2^40.
+HELD_OUT_BASE = 1 << 40
 
 
 def train(model, scene, steps, batch, pool=1 << 18, spp=256, reuse=4, seed=0, lr=1e-2, beta1=0.9, beta2=0.99,
@@ -23,17 +26,15 @@ def train(model, scene, steps, batch, pool=1 << 18, spp=256, reuse=4, seed=0, lr
     passes.  forward: "fp16" runs the FP16 path of the query in the forward (config 2), "fp32"
     the FP32 one.  Returns a dict with the loss history and the time spent per phase.
     """
-    from niv_inputs.samples import training_pool
     model.set_train_forward(forward)
     blob = scene.blob()
     hist, t_mc, t_fit = [], 0.0, 0.0
     step, pool_id, index_base = 0, 0, 0
     while step < steps:
-        x4, n4, t = training_pool(scene, pool, seed=seed * 1000003 + pool_id, with_t=with_t)
-        dx, dn = torch.from_numpy(x4).to(device), torch.from_numpy(n4).to(device)
-        dt = torch.from_numpy(t).to(device) if t is not None else None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        dx, dn, dt, _ = training_samples(blob, pool, seed=seed, index_base=pool_id * pool, with_t=with_t,
+                                         device=device)
         E, keep = mc_irradiance(blob, dx, dn, spp, seed=seed, mode="indirect", t=dt, index_base=index_base)
         kx, kn, ky, kt = compact_targets(dx, dn, E, keep, t=dt)
         torch.cuda.synchronize()
@@ -64,12 +65,11 @@ def train(model, scene, steps, batch, pool=1 << 18, spp=256, reuse=4, seed=0, lr
 def held_out(scene, n, spp, seed, with_t=False, t_levels=0, device="cuda"):
     """Evaluation samples (kept after culling) and their Monte Carlo reference E (float64, [k][3]).
     t_levels > 0: sample i takes t = ((i mod t_levels) + 1/2) / t_levels instead of a uniform t."""
-    from niv_inputs.samples import training_pool
-    x4, n4, t = training_pool(scene, n, seed=seed, with_t=with_t)
+    dx, dn, dt, _ = training_samples(scene.blob(), n, seed=seed, index_base=HELD_OUT_BASE, with_t=with_t,
+                                     device=device)
     if with_t and t_levels > 0:
-        t = ((np.arange(len(t)) % t_levels + 0.5) / t_levels).astype(np.float32)
-    dx, dn = torch.from_numpy(x4).to(device), torch.from_numpy(n4).to(device)
-    dt = torch.from_numpy(t).to(device) if t is not None else None
+        t = ((np.arange(n) % t_levels + 0.5) / t_levels).astype(np.float32)
+        dt = torch.from_numpy(t).to(device)
     E, keep = mc_irradiance(scene.blob(), dx, dn, spp, seed=seed + 77, mode="indirect", t=dt, index_base=1 << 40)
     keep_b = keep.bool()
     return dx[keep_b].contiguous(), dn[keep_b].contiguous(), E[keep_b], (dt[keep_b] if dt is not None else None)
@@ -84,17 +84,17 @@ def errors(pred, ref):
     return mse, rel
 
 
-def memory_error_sweep(scene, log2_Ts, shape, steps=2000, batch=1 << 16, pool=1 << 18, spp=128, reuse=2,
-                       held=(1 << 14, 4096), probe_rays=1024, seed=1, aabb_min=(-5.0, -5.0, -5.0),
+def memory_error_sweep(scene, log2_Ts, shape, init_params, steps=2000, batch=1 << 16, pool=1 << 18, spp=128,
+                       reuse=2, held=(1 << 14, 4096), probe_rays=1024, seed=1, aabb_min=(-5.0, -5.0, -5.0),
                        aabb_max=(5.0, 5.0, 5.0), device="cuda"):
     """Memory-error trade-off (Sec. 4.1's hash-table-size study and Sec. 5.1's comparison with
     probes): for every hash table size 2^log2_T, NIV of the given shape is trained on `scene`,
     and the SH probe grid with the largest cubic lattice that fits the same memory is baked;
     the probes are queried with the cosine fall-off and with ray-traced visibility ("+ RT").
     Returns one row per size with the FP16 memory and the (MSE, relative MSE) of each on the
-    same held-out samples (Monte Carlo references at held[1] spp)."""
+    same held-out samples (Monte Carlo references at held[1] spp).  init_params(n_grid, layer_shapes,
+    seed) gives each model's initial flat parameter vector."""
     import torch
-    from niv_inputs import init_params
     from .model import NIVModel, ProbeGrid
     hx, hn, hE, _ = held_out(scene, held[0], held[1], seed=99, device=device)
     rows = []
@@ -123,16 +123,16 @@ def memory_error_sweep(scene, log2_Ts, shape, steps=2000, batch=1 << 16, pool=1 
     return rows
 
 
-def time_field_comparison(scene, shapes, steps=2000, batch=1 << 16, pool=1 << 18, spp=128, reuse=2,
+def time_field_comparison(scene, shapes, init_params, steps=2000, batch=1 << 16, pool=1 << 18, spp=128, reuse=2,
                           held=(1 << 14, 4096), seed=1, aabb_min=(-5.0, -5.0, -5.0), aabb_max=(5.0, 5.0, 5.0),
                           frame=None, device="cuda"):
     """Fields that change with a scene parameter t (Sec. 6; config 3): every model in `shapes`
     (name -> NIVModel keyword arguments) is trained on samples with a uniform per-sample t of
     `scene` (its rotating emitter moves with t) and scored on the same held-out (x, n, t)
     samples.  frame (optional (pos, nrm, width) device records): the FP16 query time of each
-    model on it at t = 0.5.  Returns one row per model: FP16 memory, MSE, relative MSE, ms."""
+    model on it at t = 0.5.  init_params(n_grid, layer_shapes, seed) gives each model's initial flat
+    parameter vector.  Returns one row per model: FP16 memory, MSE, relative MSE, ms."""
     import torch
-    from niv_inputs import init_params
     from .model import NIVModel
     hx, hn, hE, ht = held_out(scene, held[0], held[1], seed=199, with_t=True, t_levels=16, device=device)
     rows = []

@@ -49,11 +49,13 @@ class NIVModel:
         check(lib().niv_create(ctypes.byref(self.desc), ctypes.byref(h)))
         self._h = h
 
-    # model files: "NIVM", version 1, the description field by field, the count, the FP32 parameters
+    # model files: "NIVM", version, the description field by field, the count, the FP32 parameters
+    # (then, from version 2, the optimiser state; see niv.h)
     _FILE_HEAD = struct.Struct("<4sI4i2d5iI2iq")
 
     def save(self, path, stream=None):
-        """Write the description and the FP32 master parameters to `path` (niv_save)."""
+        """Write the description, the FP32 master parameters and the optimiser state (Adam
+        moments, step count, training forward) to `path` (niv_save)."""
         check(lib().niv_save(self._h, os.fsencode(path), _stream(stream)))
 
     @classmethod
@@ -443,6 +445,22 @@ def mc_irradiance(scene_blob, x4, n4, spp, seed=0, mode="indirect", t=None, inde
                                   int(index_base), md, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(keep.data_ptr()),
                                   _stream(stream)))
     return E, keep
+
+
+def training_samples(scene_blob, n, surface_frac=0.2, seed=0, index_base=0, with_t=False, want_patch=False,
+                     device="cuda", stream=None):
+    """Training-sample candidates of Sec. 4.5 / App. I on the device (niv_training_samples):
+    (x4 [n][4], n4 [n][4], t [n] or None, patch [n] int32 or None), float32 device tensors."""
+    blob = np.ascontiguousarray(scene_blob, np.float32)
+    x4 = torch.empty((n, 4), dtype=torch.float32, device=device)
+    n4 = torch.empty((n, 4), dtype=torch.float32, device=device)
+    t = torch.empty(n, dtype=torch.float32, device=device) if with_t else None
+    patch = torch.empty(n, dtype=torch.int32, device=device) if want_patch else None
+    check(lib().niv_training_samples(ctypes.c_void_p(blob.ctypes.data), blob.size, int(n), float(surface_frac),
+                                     int(seed), int(index_base), ctypes.c_void_p(x4.data_ptr()),
+                                     ctypes.c_void_p(n4.data_ptr()), ctypes.c_void_p(t.data_ptr() if t is not None else 0),
+                                     ctypes.c_void_p(patch.data_ptr() if patch is not None else 0), _stream(stream)))
+    return x4, n4, t, patch
 
 
 def compact_targets(x4, n4, E, keep, t=None, stream=None):

@@ -76,8 +76,27 @@ def test_inside_geometry_is_culled(niv):
     assert keep.cpu().numpy().tolist() == [0, 1]
 
 
+def near_geometry(scene, x, eps=1e-2):
+    """Points inside an object or within eps of a surface of the scene (room walls, spheres,
+    boxes): there FP32 and FP64 geometry can decide a first hit differently, and the paths of the
+    two integrators part."""
+    x = np.asarray(x, np.float64)[:, :3]
+    flag = np.zeros(len(x), bool)
+    lo, hi = np.asarray(scene.room_min, np.float64), np.asarray(scene.room_max, np.float64)
+    flag |= np.any((x - lo < eps) | (hi - x < eps), axis=1)
+    for sph in np.asarray(scene.spheres, np.float64):
+        flag |= np.linalg.norm(x - sph[:3], axis=1) < sph[3] + eps
+    for bx in np.asarray(scene.boxes, np.float64):
+        flag |= np.all((x > bx[:3] - eps) & (x < bx[3:6] + eps), axis=1)
+    return flag
+
+
 def test_room_matches_cpu_oracle(niv):
-    """Indirect irradiance in the seeded room (skylight, emitter, rotating emitter time): GPU vs CPU oracle."""
+    """Indirect irradiance in the seeded room (skylight, emitter, rotating emitter time): GPU vs CPU
+    oracle on the same streams.  On every point both sides keep and that is not within 1 cm of
+    geometry: |E_gpu - E_cpu| within 4 combined standard errors (sqrt(2) times the oracle's
+    standard error of the estimate); and the shared streams make most points agree to float
+    rounding."""
     scene = room_scene(0)
     blob = scene.blob()
     rng = np.random.default_rng(2)
@@ -89,15 +108,19 @@ def test_room_matches_cpu_oracle(niv):
     nr = np.zeros((m, 4), np.float32)
     xr[:, :3], nr[:, :3] = x, n
     spp = 256
-    Eg, kg = niv.mc_irradiance(blob, torch.from_numpy(xr).cuda(), torch.from_numpy(nr).cuda(), spp=spp, seed=11,
-                               mode="indirect", t=torch.from_numpy(t).cuda())
+    dx, dn, dt = torch.from_numpy(xr).cuda(), torch.from_numpy(nr).cuda(), torch.from_numpy(t).cuda()
+    Eg, kg = niv.mc_irradiance(blob, dx, dn, spp=spp, seed=11, mode="indirect", t=dt)
     Eg, kg = Eg.cpu().numpy(), kg.cpu().numpy()
-    Ec, kc = oracle.mc_irradiance(blob, xr, nr, spp, seed=11, mode=oracle.MC_INDIRECT, t=t)
+    Ec, kc, se = oracle.mc_irradiance(blob, xr, nr, spp, seed=11, mode=oracle.MC_INDIRECT, t=t, want_se=True)
     assert (kg == kc).mean() >= 0.99
     both = (kg == 1) & (kc == 1)
-    rel = np.abs(Eg[both] - Ec[both]).max(axis=1) / np.maximum(Ec[both].max(axis=1), 1e-6)
-    print("room: median rel diff %.3g, p90 %.3g, frame-mean ratio %.5f" % (
-        np.median(rel), np.percentile(rel, 90), Eg[both].mean() / Ec[both].mean()))
+    checked = both & ~near_geometry(scene, xr)
+    diff = np.abs(Eg - Ec)
+    bound = 4.0 * math.sqrt(2.0) * se + 1e-9 * np.abs(Ec).max()
+    rel = diff[both].max(axis=1) / np.maximum(Ec[both].max(axis=1), 1e-6)
+    print("room: %d points checked, median rel diff %.3g, p90 %.3g, largest |diff| / (4 sqrt2 se) %.3g" % (
+        checked.sum(), np.median(rel), np.percentile(rel, 90), float((diff[checked] / bound[checked]).max())))
+    assert checked.sum() >= 0.8 * both.sum()
+    assert np.all(diff[checked] <= bound[checked])
     # identical random streams: most points agree to float rounding, a few differ by path divergence
     assert np.median(rel) < 1e-4
-    assert abs(Eg[both].mean() / Ec[both].mean() - 1) < 0.02

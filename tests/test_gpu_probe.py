@@ -21,18 +21,31 @@ def niv():
 
 
 def test_probe_bake_matches_oracle(niv):
-    """Same Philox streams: the GPU bake reproduces the oracle's coefficients."""
+    """Same Philox streams: the GPU bake reproduces the oracle's coefficients.  Paths coincide
+    except where FP32 and FP64 geometry decide a hit differently, so on every probe not within 1 cm
+    of geometry each coefficient lies within 4 combined standard errors (sqrt(2) times the oracle's
+    standard error of the coefficient), and most agree to float rounding."""
+    from test_gpu_mc import near_geometry
     scene = room_scene(0)
     P = (3, 4, 3)
     lo, hi = np.array([-4.0, -4.0, -4.0], np.float32), np.array([4.0, 4.0, 4.0], np.float32)
     g = niv.ProbeGrid(P, lo, hi)
     c64 = g.bake(scene.blob(), rays=2048, seed=5, want_f64=True).cpu().numpy()
-    ref = oracle.probe_bake(scene.blob(), np.array(P, np.int32), lo, hi, rays=2048, seed=5)
-    ref = ref.reshape(len(ref), 27)
-    err = np.abs(c64 - ref).max() / np.abs(ref).max()
-    print("bake max err normalised %.3g" % err)
-    assert err < 2e-2  # identical paths except FP32-vs-FP64 geometry decisions
-    assert np.median(np.abs(c64 - ref) / np.abs(ref).max()) < 1e-4
+    c64_again = g.bake(scene.blob(), rays=2048, seed=5, want_f64=True).cpu().numpy()
+    np.testing.assert_array_equal(c64_again, c64)  # the bake is deterministic for a given stream
+    ref, se = oracle.probe_bake(scene.blob(), np.array(P, np.int32), lo, hi, rays=2048, seed=5, want_se=True)
+    ref, se = ref.reshape(len(ref), 27), se.reshape(len(se), 27)
+    ijk = np.stack(np.unravel_index(np.arange(int(np.prod(P))), P[::-1]), -1)[:, ::-1]  # probe index: x fastest
+    probes = lo + (hi - lo) * ijk / (np.array(P) - 1)
+    checked = ~near_geometry(scene, probes)
+    diff = np.abs(c64 - ref)
+    bound = 4.0 * np.sqrt(2.0) * se + 1e-9 * np.abs(ref).max()
+    err = diff / np.abs(ref).max()
+    print("bake: %d of %d probes checked, max err normalised %.3g, median %.3g, largest |diff| / (4 sqrt2 se) %.3g"
+          % (checked.sum(), len(checked), err.max(), np.median(err), float((diff[checked] / bound[checked]).max())))
+    assert checked.sum() >= len(checked) // 2
+    assert np.all(diff[checked] <= bound[checked])
+    assert np.median(err) < 1e-4
     c16 = g.coef16.cpu().numpy().astype(np.float64)
     np.testing.assert_array_equal(c16[:, 27], 0.0)
     # the kernel rounds FP64 -> FP32 -> FP16

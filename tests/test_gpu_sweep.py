@@ -9,7 +9,7 @@ visibility changes the probe answer.  The table is printed.
 """
 import pytest
 
-from niv_inputs import room_scene
+from niv_inputs import init_params, room_scene
 from niv_inputs.configs import MODEL_C1
 
 pytestmark = pytest.mark.gpu
@@ -26,7 +26,7 @@ def niv():
 
 def test_memory_error_tradeoff(niv):
     from paper_2602_12949_gb300 import fitting
-    rows = fitting.memory_error_sweep(room_scene(0), [13, 15, 17], MODEL_C1, steps=1500)
+    rows = fitting.memory_error_sweep(room_scene(0), [13, 15, 17], MODEL_C1, init_params, steps=1500)
     for r in rows:
         print("T=2^%d %6.2f MB: NIV MSE %.3g | probes %d^3 (%.2f MB) MSE %.3g, +RT %.3g | ratio %.1fx"
               % (r["log2_T"], r["mb"], r["niv_mse"], r["probes_per_axis"], r["probe_mb"], r["probe_mse"],

@@ -10,7 +10,7 @@ is learned.  The table is printed.
 """
 import pytest
 
-from niv_inputs import room_scene
+from niv_inputs import init_params, room_scene
 from niv_inputs.configs import MODEL_C3
 
 pytestmark = pytest.mark.gpu
@@ -35,7 +35,7 @@ def niv():
 
 def test_time_aware_designs_learn_t(niv):
     from paper_2602_12949_gb300 import fitting
-    rows = fitting.time_field_comparison(room_scene(0), SHAPES, steps=1500)
+    rows = fitting.time_field_comparison(room_scene(0), SHAPES, init_params, steps=1500)
     for r in rows:
         print("%-48s %6.2f MB  MSE %.3g  rel %.3g" % (r["model"], r["mb"], r["mse"], r["rel_mse"]))
     mse = {r["model"]: r["mse"] for r in rows}

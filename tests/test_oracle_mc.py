@@ -123,3 +123,26 @@ def test_philox_uniform_and_decorrelated():
     # different keys give different streams; same counter and key give the same words
     assert not np.array_equal(oracle.philox([1, 2, 3, 4], [0, 0]), oracle.philox([1, 2, 3, 4], [0, 1]))
     assert np.array_equal(oracle.philox([1, 2, 3, 4], [5, 6]), oracle.philox([1, 2, 3, 4], [5, 6]))
+
+
+def test_standard_error_matches_the_spread_of_independent_estimates():
+    """The per-point standard error the oracle reports (sample variance of the path radiances)
+    agrees with the spread of independent estimates on other streams."""
+    from niv_inputs import room_scene
+    blob = room_scene(0).blob()
+    x = np.tile(np.array([[1.0, -2.0, 0.5, 0.0]], np.float32), (200, 1))
+    n = np.tile(np.array([[0.0, 1.0, 0.0, 0.0]], np.float32), (200, 1))
+    # 200 estimates of the same point, each on its own stream (index_base = point index)
+    E, keep, se = oracle.mc_irradiance(blob, x, n, 64, seed=3, mode=oracle.MC_INDIRECT, want_se=True)
+    spread = E.std(axis=0, ddof=1)
+    rms_se = np.sqrt((se ** 2).mean(axis=0))
+    np.testing.assert_allclose(rms_se, spread, rtol=0.25)
+    # the bake's standard error against 100 bakes of the same probe on other streams
+    P = np.array([2, 2, 2], np.int32)
+    lo, hi = np.array([-1, -1, -1], np.float32), np.array([1, 1, 1], np.float32)
+    bakes = np.stack([oracle.probe_bake(blob, P, lo, hi, 32, seed=10 + k) for k in range(100)])
+    _, cse = oracle.probe_bake(blob, P, lo, hi, 32, seed=10, want_se=True)
+    spread = bakes.std(axis=0, ddof=1)
+    big = spread > 0.05 * spread.max()
+    ratio = np.sqrt((cse[big] ** 2).mean()) / np.sqrt((spread[big] ** 2).mean())
+    assert 0.8 < ratio < 1.25
