@@ -163,13 +163,16 @@ NIV_API int niv_get_params(niv_handle h, float* out, int64_t n, niv_stream strea
 
 /*
  * Save a model to a file, and load one into a new handle on the current device.  The
- * file holds, little-endian: the 4 bytes "NIVM", uint32 format version 1; the model
+ * file holds, little-endian: the 4 bytes "NIVM", uint32 format version 2; the model
  * description field by field in the order of niv_model_desc (int32 dims, levels, feat,
  * log2_T; float64 base, growth; int32 n_hidden, width, in_extra, out_dim, out_act;
- * uint32 prime_t; int32 pe_bands, t_bands); int64 n; then the n FP32 master parameters in
- * the order of niv_set_params.  The Adam state is not saved (a loaded model starts a new
- * optimisation).
- *  - niv_save synchronises `stream` (the parameters are read from the device).
+ * uint32 prime_t; int32 pe_bands, t_bands); int64 n; the n FP32 master parameters in
+ * the order of niv_set_params; then the optimiser state, so that training resumes where
+ * it stopped: int32 training forward precision (NIV_FP32 or NIV_FP16), int64 Adam step
+ * count, int32 1 if the Adam moments follow (a training call has run) else 0, and then
+ * the n FP32 first moments and the n FP32 second moments.  Version 1 files (no
+ * optimiser state) still load, starting a new optimisation.
+ *  - niv_save synchronises `stream` (parameters and moments are read from the device).
  *  - niv_load reads and checks the header before it touches the device: a missing file,
  *    another magic or version, or a description that niv_create refuses is NIV_ERR_ARG
  *    with a message.  A parameter count that differs from the description's, or a short
@@ -292,6 +295,28 @@ NIV_API int niv_fp8_get_scales(niv_handle h, float* s_act, float* s_w, float* am
 /* Monte Carlo modes: every radiance reaching x, or only light that bounced at least once. */
 #define NIV_MC_TOTAL 0
 #define NIV_MC_INDIRECT 1
+
+/*
+ * Training-sample candidates (Sec. 4.5 / App. I): a fraction surface_frac (0.2 in
+ * the paper) of the n points lie on the scene's surfaces, spread over them in
+ * proportion to area, with the surface normal as direction; the rest are uniform
+ * in the room with directions uniform on the sphere.  The surfaces, in order: the
+ * room walls (axis 0..2, the wall at room_min first, normals into the room; the
+ * ceiling cut into the strips around the open skylight), every sphere that does
+ * not emit (at rest), every box face (outward normals).  Sample j = index_base + i
+ * draws Philox4x32-10 at counters (j lo, j hi, 0x53414D50, 0 | 1), key (seed lo,
+ * seed hi); u = float(r >> 8) 2^-24 + 2^-25.  Surface iff u(r0) < surface_frac;
+ * surface k = first k with u(r1) < cdf[k] (cumulative area fractions, FP64 sums
+ * rounded to FP32); rectangle coordinates lo + (hi - lo) u in FP32; sphere points
+ * c + r d; t = u(r6).
+ * scene: host description as in niv_mc_irradiance; x4, n4: device float32 [n][4]
+ * (16-byte aligned); t: device float32 [n] or NULL; patch: device int32 [n] or NULL
+ * (-1 for volume samples, else the surface index).  Candidates inside geometry are
+ * left in (niv_mc_irradiance flags them).  Asynchronous.
+ */
+NIV_API int niv_training_samples(const float* scene, int64_t scene_len, int64_t n, float surface_frac, uint64_t seed,
+                                 uint64_t index_base, float* x4, float* n4, float* t, int32_t* patch,
+                                 niv_stream stream);
 
 /*
  * Monte Carlo irradiance of the analytic scene (Eq. 1): the training targets of

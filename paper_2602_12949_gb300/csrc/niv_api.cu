@@ -182,8 +182,13 @@ GridArgs niv_grid_args(const niv_model* m, const niv_query_params* p) {
         g.resm1_f[l] = (float)(m->res[l] - 1);
         g.stride1[l] = (uint32_t)m->res[l] + 1u;
         g.stride2[l] = g.stride1[l] * g.stride1[l];
+        g.resm1_b[l] = (float)(8388608.0 + (double)(m->res[l] - 1));  // exact: N <= 2^20
+        uint32_t span = 1u + g.stride1[l] + g.stride2[l];
+        if (m->d.dims == 4) span += g.stride2[l] * g.stride1[l];
+        g.dense_off[l] = 0u - kNivBias * span;
         if (m->dense[l]) g.dense_mask |= 1u << l;
     }
+    g.prime_t_off = 0u - kNivBias * g.prime_t;
     for (int k = 0; k < 3; ++k) {
         g.aabb_min[k] = p->aabb_min[k];
         g.inv_ext[k] = (float)(1.0 / ((double)p->aabb_max[k] - (double)p->aabb_min[k]));
@@ -335,9 +340,10 @@ int niv_get_params(niv_handle h, float* out, int64_t n, niv_stream stream) {
 
 namespace {
 // Model files (little-endian hosts): "NIVM", version, the description field by field, the
-// parameter count, the FP32 parameters.
+// parameter count, the FP32 parameters; version 2 adds the optimiser state (training forward
+// precision, Adam step count, whether the moments follow, the two FP32 moment vectors).
 constexpr char kFileMagic[4] = {'N', 'I', 'V', 'M'};
-constexpr uint32_t kFileVersion = 1;
+constexpr uint32_t kFileVersion = 2;
 
 bool put_bytes(FILE* f, const void* v, size_t n) { return fwrite(v, n, 1, f) == 1; }
 bool get_bytes(FILE* f, void* v, size_t n) { return fread(v, n, 1, f) == 1; }
@@ -362,10 +368,23 @@ int niv_save(niv_handle h, const char* path, niv_stream stream) {
     std::vector<float> params((size_t)n);
     int rc = niv_get_params(h, params.data(), n, stream);
     if (rc) return rc;
+    // the optimiser state: Adam moments exist once a training call has run
+    const int32_t fwd = h->train_f16 ? NIV_FP16 : NIV_FP32;
+    const int64_t step = h->adam_step;
+    const int32_t has_moments = (h->adam_m && h->adam_v) ? 1 : 0;
+    std::vector<float> mom;
+    if (has_moments) {
+        mom.resize(2 * (size_t)n);
+        cudaStream_t s = (cudaStream_t)stream;
+        NIV_CUDA(cudaMemcpyAsync(mom.data(), h->adam_m, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+        NIV_CUDA(cudaMemcpyAsync(mom.data() + n, h->adam_v, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+        NIV_CUDA(cudaStreamSynchronize(s));
+    }
     FILE* f = fopen(path, "wb");
     if (!f) return niv_fail(NIV_ERR_ARG, std::string("cannot open for writing: ") + path);
     bool ok = fwrite(kFileMagic, 1, 4, f) == 4 && put(f, kFileVersion) && put_desc(f, h->d) && put(f, n) &&
-              fwrite(params.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+              fwrite(params.data(), sizeof(float), (size_t)n, f) == (size_t)n && put(f, fwd) && put(f, step) &&
+              put(f, has_moments) && (!has_moments || fwrite(mom.data(), sizeof(float), mom.size(), f) == mom.size());
     ok = (fclose(f) == 0) && ok;
     if (!ok) return niv_fail(NIV_ERR_ARG, std::string("write failed: ") + path);
     return NIV_OK;
@@ -384,7 +403,7 @@ int niv_load(const char* path, niv_handle* out) {
         fclose(f);
         return niv_fail(NIV_ERR_ARG, "not a model file (magic)");
     }
-    if (version != kFileVersion || !get_desc(f, d) || !get(f, n)) {
+    if (version < 1 || version > kFileVersion || !get_desc(f, d) || !get(f, n)) {
         fclose(f);
         return niv_fail(NIV_ERR_ARG, "unsupported model file version or truncated header");
     }
@@ -404,18 +423,36 @@ int niv_load(const char* path, niv_handle* out) {
         niv_destroy(h);
         return niv_fail(NIV_ERR_ARG, "parameter count differs from the description's");
     }
-    std::vector<float> params((size_t)n);
-    const bool full = fread(params.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+    std::vector<float> params((size_t)n), mom;
+    bool full = fread(params.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+    int32_t fwd = NIV_FP32, has_moments = 0;
+    int64_t step = 0;
+    if (full && version >= 2) {  // the optimiser state
+        full = get(f, fwd) && get(f, step) && get(f, has_moments) && (fwd == NIV_FP32 || fwd == NIV_FP16) &&
+               step >= 0 && (has_moments == 0 || has_moments == 1);
+        if (full && has_moments) {
+            mom.resize(2 * (size_t)n);
+            full = fread(mom.data(), sizeof(float), mom.size(), f) == mom.size();
+        }
+    }
     fclose(f);
     if (!full) {
         niv_destroy(h);
-        return niv_fail(NIV_ERR_ARG, "model file truncated");
+        return niv_fail(NIV_ERR_ARG, "model file truncated or its optimiser state malformed");
     }
     rc = niv_set_params(h, params.data(), n, nullptr);
+    if (!rc && has_moments) rc = ensure_training_state(h);
+    if (!rc && has_moments) {
+        cudaError_t e = cudaMemcpy(h->adam_m, mom.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->adam_v, mom.data() + n, sizeof(float) * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = niv_cuda_fail(e, "niv_load: Adam moments");
+    }
     if (rc) {
         niv_destroy(h);
         return rc;
     }
+    h->train_f16 = fwd == NIV_FP16;
+    h->adam_step = step;
     *out = h;
     return NIV_OK;
 }

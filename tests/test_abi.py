@@ -85,7 +85,7 @@ def test_model_files_are_checked_before_the_device(libniv, tmp_path):
     assert b"magic" in libniv.niv_last_error()
     head = struct.Struct("<4sI4i2d5iI2iq")
     newer = tmp_path / "newer.niv"
-    newer.write_bytes(head.pack(b"NIVM", 2, 3, 8, 2, 14, 4.0, 1.5, 2, 64, 3, 3, 1, 1, 0, 0, 10))
+    newer.write_bytes(head.pack(b"NIVM", 3, 3, 8, 2, 14, 4.0, 1.5, 2, 64, 3, 3, 1, 1, 0, 0, 10))
     assert libniv.niv_load(str(newer).encode(), ctypes.byref(h)) == NIV_ERR_ARG
     bad_desc = tmp_path / "bad.niv"
     bad_desc.write_bytes(head.pack(b"NIVM", 1, 5, 8, 2, 14, 4.0, 1.5, 2, 64, 3, 3, 1, 1, 0, 0, 10))  # dims 5
