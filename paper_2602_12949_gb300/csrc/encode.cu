@@ -26,31 +26,21 @@ __global__ void __launch_bounds__(128) encode_kernel(GridArgs g, IoArgs io, cons
             enc[q * ne + LG + 2 * (d * g.pe_bands + b)] = sv;
             enc[q * ne + LG + 2 * (d * g.pe_bands + b) + 1] = cv;
         }
+    // the corner entries and weights of every level come from the helper the query and training
+    // kernels use, so that the index output checks their integer pipeline itself
     for (int l = 0; l < g.levels; ++l) {
-        const int32_t N = g.res[l];
-        const bool dense = (g.dense_mask >> l) & 1u;
-        uint32_t ci[DIMS];
-        float cw[DIMS];
-#pragma unroll
-        for (int d = 0; d < DIMS; ++d) niv_cell(u[d], N, ci[d], cw[d]);
+        uint32_t e[NC];
+        float wc[NC];
+        niv_level_corners<DIMS>(g, l, u, e, wc);
         const float* tab = grid + (size_t)g.offset[l] * F;
         float acc[F];
 #pragma unroll
         for (int j = 0; j < F; ++j) acc[j] = 0.0f;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            uint32_t v[DIMS];
-            float wc = 1.0f;
+            if (idx) idx[(q * g.levels + l) * NC + c] = e[c];
 #pragma unroll
-            for (int d = 0; d < DIMS; ++d) {
-                const int bit = (c >> d) & 1;
-                v[d] = ci[d] + bit;
-                wc *= bit ? cw[d] : 1.0f - cw[d];
-            }
-            const uint32_t e = niv_vertex_index<DIMS>(dense, (uint32_t)N + 1u, v, g.hash_mask, g.prime_t);
-            if (idx) idx[(q * g.levels + l) * NC + c] = e;
-#pragma unroll
-            for (int j = 0; j < F; ++j) acc[j] = fmaf(wc, __ldg(tab + (size_t)e * F + j), acc[j]);
+            for (int j = 0; j < F; ++j) acc[j] = fmaf(wc[c], __ldg(tab + (size_t)e[c] * F + j), acc[j]);
         }
         if (enc)
 #pragma unroll

@@ -37,7 +37,19 @@ struct GridArgs {
     float resm1_f[NIV_MAX_LEVELS];
     uint32_t stride1[NIV_MAX_LEVELS];
     uint32_t stride2[NIV_MAX_LEVELS];
+    // the cell search without conversions (NIV_MAGIC_FLOOR): 2^23 + N - 1 as a float, and the
+    // offsets that remove the 2^23 bias (0x4B000000 in the bit pattern) from the index terms:
+    // dense levels -B (1 + S + S^2 (+ S^3)), the time prime -B pi_t (mod 2^32)
+    float resm1_b[NIV_MAX_LEVELS];
+    uint32_t dense_off[NIV_MAX_LEVELS];
+    uint32_t prime_t_off;
 };
+
+#ifndef NIV_MAGIC_FLOOR
+#define NIV_MAGIC_FLOOR 0
+#endif
+// Bit pattern of the float 2^23: a float 2^23 + i (0 <= i < 2^23) has the bits kNivBias + i.
+constexpr uint32_t kNivBias = 0x4B000000u;
 
 // Where a kernel finds its records and how it walks them.
 struct IoArgs {
@@ -74,33 +86,10 @@ __device__ __forceinline__ float niv_unit(float p, float lo, float inv) {
     return fminf(fmaxf(x, 0.0f), 1.0f);
 }
 
-// Cell of one coordinate at resolution N: s = fp32(u * N), i = min(floor(s), N - 1), w = s - i (exact).
-__device__ __forceinline__ void niv_cell(float u, int32_t N, uint32_t& i, float& w) {
-    float s = __fmul_rn(u, (float)N);
-    int ii = min((int)floorf(s), N - 1);
-    i = (uint32_t)ii;
-    w = __fsub_rn(s, (float)ii);
-}
-
 // Frequency encoding (the models of Table 1 without grid levels): for a coordinate u of
 // the normalised position and band b, (sin(2^b pi u), cos(2^b pi u)); 2^b u is exact in FP32.
 __device__ __forceinline__ void niv_pe_pair(float u, int b, float& s, float& c) {
     sincospif(__fmul_rn(u, (float)(1 << b)), &s, &c);
-}
-
-// Entry index of vertex v at a level: dense row-major (x fastest) or spatial hash.
-template <int DIMS>
-__device__ __forceinline__ uint32_t niv_vertex_index(bool dense, uint32_t stride, const uint32_t* v,
-                                                     uint32_t mask, uint32_t prime_t) {
-    if (dense) {
-        uint32_t idx = v[DIMS - 1];
-#pragma unroll
-        for (int k = DIMS - 2; k >= 0; --k) idx = idx * stride + v[k];
-        return idx;
-    }
-    uint32_t h = v[0] * NIV_PI1 ^ v[1] * NIV_PI2 ^ v[2] * NIV_PI3;
-    if (DIMS == 4) h ^= v[3] * prime_t;
-    return h & mask;
 }
 
 // Multilinear weights of the 2^d corners from the per-axis fractions w1 (Sec. 4.1):
@@ -143,19 +132,29 @@ __device__ __forceinline__ void niv_level_weights(const float* w1, float* wc) {
 template <int DIMS, int ND = -1>
 __device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, const float* u, uint32_t* e, float* w1) {
     constexpr int NC = 1 << DIMS;
-    const float fN = g.res_f[l], fmax = g.resm1_f[l];
-    uint32_t ci[DIMS];
+    const float fN = g.res_f[l];
+    uint32_t ci[DIMS];  // the cell (NIV_MAGIC_FLOOR: plus the 2^23 bias, removed in the index terms)
+    constexpr uint32_t kB = NIV_MAGIC_FLOOR ? kNivBias : 0u;
 #pragma unroll
     for (int d = 0; d < DIMS; ++d) {
         const float s = __fmul_rn(u[d], fN);
-        const float fl = fminf(floorf(s), fmax);
-        ci[d] = (uint32_t)(int)fl;
-        w1[d] = __fsub_rn(s, fl);
+        if (NIV_MAGIC_FLOOR) {
+            // 0 <= s <= N < 2^23: s + 2^23 rounded down is 2^23 + floor(s) exactly; clamped to
+            // 2^23 + N - 1, its bits are kNivBias + i and its value minus 2^23 is i (exact)
+            const float tb = fminf(__fadd_rd(s, 8388608.0f), g.resm1_b[l]);
+            ci[d] = __float_as_uint(tb);
+            w1[d] = __fsub_rn(s, __fsub_rn(tb, 8388608.0f));
+        } else {
+            const float fl = fminf(floorf(s), g.resm1_f[l]);
+            ci[d] = (uint32_t)(int)fl;
+            w1[d] = __fsub_rn(s, fl);
+        }
     }
     if (ND >= 0 ? l < ND : ((g.dense_mask >> l) & 1u) != 0u) {
         const uint32_t S = g.stride1[l], S2 = g.stride2[l];
         uint32_t base = ci[2] * S2 + ci[1] * S + ci[0];
         if (DIMS == 4) base += ci[DIMS - 1] * S2 * S;
+        if (NIV_MAGIC_FLOOR) base += g.dense_off[l];
         uint32_t oh[NC / 2];
         oh[0] = base;
         oh[1] = base + S;
@@ -171,22 +170,23 @@ __device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, cons
             e[2 * q + 1] = oh[q] + 1u;
         }
     } else {
-        const uint32_t hy0 = ci[1] * NIV_PI2, hy1 = hy0 + NIV_PI2;
-        const uint32_t hz0 = ci[2] * NIV_PI3, hz1 = hz0 + NIV_PI3;
+        const uint32_t hy0 = ci[1] * NIV_PI2 + (0u - kB * NIV_PI2), hy1 = hy0 + NIV_PI2;
+        const uint32_t hz0 = ci[2] * NIV_PI3 + (0u - kB * NIV_PI3), hz1 = hz0 + NIV_PI3;
         uint32_t hh[NC / 2];
         hh[0] = hy0 ^ hz0;
         hh[1] = hy1 ^ hz0;
         hh[2] = hy0 ^ hz1;
         hh[3] = hy1 ^ hz1;
         if (DIMS == 4) {
-            const uint32_t ht0 = ci[DIMS - 1] * g.prime_t, ht1 = ht0 + g.prime_t;
+            const uint32_t ht0 = ci[DIMS - 1] * g.prime_t + (NIV_MAGIC_FLOOR ? g.prime_t_off : 0u),
+                           ht1 = ht0 + g.prime_t;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 hh[(q + 4) % (NC / 2)] = hh[q] ^ ht1;
                 hh[q] = hh[q] ^ ht0;
             }
         }
-        const uint32_t x0 = ci[0], x1 = ci[0] + 1u, m = g.hash_mask;
+        const uint32_t x0 = ci[0] - kB, x1 = ci[0] + (1u - kB), m = g.hash_mask;
 #pragma unroll
         for (int q = 0; q < NC / 2; ++q) {
             e[2 * q] = (x0 ^ hh[q]) & m;
