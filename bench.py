@@ -39,8 +39,8 @@ WORKLOAD = ("config1-1080p: seeded 10 m room (24 spheres, 8 boxes, sphere emitte
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="niv", choices=["niv", "reference"])
     ap.add_argument("--precision", default="fp16", choices=["fp32", "fp16", "fp8"])
     ap.add_argument("--res", default="1080p", choices=["1080p", "4k"])
@@ -453,11 +453,11 @@ def run_sweep(a):
     ray-traced visibility; MSE on 2^14 held-out samples with 4096-spp references."""
     import torch
     from paper_2602_12949_gb300 import fitting
-    from niv_inputs import room_scene
+    from niv_inputs import init_params, room_scene
     from niv_inputs.configs import MODEL_C1
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
-    rows = fitting.memory_error_sweep(room_scene(0), [13, 15, 17, 19], MODEL_C1, steps=2000)
+    rows = fitting.memory_error_sweep(room_scene(0), [13, 15, 17, 19], MODEL_C1, init_params, steps=2000)
     ref = next(r for r in rows if r["log2_T"] == 17)
     line = {"metric": "held-out MSE, NIV vs SH probes of equal memory (hash table size sweep)",
             "value": ref["probe_mse"] / ref["niv_mse"], "unit": "x (probe MSE / NIV MSE at T=2^17)",
@@ -521,7 +521,7 @@ def run_time(a):
     time on the 4K room frame."""
     import torch
     from paper_2602_12949_gb300 import fitting
-    from niv_inputs import room_scene
+    from niv_inputs import init_params, room_scene
     from niv_inputs.configs import MODEL_C3, room_gbuffer
     torch.cuda.set_device(0)
     pos, nrm, _ = room_gbuffer(3840, 2160)
@@ -529,7 +529,7 @@ def run_time(a):
     sec6 = dict(dims=3, levels=16, feat=2, log2_T=18, base=16.0, growth=1.38, n_hidden=3, width=64)
     shapes = {"4d_grid_config3": MODEL_C3, "3d_grid_t_bands4_sec6": dict(sec6, t_bands=4), "static_3d_no_t": sec6}
     t0 = time.perf_counter()
-    rows = fitting.time_field_comparison(room_scene(0), shapes, steps=2000, frame=frame)
+    rows = fitting.time_field_comparison(room_scene(0), shapes, init_params, steps=2000, frame=frame)
     by = {r["model"]: r for r in rows}
     line = {"metric": "held-out MSE of time-varying fields (config 3's 4-D grid vs Sec. 6's encoded t)",
             "value": by["4d_grid_config3"]["mse"] / by["3d_grid_t_bands4_sec6"]["mse"],
@@ -548,16 +548,14 @@ def run_train(a):
     samples, and the time the whole schedule (5,000 steps, 2^20-sample pools at 1024 spp,
     one pool per 4 steps) takes at these rates."""
     import torch
-    from paper_2602_12949_gb300 import NIVModel, mc_irradiance, sync_status
+    from paper_2602_12949_gb300 import NIVModel, mc_irradiance, sync_status, training_samples
     from niv_inputs import init_params, room_scene
     from niv_inputs.configs import MODEL_C1, ROOM_MIN, ROOM_MAX
-    from niv_inputs.samples import training_pool
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     scene = room_scene(0)
     batch = 1 << 18
-    x4, n4, _ = training_pool(scene, batch, seed=5)
-    dx, dn = torch.from_numpy(x4).to(dev), torch.from_numpy(n4).to(dev)
+    dx, dn, _, _ = training_samples(scene.blob(), batch, seed=5, device=dev)
     y = torch.rand((batch, 4), device=dev) * 2.0 + 0.1
     m = NIVModel(**MODEL_C1)
     g, nm = m.param_count()
@@ -580,8 +578,7 @@ def run_train(a):
         step[fwd] = s0.elapsed_time(e0) / a.steps
     step_ms = step["fp16"]  # config 2: FP16 forward, FP32 master weights
     mc_n, spp = 1 << 16, 1024
-    mx, mn, _ = training_pool(scene, mc_n, seed=6)
-    mxd, mnd = torch.from_numpy(mx).to(dev), torch.from_numpy(mn).to(dev)
+    mxd, mnd, _, _ = training_samples(scene.blob(), mc_n, seed=6, device=dev)
     mc_irradiance(scene.blob(), mxd, mnd, 16, seed=1, mode="indirect")
     torch.cuda.synchronize()
     s0.record(stream)
@@ -764,11 +761,11 @@ def main():
     if not a.no_compare:
         out32 = torch.empty((npx, 4), dtype=torch.float32, device=dev)
         ms32 = timed("fp32", out32, max(5, a.steps // 2), 3)
-        extra["fp32_plain"] = {"ms_per_frame": statistics.mean(ms32),
-                               "gqueries_per_s": npx / (statistics.mean(ms32) * 1e-3) / 1e9}
+        extra["fp32_plain"] = {"ms_per_frame": statistics.median(ms32),
+                               "gqueries_per_s": npx / (statistics.median(ms32) * 1e-3) / 1e9}
         ffma = _extra_peaks().get("fp32_ffma_tflops")
-        if ffma:  # the plain path's network on the FP32 FMA pipes (SURVEY's FP32-plain bound)
-            ach = FLOP_PER_QUERY["c1"] * npx / (statistics.mean(ms32) * 1e-3) / 1e12
+        if ffma:  # the plain path runs its network on the FP32 FMA pipes: its bound is the FFMA rate
+            ach = FLOP_PER_QUERY["c1"] * npx / (statistics.median(ms32) * 1e-3) / 1e12
             extra["fp32_plain"]["roofline"] = {"bound": "ffma", "achieved": ach, "peak": ffma, "unit": "TFLOP/s",
                                                "frac": ach / ffma,
                                                "peak_source": "measured (profiles/measured_peaks_gb300.md)"}
@@ -783,16 +780,17 @@ def main():
     for _ in range(2):
         model.query_host(hp, hn, out=ho, precision=a.precision, **qkw)
     e2e_t = []
-    for _ in range(max(3, min(a.steps, 10))):
+    for _ in range(max(3, a.steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         model.query_host(hp, hn, out=ho, precision=a.precision, **qkw)
         e2e_t.append(time.perf_counter() - t0)
-    ms_total, e2e_total = reduce_max([sum(ms), sum(e2e_t)], ws, dev)
-    ms_step = ms_total / a.steps
+    # per-step figures: the median over the timed steps (mean beside it), max over ranks
+    ms_med, e2e_med, ms_total = reduce_max([statistics.median(ms), statistics.median(e2e_t), sum(ms)], ws, dev)
+    ms_step = ms_med
     value = weak_throughput(npx, ws, ms_step * 1e-3)
-    e2e_val = weak_throughput(npx, ws, e2e_total / len(e2e_t))
+    e2e_val = weak_throughput(npx, ws, e2e_med)
 
     if rank != 0:
         if ws > 1:
@@ -800,7 +798,7 @@ def main():
         return
 
     peaks = _peaks()
-    mean_ms = statistics.mean(ms)
+    mean_ms = ms_med  # the roofline and the records below use the median step
     flop = FLOP_PER_QUERY["c1"] * npx
     achieved = flop / (mean_ms * 1e-3) / 1e12
     prof = _profiled_record() if (a.precision == "fp16" and a.res == "1080p") else None
@@ -856,7 +854,9 @@ def main():
 
     line = {
         "metric": METRIC, "value": value, "unit": "Gqueries/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": ms_step, "ms_per_frame": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": ms_step, "ms_per_frame": mean_ms, "ms_per_step_mean": ms_total / a.steps,
+        "timing": "CUDA events per step on the launching stream; median of the timed steps",
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "fp8": "e4m3"}[a.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("1920x1080", "%dx%d" % (w, h)), "pixels": npx,
@@ -865,7 +865,8 @@ def main():
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "Gqueries/s", "h2d_bytes_per_step": int(2 * hp.nbytes),
-                "d2h_bytes_per_step": int(ho.nbytes), "ms_per_frame": 1e3 * e2e_total / len(e2e_t),
+                "d2h_bytes_per_step": int(ho.nbytes), "ms_per_frame": 1e3 * e2e_med,
+                "calls": len(e2e_t), "statistic": "median wall-clock time of the calls",
                 "path": "niv_query_host on page-locked buffers: the query kernel reads pos/nrm from host memory "
                         "and writes E to it over NVLink-C2C; L2 flushed before each call"},
         "clocks": clk.summary(),
