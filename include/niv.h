@@ -201,7 +201,7 @@ NIV_API int niv_query(niv_handle h, const void* pos, const void* nrm, int64_t n,
  *    out_E directly (over NVLink-C2C on Grace systems), with no staging copies.
  *  - Other memory: pos/nrm are copied to a handle-owned device staging area and E
  *    back.  Calls of more than 131072 records are split into up to 32 chunks of whole
- *    128-record tiles (whole 8-row bands of the image when image_width > 0), about
+ *    128-record tiles (whole bands of 4-row tiles of the image when image_width > 0), about
  *    two waves of the FP16 kernel each, whose host-to-device copy, query and
  *    device-to-host copy run on three streams at once (two copy streams owned by the
  *    handle, ordered after the work already queued on `stream`).

@@ -124,23 +124,17 @@ __device__ __forceinline__ void niv_level_weights(const float* w1, float* wc) {
     }
 }
 
-// Corner entries of level l at normalised coordinate u and the per-axis fractions w1
-// (Sec. 4.1), with the per-corner work factored: one cell per axis, per-axis index terms
-// (dense strides or hash products) combined per corner.  Corner c has offset bit d along
-// dimension d.  ND >= 0: the dense levels are exactly levels 0 .. ND-1, known at compile
-// time (with the level unrolled, the dense / hashed choice then costs no branch).
-template <int DIMS, int ND = -1>
-__device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, const float* u, uint32_t* e, float* w1) {
-    constexpr int NC = 1 << DIMS;
+// The cell of level l at normalised coordinate u (Sec. 4.1): per axis s = fp32(u N),
+// i = min(floor(s), N - 1) and the fraction w1 = s - i (exact).  NIV_MAGIC_FLOOR: floor(s)
+// from s + 2^23 rounded down (0 <= s <= N < 2^23 makes that 2^23 + floor(s) exactly), i kept
+// with the bias kNivBias in its bits; the index terms below remove it.
+template <int DIMS>
+__device__ __forceinline__ void niv_level_cell(const GridArgs& g, int l, const float* u, uint32_t* ci, float* w1) {
     const float fN = g.res_f[l];
-    uint32_t ci[DIMS];  // the cell (NIV_MAGIC_FLOOR: plus the 2^23 bias, removed in the index terms)
-    constexpr uint32_t kB = NIV_MAGIC_FLOOR ? kNivBias : 0u;
 #pragma unroll
     for (int d = 0; d < DIMS; ++d) {
         const float s = __fmul_rn(u[d], fN);
         if (NIV_MAGIC_FLOOR) {
-            // 0 <= s <= N < 2^23: s + 2^23 rounded down is 2^23 + floor(s) exactly; clamped to
-            // 2^23 + N - 1, its bits are kNivBias + i and its value minus 2^23 is i (exact)
             const float tb = fminf(__fadd_rd(s, 8388608.0f), g.resm1_b[l]);
             ci[d] = __float_as_uint(tb);
             w1[d] = __fsub_rn(s, __fsub_rn(tb, 8388608.0f));
@@ -150,6 +144,16 @@ __device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, cons
             w1[d] = __fsub_rn(s, fl);
         }
     }
+}
+
+// Corner entries of level l for the cell ci, with the per-corner work factored: per-axis index
+// terms (dense strides or hash products) combined per corner.  Corner c has offset bit d along
+// dimension d.  ND >= 0: the dense levels are exactly levels 0 .. ND-1, known at compile time
+// (with the level unrolled, the dense / hashed choice then costs no branch).
+template <int DIMS, int ND = -1>
+__device__ __forceinline__ void niv_level_index(const GridArgs& g, int l, const uint32_t* ci, uint32_t* e) {
+    constexpr int NC = 1 << DIMS;
+    constexpr uint32_t kB = NIV_MAGIC_FLOOR ? kNivBias : 0u;
     if (ND >= 0 ? l < ND : ((g.dense_mask >> l) & 1u) != 0u) {
         const uint32_t S = g.stride1[l], S2 = g.stride2[l];
         uint32_t base = ci[2] * S2 + ci[1] * S + ci[0];
@@ -193,6 +197,14 @@ __device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, cons
             e[2 * q + 1] = (x1 ^ hh[q]) & m;
         }
     }
+}
+
+// Corner entries of level l at normalised coordinate u and the per-axis fractions w1 (Sec. 4.1).
+template <int DIMS, int ND = -1>
+__device__ __forceinline__ void niv_level_entries(const GridArgs& g, int l, const float* u, uint32_t* e, float* w1) {
+    uint32_t ci[DIMS];
+    niv_level_cell<DIMS>(g, l, u, ci, w1);
+    niv_level_index<DIMS, ND>(g, l, ci, e);
 }
 
 // Corner entries and multilinear weights of level l at normalised coordinate u.
@@ -247,14 +259,72 @@ __device__ __forceinline__ void niv_unpack(float4 r, float* f) {
 #endif
 // Two FP16 features per entry: both features of a corner in one packed FP32 FMA, each
 // lane the scalar FMA of its feature in the same corner order.
+#ifndef NIV_BLEND_SPLIT
+#define NIV_BLEND_SPLIT 0
+#endif
 template <int NC>
 __device__ __forceinline__ void niv_level_blend2(const uint32_t* raw, const float* wc, float* acc) {
+    if (NIV_BLEND_SPLIT) {  // even and odd corners in two chains, added at the end (half the depth)
+        float2 a = make_float2(0.0f, 0.0f), b = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < NC; c += 2) {
+            a = __ffma2_rn(make_float2(wc[c], wc[c]), __half22float2(*reinterpret_cast<const __half2*>(&raw[c])), a);
+            b = __ffma2_rn(make_float2(wc[c + 1], wc[c + 1]),
+                           __half22float2(*reinterpret_cast<const __half2*>(&raw[c + 1])), b);
+        }
+        a = __fadd2_rn(a, b);
+        acc[0] = a.x;
+        acc[1] = a.y;
+        return;
+    }
     float2 a = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
         a = __ffma2_rn(make_float2(wc[c], wc[c]), __half22float2(*reinterpret_cast<const __half2*>(&raw[c])), a);
     acc[0] = a.x;
     acc[1] = a.y;
+}
+
+#ifndef NIV_BLEND_LERP
+#define NIV_BLEND_LERP 0
+#endif
+// Two FP16 features per entry, multilinear interpolation as nested lerps a + w (b - a) from the
+// per-axis fractions w1 (the same interpolant as the corner-weight form, rounded differently):
+// along x per corner pair (b - a from the FP16 value of b and the FP32 value of a in one mixed-
+// precision add), then along y, z (and t), both features at once on the packed FP32 pipe.
+__device__ __forceinline__ float niv_h2f(uint16_t h) {
+    float f;
+    asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));
+    return f;
+}
+__device__ __forceinline__ float niv_h_minus(uint16_t b, float a) {  // fp32(b) - a, one rounding
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(b), "f"(-a));
+    return d;
+}
+template <int DIMS>
+__device__ __forceinline__ void niv_level_lerp2(const uint32_t* raw, const float* w1, float* acc) {
+    constexpr int NC = 1 << DIMS;
+    float2 v[NC / 2];
+#pragma unroll
+    for (int q = 0; q < NC / 2; ++q) {
+        const uint32_t a = raw[2 * q], b = raw[2 * q + 1];
+        const float a0 = niv_h2f((uint16_t)(a & 0xFFFFu)), a1 = niv_h2f((uint16_t)(a >> 16));
+        const float2 d = make_float2(niv_h_minus((uint16_t)(b & 0xFFFFu), a0), niv_h_minus((uint16_t)(b >> 16), a1));
+        v[q] = __ffma2_rn(make_float2(w1[0], w1[0]), d, make_float2(a0, a1));
+    }
+#pragma unroll
+    for (int d = 1; d < DIMS; ++d) {
+        const int half = NC >> (d + 1);  // pairs along dimension d: entries q and q + ... (bit d-1 of q)
+        const float2 wd = make_float2(w1[d], w1[d]);
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            const float2 lo = v[2 * q], hi = v[2 * q + 1];
+            v[q] = __ffma2_rn(wd, __fadd2_rn(hi, make_float2(-lo.x, -lo.y)), lo);
+        }
+    }
+    acc[0] = v[0].x;
+    acc[1] = v[0].y;
 }
 
 template <int NC, int F, typename R>
@@ -274,6 +344,101 @@ __device__ __forceinline__ void niv_level_blend(const R* raw, const float* wc, f
     }
 }
 
+// Interpolated features of level l from an FP16 table, as the fused query kernels take them:
+// two features per entry in the nested-lerp form (NIV_BLEND_LERP), else corner weights.
+// 0: off; 1: every model with two features per entry; 2: the 4-D models only (measured: 1%
+// faster on config 3's 4-D grid, 2-5% slower on the 3-D config-1 grid)
+#ifndef NIV_DENSE_PAIRS
+#define NIV_DENSE_PAIRS 2
+#endif
+#ifndef NIV_WARP_COOP
+#define NIV_WARP_COOP 0  // levels 0 .. NIV_WARP_COOP-1 try the warp-cooperative gather
+#endif
+// pair (optional, two FP16 features per entry, dense levels 0 .. ND-1 known at compile time):
+// entry e of a dense level holds the words of entries e and e + 1, the two corners of a cell
+// edge along x, so one 8-byte load serves both.
+template <int DIMS, int F, int ND = -1>
+__device__ __forceinline__ void niv_level_features16(const GridArgs& g, const __half* __restrict__ tab, int l,
+                                                     const float* u, float* acc, const uint2* __restrict__ pair = nullptr) {
+    constexpr int NC = 1 << DIMS;
+    using R = typename NivRaw<F, __half>::T;
+    uint32_t e[NC];
+    R raw[NC];
+    if constexpr (NIV_WARP_COOP > 0 && F == 2 && ND >= 0) {
+        // Levels coarser than the warp's 8 x 4 pixel block: when all 32 queries of the warp lie
+        // in one cell, lane j fetches corner j mod 2^d once and the corners reach every lane by
+        // warp shuffles (8 or 16 shuffles in place of the per-lane index work and gathers).
+        if (l < NIV_WARP_COOP) {
+            float w1[DIMS];
+            uint32_t ci[DIMS];
+            niv_level_cell<DIMS>(g, l, u, ci, w1);
+            constexpr uint32_t kB = NIV_MAGIC_FLOOR ? kNivBias : 0u;
+            const uint32_t key = (ci[0] - kB) | ((ci[1] - kB) << 11) | ((ci[2] - kB) << 22);
+            if (__all_sync(0xFFFFFFFFu, key == __shfl_sync(0xFFFFFFFFu, key, 0))) {
+                const int c = (int)(threadIdx.x & (NC - 1));
+                uint32_t v[DIMS];
+#pragma unroll
+                for (int d = 0; d < DIMS; ++d) v[d] = ci[d] - kB + ((c >> d) & 1);
+                uint32_t idx;
+                if (l < ND) {
+                    const uint32_t S = g.stride1[l], S2 = g.stride2[l];
+                    idx = v[2] * S2 + v[1] * S + v[0];
+                    if (DIMS == 4) idx += v[DIMS - 1] * S2 * S;
+                } else {
+                    idx = v[0] ^ (v[1] * NIV_PI2) ^ (v[2] * NIV_PI3);
+                    if (DIMS == 4) idx ^= v[DIMS - 1] * g.prime_t;
+                    idx &= g.hash_mask;
+                }
+                const uint32_t mine = __ldg(reinterpret_cast<const uint32_t*>(tab) + idx);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) raw[k] = __shfl_sync(0xFFFFFFFFu, mine, k);
+                float wc[NC];
+                niv_level_weights<DIMS>(w1, wc);
+                niv_level_blend<NC, F>(raw, wc, acc);
+                return;
+            }
+            niv_level_index<DIMS, ND>(g, l, ci, e);
+            niv_level_gather<NC, F, __half>(tab, e, raw);
+            float wc[NC];
+            niv_level_weights<DIMS>(w1, wc);
+            niv_level_blend<NC, F>(raw, wc, acc);
+            return;
+        }
+    }
+    if constexpr ((NIV_DENSE_PAIRS == 1 || (NIV_DENSE_PAIRS == 2 && DIMS == 4)) && F == 2 && ND > 0) {
+        if (pair != nullptr && l < ND) {
+            float w1[DIMS];
+            niv_level_entries<DIMS, ND>(g, l, u, e, w1);
+            const uint2* pt = pair + g.offset[l];
+#pragma unroll
+            for (int q = 0; q < NC / 2; ++q) {
+                const uint2 v = __ldg(pt + e[2 * q]);
+                raw[2 * q] = v.x;
+                raw[2 * q + 1] = v.y;
+            }
+            if constexpr (NIV_BLEND_LERP) {
+                niv_level_lerp2<DIMS>(raw, w1, acc);
+            } else {
+                float wc[NC];
+                niv_level_weights<DIMS>(w1, wc);
+                niv_level_blend<NC, F>(raw, wc, acc);
+            }
+            return;
+        }
+    }
+    if constexpr (NIV_BLEND_LERP && F == 2) {
+        float w1[DIMS];
+        niv_level_entries<DIMS, ND>(g, l, u, e, w1);
+        niv_level_gather<NC, F, __half>(tab, e, raw);
+        niv_level_lerp2<DIMS>(raw, w1, acc);
+    } else {
+        float wc[NC];
+        niv_level_corners<DIMS, ND>(g, l, u, e, wc);
+        niv_level_gather<NC, F, __half>(tab, e, raw);
+        niv_level_blend<NC, F>(raw, wc, acc);
+    }
+}
+
 // Interpolated features of level l (corners, gathers, blend).
 template <int DIMS, int F, typename TabT>
 __device__ __forceinline__ void niv_encode_level(const GridArgs& g, const TabT* __restrict__ grid, int l,
@@ -290,7 +455,7 @@ __device__ __forceinline__ void niv_encode_level(const GridArgs& g, const TabT* 
 // Image tiles: NIV_TILE_W x (128 / NIV_TILE_W) pixels, each warp of a tile an NIV_WARP_W x
 // (32 / NIV_WARP_W) block, the warps row-major in the tile.
 #ifndef NIV_TILE_W
-#define NIV_TILE_W 16
+#define NIV_TILE_W 32
 #endif
 #ifndef NIV_WARP_W
 #define NIV_WARP_W 8
@@ -412,3 +577,14 @@ __device__ __forceinline__ void niv_store_result(const IoArgs& io, int64_t i, fl
 
 // softplus(z) = max(z, 0) + log1p(exp(-|z|)) in FP32 with CUDA's libm functions.
 __device__ __forceinline__ float niv_softplus(float z) { return fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))); }
+
+// The same for the reduced-precision paths (FP16 / E4M3 networks): CUDA's fast exp and log
+// intrinsics, whose error (about 1e-7 absolute here, log(1 + x) near x = 0 included) lies far
+// below the 2^-11 relative resolution those paths keep.
+#ifndef NIV_FAST_SOFTPLUS
+#define NIV_FAST_SOFTPLUS 1
+#endif
+__device__ __forceinline__ float niv_softplus_lp(float z) {
+    if (!NIV_FAST_SOFTPLUS) return niv_softplus(z);
+    return fmaxf(z, 0.0f) + __logf(1.0f + __expf(-fabsf(z)));
+}

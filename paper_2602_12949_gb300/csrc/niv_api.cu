@@ -32,6 +32,13 @@ __global__ void f32_to_f16_kernel(const float* __restrict__ src, __half* __restr
         dst[i] = __float2half_rn(src[i]);
 }
 
+// Pair table of the dense levels: entry e = (word e, word e + 1) of the FP16 grid (two features
+// per word); the last entry's second word is 0.
+__global__ void pair_table_kernel(const uint32_t* __restrict__ words, uint2* __restrict__ pair, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pair[i] = make_uint2(words[i], i + 1 < n ? words[i + 1] : 0u);
+}
+
 int validate_desc(const niv_model_desc* d) {
     if (!d) return niv_fail(NIV_ERR_ARG, "desc is NULL");
     if (d->dims != 3 && d->dims != 4) return niv_fail(NIV_ERR_ARG, "dims must be 3 or 4");
@@ -74,6 +81,13 @@ int convert_grid_f16(niv_model* m, cudaStream_t s) {
     if (blocks > 4096) blocks = 4096;
     f32_to_f16_kernel<<<(unsigned)blocks, 256, 0, s>>>(m->params, m->grid_f16, n);
     NIV_CUDA(cudaGetLastError());
+    if (m->grid_pair16) {
+        int64_t pb = (m->n_pair + 255) / 256;
+        if (pb > 4096) pb = 4096;
+        pair_table_kernel<<<(unsigned)pb, 256, 0, s>>>(reinterpret_cast<const uint32_t*>(m->grid_f16), m->grid_pair16,
+                                                      m->n_pair);
+        NIV_CUDA(cudaGetLastError());
+    }
     return NIV_OK;
 }
 
@@ -81,6 +95,7 @@ void free_model(niv_model* m) {
     if (!m) return;
     cudaFree(m->params);
     cudaFree(m->grid_f16);
+    cudaFree(m->grid_pair16);
     cudaFree(m->mlp_plain);
     cudaFree(m->mlp_tc);
     cudaFree(m->mlp_f8);
@@ -278,6 +293,16 @@ int niv_create(const niv_model_desc* desc, niv_handle* out) {
     if (e == cudaSuccess) e = cudaMemset(m->params, 0, sizeof(float) * (m->n_grid + m->n_mlp));
     if (e == cudaSuccess) e = cudaMemset(m->grid_f16, 0, sizeof(__half) * (m->n_grid > 0 ? m->n_grid : 1));
     if (e == cudaSuccess) e = cudaMemset(m->mlp_plain, 0, sizeof(float) * m->mlp_plain_len);
+    // pair table when the dense levels are the first ones and an entry is one 32-bit word
+    int nd = 0;
+    while (nd < desc->levels && m->dense[nd]) ++nd;
+    bool prefix = nd > 0 && desc->feat == 2 && (NIV_DENSE_PAIRS == 1 || (NIV_DENSE_PAIRS == 2 && desc->dims == 4));
+    for (int l = nd; l < desc->levels; ++l) prefix = prefix && !m->dense[l];
+    if (e == cudaSuccess && prefix) {
+        m->n_pair = nd < desc->levels ? m->offset[nd] : m->total_entries;
+        e = cudaMalloc(&m->grid_pair16, sizeof(uint2) * m->n_pair);
+        if (e == cudaSuccess) e = cudaMemset(m->grid_pair16, 0, sizeof(uint2) * m->n_pair);
+    }
     if (e != cudaSuccess) {
         free_model(m);
         return niv_cuda_fail(e, "niv_create allocation");
@@ -592,7 +617,7 @@ void* mapped_host(const void* p) {
 
 // Page-locked host buffers that the GPU can address are read and written by the query
 // kernel itself (over NVLink-C2C on Grace systems): one launch, no staging copies.  Other
-// host memory is split into chunks of whole tiles (whole 8-row bands of the image when
+// host memory is split into chunks of whole tiles (whole bands of tile rows of the image when
 // image_width > 0) that flow through three engines at once: the host->device copy of
 // chunk c+1, the query of chunk c and the device->host copy of chunk c-1 overlap, so a
 // call costs about the slowest of the three plus one chunk of each of the others.

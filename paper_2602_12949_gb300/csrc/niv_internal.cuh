@@ -32,6 +32,9 @@ struct niv_model {
     float* params;
     // Inference copies rebuilt by niv_set_params.
     __half* grid_f16;        // grid values in FP16
+    uint2* grid_pair16;      // dense levels (a prefix of the levels, two features): entry e holds the
+                             // FP16 words of entries e and e + 1 (nullptr for other models)
+    int64_t n_pair;          // entries of grid_pair16
     float* mlp_plain;        // network packed for the plain FP32 kernel
     int64_t mlp_plain_len;
     uint8_t* mlp_tc;         // network packed for the tensor-core kernels (FP16 tiles)

@@ -112,20 +112,16 @@ __device__ __forceinline__ void issue_layer8(uint32_t tmem, uint32_t act, uint32
 // converted as soon as it is blended.
 template <int DIMS, int F, int ND = -1>
 __device__ __forceinline__ void encode_chunk8(const GridArgs& g, const __half* __restrict__ grid16, int l0, int L,
-                                              const float* u, float q0, uint4& hi, uint4& lo) {
+                                              const float* u, float q0, uint4& hi, uint4& lo,
+                                              const uint2* __restrict__ pair = nullptr) {
     constexpr int NC = 1 << DIMS, G = 16 / F;
     using R = typename NivRaw<F, __half>::T;
     uint32_t wd[4] = {0u, 0u, 0u, 0u}, wl[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int q = 0; q < G; ++q) {
         if (l0 + q >= L) continue;
-        uint32_t e[NC];
-        float wc[NC];
-        R raw[NC];
-        niv_level_corners<DIMS, ND>(g, l0 + q, u, e, wc);
-        niv_level_gather<NC, F, __half>(grid16 + (size_t)g.offset[l0 + q] * F, e, raw);
         float acc[F];
-        niv_level_blend<NC, F>(raw, wc, acc);
+        niv_level_features16<DIMS, F, ND>(g, grid16 + (size_t)g.offset[l0 + q] * F, l0 + q, u, acc, pair);
         if (F == 1) {
             const uint32_t p = e4m3_pair2<false>(acc[0] * q0, 0.0f);
             wd[q >> 2] |= (p & 0xFFu) << (8 * (q & 3));
@@ -165,7 +161,8 @@ template <int DIMS, int F, int LV, int WT = 0, int KT = 0, int NHT = 0, int ND =
 __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArgs io, const __half* __restrict__ grid16,
                                                                 const uint8_t* __restrict__ packed, F8Layout lay,
                                                                 int out_act, int64_t n_tiles, uint32_t tmem_cols,
-                                                                int* __restrict__ status) {
+                                                                int* __restrict__ status,
+                                                                const uint2* __restrict__ pair) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);  // one per warpgroup
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + 64);
@@ -228,7 +225,7 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
 #pragma unroll
             for (int l0 = 0; l0 < LV; l0 += G) {
                 uint4 hi, lo;
-                encode_chunk8<DIMS, F, ND>(g, grid16, l0, LV, u, q0, hi, lo);
+                encode_chunk8<DIMS, F, ND>(g, grid16, l0, LV, u, q0, hi, lo, pair);
                 *reinterpret_cast<uint4*>(s_act + core_off8(tid, l0 * F, K2)) = hi;
                 *reinterpret_cast<uint4*>(s_act + core_off8(tid, K1 + l0 * F, K2)) = lo;
             }
@@ -315,9 +312,9 @@ __global__ void __launch_bounds__(kT * kWG, 1) query_f8_kernel(GridArgs g, IoArg
         const float* bo = s_b + nh * W;
         float z0 = fmaf(zz[0], c, bo[0]), z1 = fmaf(zz[1], c, bo[1]), z2 = fmaf(zz[2], c, bo[2]);
         if (out_act == 1) {
-            z0 = niv_softplus(z0);
-            z1 = niv_softplus(z1);
-            z2 = niv_softplus(z2);
+            z0 = niv_softplus_lp(z0);
+            z1 = niv_softplus_lp(z1);
+            z2 = niv_softplus_lp(z2);
         }
         if (valid) niv_store_result(io, r, z0, z1, z2);
         tc::fence_before_sync();
@@ -366,7 +363,7 @@ int launch8(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_
     const int64_t need = (tiles + kWG - 1) / kWG;
     const int64_t blocks = need < (int64_t)sms * per_sm ? need : (int64_t)sms * per_sm;
     kern<<<(unsigned)blocks, kT * kWG, smem, s>>>(g, io, m->grid_f16, m->mlp_f8, *lay, m->d.out_act, tiles, cols,
-                                                  status);
+                                                  status, m->grid_pair16);
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }

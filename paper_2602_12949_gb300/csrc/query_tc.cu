@@ -1,6 +1,6 @@
 // Fused query path on the 5th-generation tensor cores (sm_103a).
 //
-// A warpgroup (128 threads) owns a tile of 128 G-buffer records at a time (a 16 x 8
+// A warpgroup (128 threads) owns a tile of 128 G-buffer records at a time (a 32 x 4
 // pixel block for images) and walks tiles persistently.  Per tile:
 //   1. every thread encodes its own record (Sec. 4.1: per level the cell, the
 //      2^d corner entries -- dense or hashed --, FP16 feature gathers served from
@@ -151,10 +151,28 @@ __device__ __forceinline__ void encode_pe(const GridArgs& g, const float* u, uin
 // kILP levels' gathers in flight at a time.
 template <int DIMS, int F, typename TabT, int ND = -1>
 __device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const TabT* __restrict__ grid, int l0, int L,
-                                              const float* u) {
+                                              const float* u, const uint2* __restrict__ pair = nullptr) {
     constexpr int NC = 1 << DIMS, G = 8 / F;
     using R = typename NivRaw<F, TabT>::T;
     uint32_t wd[4] = {0u, 0u, 0u, 0u};
+    if constexpr (kILP == 1 && std::is_same<TabT, __half>::value) {
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            if (l0 + q >= L) continue;
+            float acc[F];
+            niv_level_features16<DIMS, F, ND>(g, grid + (size_t)g.offset[l0 + q] * F, l0 + q, u, acc, pair);
+            if (F == 1) {
+                const uint32_t v = (uint32_t)__half_as_ushort(__float2half_rn(acc[0]));
+                wd[q >> 1] |= (q & 1) ? (v << 16) : v;
+            } else if (F == 2) {
+                wd[q % 4] = pack_half2(acc[0], acc[1 % F]);
+            } else {
+                wd[(2 * q) % 4] = pack_half2(acc[0], acc[1 % F]);
+                wd[(2 * q + 1) % 4] = pack_half2(acc[2 % F], acc[3 % F]);
+            }
+        }
+        return make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
 #pragma unroll
     for (int q = 0; q < G; q += kILP) {
         const int la = l0 + q, lb = l0 + q + 1;
@@ -188,6 +206,37 @@ __device__ __forceinline__ uint4 encode_chunk(const GridArgs& g, const TabT* __r
 
 __device__ __forceinline__ void group_sync(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory"); }
 
+#ifndef NIV_TC_WAIT1
+#define NIV_TC_WAIT1 0
+#endif
+// OR of v over the warpgroup's 128 threads at its named barrier (all of them wait there).
+__device__ __forceinline__ bool group_any(int wg, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(1 + wg)
+        : "memory");
+    return r != 0;
+}
+
+// Wait for the warpgroup's MMA-completion barrier (phase `parity`), bounded.  NIV_TC_WAIT1: the
+// first warp polls the barrier while the other three wait at the named barrier, which takes no
+// issue slots; the outcome reaches all four warps through the barrier's OR.  Returns false when
+// the wait ran out.
+__device__ __forceinline__ bool group_wait_mma(uint32_t bar, uint32_t parity, int warp, int wg) {
+    if (!NIV_TC_WAIT1) return tc::mbar_wait_bounded(bar, parity, kWaitLimitNs);
+    bool fail = false;
+    if (warp == 0) {
+        fail = !tc::mbar_wait_bounded(bar, parity, kWaitLimitNs);
+        tc::fence_before_sync();
+    }
+    return !group_any(wg, fail);
+}
+
 
 // kWG independent warpgroups per CTA; each owns a 128-row tile pipeline (activation tile,
 // mbarrier, named barrier, 64 TMEM columns) and all share the weights in shared memory.
@@ -202,7 +251,8 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                                                                 const TabT* __restrict__ grid,
                                                                 const uint8_t* __restrict__ packed, TcLayout lay,
                                                                 int out_act, int64_t n_tiles, uint32_t tmem_cols,
-                                                                int* __restrict__ status) {
+                                                                int* __restrict__ status,
+                                                                const uint2* __restrict__ pair) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);  // one per warpgroup
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + 64);
@@ -262,7 +312,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         } else if constexpr (LV > 0) {
 #pragma unroll
             for (int l0 = 0; l0 < LV; l0 += G)
-                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F, TabT, ND>(g, grid, l0, LV, u);
+                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F, TabT, ND>(g, grid, l0, LV, u, pair);
         } else {
             for (int l0 = 0; l0 < L; l0 += G)
                 *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, L, u);
@@ -312,8 +362,8 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                 tc::fence_after_sync();
                 issue_layer(tmem, act_a, net_a + w_off, K, idesc_h, bar);
             }
-            if (!tc::mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
-                atomicExch(status, 1);
+            if (!group_wait_mma(bar, phase, warp, wg)) {
+                if (tid == 0) atomicExch(status, 1);
                 ok = false;
                 break;
             }
@@ -375,8 +425,8 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                 tc::fence_after_sync();
                 issue_layer(tmem, act_a, net_a + lay.wo, (uint32_t)W, idesc_o, bar);
             }
-            if (!tc::mbar_wait_bounded(bar, phase, kWaitLimitNs)) {
-                atomicExch(status, 1);
+            if (!group_wait_mma(bar, phase, warp, wg)) {
+                if (tid == 0) atomicExch(status, 1);
                 ok = false;
                 break;
             }
@@ -390,9 +440,9 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             z2 = z[2] + bo[2];
         }
         if (out_act == 1) {
-            z0 = niv_softplus(z0);
-            z1 = niv_softplus(z1);
-            z2 = niv_softplus(z2);
+            z0 = niv_softplus_lp(z0);
+            z1 = niv_softplus_lp(z1);
+            z2 = niv_softplus_lp(z2);
         }
         if (valid) niv_store_result(io, r, z0, z1, z2);
         tc::fence_before_sync();
@@ -477,7 +527,7 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
     const int64_t need = (tiles + kWG - 1) / kWG;
     const int64_t blocks = need < (int64_t)sms * per_sm ? need : (int64_t)sms * per_sm;
     kern<<<(unsigned)blocks, kT * kWG, smem, s>>>(g, io, grid, m->mlp_tc, *lay, m->d.out_act, tiles, cols,
-                                                 status);
+                                                 status, m->grid_pair16);
     NIV_CUDA(cudaGetLastError());
     return NIV_OK;
 }
