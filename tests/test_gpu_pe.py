@@ -81,8 +81,10 @@ def test_fp32_and_fp16_match_oracle(niv, spec, n):
     e16 = m.query(dp, dn, precision="fp16", out_dtype=torch.float32)[:, :3].cpu().numpy()
     fmt = rel_err(ref16_path, ref16)
     worst, agree = path_parity(e16, ref16_path)
-    print("fp32 %.2e  fp16 vs path: max %.2e agree %.4f  fp16 vs network %.2e  format %.2e"
-          % (rel_err(e32, ref), worst, agree, rel_err(e16, ref16), fmt))
+    print("PE %s n=%d: fp32 %.2e  fp16 vs FP16 path: max %.2e agree %.4f  fp16 vs FP64 network on FP16 "
+          "parameters %.2e, on the FP32 parameters %.2e  format alone %.2e"
+          % ("w%d b%d h%d" % (spec["width"], spec["pe_bands"], spec["n_hidden"]), n, rel_err(e32, ref), worst, agree,
+             rel_err(e16, ref16), rel_err(e16, ref), fmt))
     assert rel_err(e32, ref) <= FP32_BOUND
     assert worst <= FP16_PATH_NORM_BOUND and agree >= FP16_PATH_AGREE
     assert rel_err(e16, ref16) <= max(FP16_BOUND, 1.5 * fmt)
