@@ -40,8 +40,11 @@
 
 namespace {
 
+#ifndef NIV_TC_PPT
+#define NIV_TC_PPT 1  // records per thread: 2 gives each warpgroup two 128-row tiles at a time
+#endif
 #ifndef NIV_TC_WG
-#define NIV_TC_WG 8
+#define NIV_TC_WG (NIV_TC_PPT == 2 ? 4 : 8)
 #endif
 #ifndef NIV_TC_ILP
 #define NIV_TC_ILP 1
@@ -58,6 +61,7 @@ namespace {
 
 constexpr int kT = 128;          // rows per tile = threads per warpgroup
 constexpr int kWG = NIV_TC_WG;   // warpgroups (independent tile pipelines) per CTA
+constexpr int kP = NIV_TC_PPT;   // 128-row tiles a warpgroup carries at a time (records per thread)
 constexpr int kILP = NIV_TC_ILP; // levels whose gathers are in flight together (1 or 2)
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 #ifndef NIV_TC_OUT_FMA
@@ -103,13 +107,16 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
     for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Issue one layer: sum over K/16 steps of act x W^T into TMEM, then signal `bar`.
+// Issue one layer for each of the kP tiles: sum over K/16 steps of act x W^T into TMEM (tile p
+// reads act + p act_stride and accumulates at tmem + p tmem_stride), then signal `bar`.
 __device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t act, uint32_t w, uint32_t K, uint32_t idesc,
-                                            uint32_t bar) {
+                                            uint32_t bar, uint32_t act_stride = 0, uint32_t tmem_stride = 0) {
     const uint32_t sbo = (K >> 3) * 128u;
-    for (uint32_t ks = 0; ks < K / 16; ++ks)
-        tc::mma_f16(tmem, tc::smem_desc(act + ks * 256u, 128u, sbo), tc::smem_desc(w + ks * 256u, 128u, sbo), idesc,
-                    ks > 0 ? 1u : 0u);
+#pragma unroll
+    for (int p = 0; p < kP; ++p)
+        for (uint32_t ks = 0; ks < K / 16; ++ks)
+            tc::mma_f16(tmem + p * tmem_stride, tc::smem_desc(act + p * act_stride + ks * 256u, 128u, sbo),
+                        tc::smem_desc(w + ks * 256u, 128u, sbo), idesc, ks > 0 ? 1u : 0u);
     tc::mma_commit(bar);
 }
 
@@ -257,7 +264,9 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
     uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem);  // one per warpgroup
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + 64);
     uint8_t* s_net = smem + kHdr;
-    const uint32_t act_bytes = (uint32_t)kT * (uint32_t)(lay.K1 > lay.W ? lay.K1 : lay.W) * 2u;
+    static_assert(kP == 1 || !kOutFma, "two tiles per warpgroup take the output layer on the tensor core");
+    const uint32_t tile_bytes = (uint32_t)kT * (uint32_t)(lay.K1 > lay.W ? lay.K1 : lay.W) * 2u;  // one 128-row tile
+    const uint32_t act_bytes = tile_bytes * kP;
 
     const int wg = threadIdx.x / kT, tid = threadIdx.x % kT, warp = tid >> 5;
     uint8_t* s_act = s_net + ((lay.total + 127u) & ~127u) + wg * act_bytes;
@@ -280,8 +289,8 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
     __syncthreads();
     tc::fence_after_sync();
 
-    const uint32_t wg_cols = lay.W <= 32 ? 32u : 64u;  // accumulator columns of one warpgroup
-    const uint32_t tmem = *s_tmem + (uint32_t)wg * wg_cols;
+    const uint32_t wg_cols = lay.W <= 32 ? 32u : 64u;  // accumulator columns of one 128-row tile
+    const uint32_t tmem = *s_tmem + (uint32_t)wg * wg_cols * kP;
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     const uint32_t bar = tc::smem_u32(s_bar + wg);
     const uint32_t act_a = tc::smem_u32(s_act), net_a = tc::smem_u32(s_net);
@@ -293,38 +302,55 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
     uint32_t phase = 0;
     bool ok = true;
 
-    NivTileWalk walk;
-    walk.init((int64_t)blockIdx.x * kWG + wg, (int64_t)gridDim.x * kWG, tid, io.image_width);
-    for (; walk.tile < n_tiles && ok; walk.next()) {
-        const int64_t r = walk.record(tid, io.n, io.image_width);
-        const bool valid = r < io.n;
-        const int64_t rr = valid ? walk.source(r, io) : 0;
-        const float4 p = niv_load_rec(io.pos, rr, io.in_f16);
-        float u[4];
-        u[0] = niv_unit(p.x, g.aabb_min[0], g.inv_ext[0]);
-        u[1] = niv_unit(p.y, g.aabb_min[1], g.inv_ext[1]);
-        u[2] = niv_unit(p.z, g.aabb_min[2], g.inv_ext[2]);
-        u[3] = fminf(fmaxf(g.t, 0.0f), 1.0f);
+    // tile p of this warpgroup's pair is tile (first + p) of the walk; both walkers advance together
+    NivTileWalk walk[kP];
+#pragma unroll
+    for (int p = 0; p < kP; ++p)
+        walk[p].init(((int64_t)blockIdx.x * kWG + wg) * kP + p, (int64_t)gridDim.x * kWG * kP, tid, io.image_width);
+    for (; walk[0].tile < n_tiles && ok;) {
+        int64_t r[kP], rr[kP];
+        float u[kP][4];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+            r[p] = walk[p].record(tid, io.n, io.image_width);
+            rr[p] = r[p] < io.n ? walk[p].source(r[p], io) : 0;
+            const float4 pv = niv_load_rec(io.pos, rr[p], io.in_f16);
+            u[p][0] = niv_unit(pv.x, g.aabb_min[0], g.inv_ext[0]);
+            u[p][1] = niv_unit(pv.y, g.aabb_min[1], g.inv_ext[1]);
+            u[p][2] = niv_unit(pv.z, g.aabb_min[2], g.inv_ext[2]);
+            u[p][3] = fminf(fmaxf(g.t, 0.0f), 1.0f);
+        }
 
-        // ---- 1. encoding -> FP16 input row, one 16-byte chunk per G levels ----
+        // ---- 1. encoding -> FP16 input row, one 16-byte chunk per G levels (the kP records of
+        // this thread chunk by chunk, so that their independent work interleaves) ----
         if (PE != 0) {
-            encode_pe<PE>(g, u, s_act, tid, K1);
+#pragma unroll
+            for (int p = 0; p < kP; ++p) encode_pe<PE>(g, u[p], s_act + p * tile_bytes, tid, K1);
         } else if constexpr (LV > 0) {
 #pragma unroll
             for (int l0 = 0; l0 < LV; l0 += G)
-                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F, TabT, ND>(g, grid, l0, LV, u, pair);
+#pragma unroll
+                for (int p = 0; p < kP; ++p)
+                    *reinterpret_cast<uint4*>(s_act + p * tile_bytes + core_off(tid, l0 * F, K1)) =
+                        encode_chunk<DIMS, F, TabT, ND>(g, grid, l0, LV, u[p], pair);
         } else {
             for (int l0 = 0; l0 < L; l0 += G)
-                *reinterpret_cast<uint4*>(s_act + core_off(tid, l0 * F, K1)) = encode_chunk<DIMS, F>(g, grid, l0, L, u);
+#pragma unroll
+                for (int p = 0; p < kP; ++p)
+                    *reinterpret_cast<uint4*>(s_act + p * tile_bytes + core_off(tid, l0 * F, K1)) =
+                        encode_chunk<DIMS, F>(g, grid, l0, L, u[p]);
         }
-        const float4 nv = niv_load_rec(io.nrm, rr, io.in_f16);  // read late: not live during the encoding
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+        uint8_t* s_row = s_act + p * tile_bytes;
+        const float4 nv = niv_load_rec(io.nrm, rr[p], io.in_f16);  // read late: not live during the encoding
         int tail = 8;  // columns written from col_extra on
         if (g.t_bands == 0) {  // [n.x, n.y, n.z, (t), 1, 0, ...]: the 1 multiplies the first layer's bias column
             const bool has_t = g.n_in > (PE != 0 ? 0 : L * F) + 6 * g.pe_bands + 3;
             const uint32_t one = (uint32_t)__half_as_ushort(__float2half_rn(1.0f));
-            uint4 c = make_uint4(pack_half2(nv.x, nv.y), has_t ? pack_half2(nv.z, u[3]) : (pack_half2(nv.z, 0.0f) & 0xFFFFu) | (one << 16), 0u, 0u);
+            uint4 c = make_uint4(pack_half2(nv.x, nv.y), has_t ? pack_half2(nv.z, u[p][3]) : (pack_half2(nv.z, 0.0f) & 0xFFFFu) | (one << 16), 0u, 0u);
             if (has_t) c.z = one;
-            *reinterpret_cast<uint4*>(s_act + core_off(tid, col_extra, K1)) = c;
+            *reinterpret_cast<uint4*>(s_row + core_off(tid, col_extra, K1)) = c;
         } else {  // Sec. 6: [n.x, n.y, n.z, sin, cos of 2^b pi t (b < t_bands <= 6), 1, 0, ...]
             float v[16];
 #pragma unroll
@@ -334,21 +360,22 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             v[2] = nv.z;
 #pragma unroll
             for (int b = 0; b < 6; ++b)
-                if (b < g.t_bands) niv_pe_pair(u[3], b, v[3 + 2 * b], v[4 + 2 * b]);
+                if (b < g.t_bands) niv_pe_pair(u[p][3], b, v[3 + 2 * b], v[4 + 2 * b]);
 #pragma unroll
             for (int i = 3; i < 16; ++i)
                 if (i == 3 + 2 * g.t_bands) v[i] = 1.0f;
-            *reinterpret_cast<uint4*>(s_act + core_off(tid, col_extra, K1)) =
+            *reinterpret_cast<uint4*>(s_row + core_off(tid, col_extra, K1)) =
                 make_uint4(pack_half2(v[0], v[1]), pack_half2(v[2], v[3]), pack_half2(v[4], v[5]), pack_half2(v[6], v[7]));
             if (4 + 2 * g.t_bands > 8) {
-                *reinterpret_cast<uint4*>(s_act + core_off(tid, col_extra + 8, K1)) =
+                *reinterpret_cast<uint4*>(s_row + core_off(tid, col_extra + 8, K1)) =
                     make_uint4(pack_half2(v[8], v[9]), pack_half2(v[10], v[11]), pack_half2(v[12], v[13]),
                                pack_half2(v[14], v[15]));
                 tail = 16;
             }
         }
         for (int k = col_extra + tail; k < K1; k += 8)
-            *reinterpret_cast<uint4*>(s_act + core_off(tid, k, K1)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(s_row + core_off(tid, k, K1)) = make_uint4(0u, 0u, 0u, 0u);
+        }
         tc::fence_async_smem();
         tc::fence_before_sync();
         group_sync(wg);
@@ -360,7 +387,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         for (int layer = 0; layer < NH && ok; ++layer) {
             if (tid == 0) {
                 tc::fence_after_sync();
-                issue_layer(tmem, act_a, net_a + w_off, K, idesc_h, bar);
+                issue_layer(tmem, act_a, net_a + w_off, K, idesc_h, bar, tile_bytes, wg_cols);
             }
             if (!group_wait_mma(bar, phase, warp, wg)) {
                 if (tid == 0) atomicExch(status, 1);
@@ -377,9 +404,11 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                 z2 = s_bias[(NH - 1) * W + 2];
             }
 #pragma unroll
-            for (int c = 0; c < W / 16; ++c) {
+            for (int pc = 0; pc < kP * (W / 16); ++pc) {
+                const int p = pc / (W / 16), c = pc % (W / 16);
+                uint8_t* s_row = s_act + p * tile_bytes;
                 float v[16];
-                tc::tmem_ld16(tmem_row + (uint32_t)(c * 16), v);
+                tc::tmem_ld16(tmem_row + (uint32_t)(p * wg_cols + c * 16), v);
                 if (layer > 0) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {  // biases 16-byte aligned: one load per four
@@ -405,8 +434,8 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                     uint32_t h[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) h[j] = relu_pack_half2(v[2 * j], v[2 * j + 1]);
-                    *reinterpret_cast<uint4*>(s_act + core_off(tid, c * 16, W)) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4*>(s_act + core_off(tid, c * 16 + 8, W)) = make_uint4(h[4], h[5], h[6], h[7]);
+                    *reinterpret_cast<uint4*>(s_row + core_off(tid, c * 16, W)) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4*>(s_row + core_off(tid, c * 16 + 8, W)) = make_uint4(h[4], h[5], h[6], h[7]);
                 }
             }
             if (!(kOutFma && last)) {
@@ -423,7 +452,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         if (!kOutFma) {
             if (tid == 0) {
                 tc::fence_after_sync();
-                issue_layer(tmem, act_a, net_a + lay.wo, (uint32_t)W, idesc_o, bar);
+                issue_layer(tmem, act_a, net_a + lay.wo, (uint32_t)W, idesc_o, bar, tile_bytes, wg_cols);
             }
             if (!group_wait_mma(bar, phase, warp, wg)) {
                 if (tid == 0) atomicExch(status, 1);
@@ -432,21 +461,28 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             }
             phase ^= 1u;
             tc::fence_after_sync();
-            float z[4];
-            tmem_ld4(tmem_row, z);
-            const float* bo = s_bias + (NH - 1) * W;
-            z0 = z[0] + bo[0];
-            z1 = z[1] + bo[1];
-            z2 = z[2] + bo[2];
         }
-        if (out_act == 1) {
-            z0 = niv_softplus_lp(z0);
-            z1 = niv_softplus_lp(z1);
-            z2 = niv_softplus_lp(z2);
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+            if (!kOutFma) {
+                float z[4];
+                tmem_ld4(tmem_row + (uint32_t)(p * wg_cols), z);
+                const float* bo = s_bias + (NH - 1) * W;
+                z0 = z[0] + bo[0];
+                z1 = z[1] + bo[1];
+                z2 = z[2] + bo[2];
+            }
+            if (out_act == 1) {
+                z0 = niv_softplus_lp(z0);
+                z1 = niv_softplus_lp(z1);
+                z2 = niv_softplus_lp(z2);
+            }
+            if (r[p] < io.n) niv_store_result(io, r[p], z0, z1, z2);
         }
-        if (valid) niv_store_result(io, r, z0, z1, z2);
         tc::fence_before_sync();
         group_sync(wg);  // the next tile's encoder overwrites the activation tile
+#pragma unroll
+        for (int p = 0; p < kP; ++p) walk[p].next();
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -455,7 +491,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
 
 size_t tc_smem_bytes(const TcLayout& lay) {
     const int kmax = lay.K1 > lay.W ? lay.K1 : lay.W;
-    return (size_t)kHdr + ((lay.total + 127u) & ~127u) + (size_t)kWG * kT * kmax * 2;
+    return (size_t)kHdr + ((lay.total + 127u) & ~127u) + (size_t)kWG * kP * kT * kmax * 2;
 }
 
 template <int DIMS, int F, int LV, int PE = 0, int WT = 0, int KT = 0, int NHT = 0, int ND = -1>
@@ -497,7 +533,7 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
             per_sm = by_smem < by_regs ? by_smem : by_regs;
             // TMEM is allocated in powers of two from 32 to 512 columns: round the CTA's need up.
             cols = 32u;
-            while (cols < (lay->W <= 32 ? 32u : 64u) * (uint32_t)kWG) cols <<= 1;
+            while (cols < (lay->W <= 32 ? 32u : 64u) * (uint32_t)(kWG * kP)) cols <<= 1;
             if (cols > 512u) return niv_fail(NIV_ERR_UNSUPPORTED, "too many warpgroups for tensor memory");
             const int forced = niv_env_int("NIV_TC_BLOCKS_PER_SM", 0);
             if (forced > 0) per_sm = forced;
@@ -524,7 +560,7 @@ int launch(const niv_model* m, const GridArgs& g, const IoArgs& io, cudaStream_t
     if (!status) status = niv_status_word();
     if (!status) return niv_fail(NIV_ERR_CUDA, "status word unavailable");
     const int64_t tiles = niv_tile_count_host(io.n, io.image_width);
-    const int64_t need = (tiles + kWG - 1) / kWG;
+    const int64_t need = (tiles + kWG * kP - 1) / (kWG * kP);
     const int64_t blocks = need < (int64_t)sms * per_sm ? need : (int64_t)sms * per_sm;
     kern<<<(unsigned)blocks, kT * kWG, smem, s>>>(g, io, grid, m->mlp_tc, *lay, m->d.out_act, tiles, cols,
                                                  status, m->grid_pair16);
