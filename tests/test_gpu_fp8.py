@@ -109,16 +109,18 @@ def test_fp8_within_bar_of_fp64_oracle(niv, spec, kw):
     _check(E, params, om, o_sact, pos, nrm, kw, "random queries")
 
 
-@pytest.mark.parametrize("t", [0.0, 0.25, 0.6369616873214543, 1.0])
-def test_fp8_config3_model_on_room_frame(niv, t):
-    """The 4-D config-3 model on the full 1080p room G-buffer (image traversal) at several
-    values of the scene parameter; sampled pixels checked against both oracles."""
-    pos, nrm, _ = room_gbuffer(1920, 1080)
+@pytest.mark.parametrize("t,W,H", [(0.0, 1920, 1080), (0.25, 1920, 1080), (0.6369616873214543, 1920, 1080),
+                                   (1.0, 1920, 1080), (0.6369616873214543, 3840, 2160)])
+def test_fp8_config3_model_on_room_frame(niv, t, W, H):
+    """The 4-D config-3 model on the full room G-buffer (1080p, and 4K as in the benchmark; image
+    traversal) at several values of the scene parameter; sampled pixels checked against both
+    oracles."""
+    pos, nrm, _ = room_gbuffer(W, H)
     kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=t)
     cal = (pos[:: 31].copy(), nrm[:: 31].copy())  # calibration batch: every 31st pixel
-    E, params, om, o_sact = _run(niv, MODEL_C3, pos, nrm, kw, seed=0, cal=cal, image_width=1920)
+    E, params, om, o_sact = _run(niv, MODEL_C3, pos, nrm, kw, seed=0, cal=cal, image_width=W)
     pick = np.random.default_rng(3).choice(len(pos), 8192, replace=False)
-    _check(E[pick], params, om, o_sact, pos[pick], nrm[pick], kw, "config-3 frame, t=%g" % t)
+    _check(E[pick], params, om, o_sact, pos[pick], nrm[pick], kw, "config-3 %dx%d frame, t=%g" % (W, H, t))
 
 
 def test_fp8_requires_calibration(niv):

@@ -120,13 +120,15 @@ def test_fp16_other_shapes(niv, spec, kw):
     m.close()
 
 
-def test_fp16_full_frame_1080p_sampled(niv):
-    """Config 1 at full size in the benchmark's launch configuration, 8192 sampled pixels checked."""
-    pos, nrm, _ = room_gbuffer(1920, 1080)
+@pytest.mark.parametrize("W,H", [(1920, 1080), (3840, 2160)])
+def test_fp16_full_frame_sampled(niv, W, H):
+    """Config 1 at full size (1080p and 4K) in the benchmark's launch configuration, 8192 sampled
+    pixels checked."""
+    pos, nrm, _ = room_gbuffer(W, H)
     m, params, om = make(niv, MODEL_C1, seed=0)
     dp, dn = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
     kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)
-    E = m.query(dp, dn, precision="fp16", image_width=1920, **kw)
+    E = m.query(dp, dn, precision="fp16", image_width=W, **kw)
     E_lin = m.query(dp, dn, precision="fp16", **kw)
     assert torch.equal(E, E_lin)
     pick = np.random.default_rng(0).choice(len(pos), 8192, replace=False)
@@ -136,4 +138,19 @@ def test_fp16_full_frame_1080p_sampled(niv):
     # FP16 output records add one final rounding (2^-11 relative)
     assert rel_err(got, ref_q) <= FP16_BOUND + 2.0 ** -11
     assert torch.all(torch.isfinite(E))
+    m.close()
+
+
+def test_fp16_config3_4k_frame_sampled(niv):
+    """The 4-D config-3 model in FP16 on the full 4K room frame, as the benchmark runs it beside
+    the E4M3 form; 8192 sampled pixels checked."""
+    pos, nrm, _ = room_gbuffer(3840, 2160)
+    m, params, om = make(niv, MODEL_C3, seed=0)
+    dp, dn = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+    kw = dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=0.6369616873214543)
+    E = m.query(dp, dn, precision="fp16", image_width=3840, out_dtype=torch.float32, **kw)
+    pick = np.random.default_rng(1).choice(len(pos), 8192, replace=False)
+    ref_q = oracle.query(om, fp16_stored_params(params, om), pos[pick].astype(np.float32),
+                         nrm[pick].astype(np.float32), **kw)
+    assert rel_err(E[pick, :3].cpu().numpy(), ref_q) <= FP16_BOUND
     m.close()
