@@ -258,3 +258,64 @@ def test_fp16_query_before_parameters_are_set_is_refused(niv):
     niv.sync_status()
     np.testing.assert_allclose(E[:, :3].cpu().numpy(), np.log(2.0), rtol=1e-6)  # softplus(0)
     m.close()
+
+
+def _boundary_points(lo, hi, n_levels_res, seed=0):
+    """Positions on the box's faces and corners, outside it (clamped to the box), and exactly on
+    grid vertices of every level (s = u N integral), plus random points."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    pts = []
+    for cx in (0.0, 1.0):
+        for cy in (0.0, 1.0):
+            for cz in (0.0, 1.0):
+                pts.append([cx, cy, cz])
+    for axis in range(3):
+        for side in (0.0, 1.0):
+            p = rng.random((64, 3))
+            p[:, axis] = side
+            pts.extend(p.tolist())
+    p = rng.uniform(-0.5, 1.5, (256, 3))  # outside the box on some axes
+    pts.extend(p.tolist())
+    for N in n_levels_res:  # on vertices of level N: u = i / N (exact only where i / N is)
+        i = rng.integers(0, N + 1, (32, 3))
+        pts.extend((i / N).tolist())
+    u = np.asarray(pts)
+    pos = np.zeros((len(u), 4), np.float32)
+    pos[:, :3] = lo + (hi - lo) * u
+    return pos
+
+
+@pytest.mark.parametrize("spec,kw", [
+    (MODEL_C0, {}),
+    (MODEL_C1, dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX)),
+    (MODEL_C3, dict(aabb_min=ROOM_MIN, aabb_max=ROOM_MAX, t=1.0)),
+])
+def test_degenerate_positions(niv, spec, kw):
+    """The cases where the cell search clamps or lands on a vertex: points on the box's faces and
+    corners (u = 0 or 1, so s = N at the far face and the cell index is clamped to N - 1),
+    outside the box (u clamped), on grid vertices, t at its end: corner indices bit-exact, the
+    FP32 query within 1e-5 and the FP16 query within 2e-3 of the oracle."""
+    m, params, om = make(niv, spec, seed=4, bias_std=0.1)
+    lo, hi = kw.get("aabb_min", (0, 0, 0)), kw.get("aabb_max", (1, 1, 1))
+    res = [m.level_info(l)["res"] for l in range(om.levels)]
+    pos = _boundary_points(lo, hi, res[:6])
+    nrm = np.zeros_like(pos)
+    nrm[:, :3] = np.random.default_rng(1).normal(size=(len(pos), 3))
+    nrm[:, :3] /= np.linalg.norm(nrm[:, :3], axis=1, keepdims=True)
+    dp, dn = torch.from_numpy(pos).cuda(), torch.from_numpy(nrm).cuda()
+    enc, idx = m.encode(dp, **kw)
+    _, ref_idx, _ = oracle.encode(om, params, pos, lo, hi, kw.get("t", 0.0), want_corners=True)
+    np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), ref_idx)
+    ref = oracle.query(om, params, pos, nrm, **kw)
+    e32 = m.query(dp, dn, precision="fp32", out_dtype=torch.float32, **kw)[:, :3].cpu().numpy()
+    assert rel_err(e32, ref) <= 1e-5
+    ref16 = oracle.query(om, oracle_fp16_params(params, om), pos, nrm, **kw)
+    e16 = m.query(dp, dn, precision="fp16", out_dtype=torch.float32, **kw)[:, :3].cpu().numpy()
+    assert rel_err(e16, ref16) <= 2e-3
+    m.close()
+
+
+def oracle_fp16_params(params, om):
+    """The parameters as the FP16 path stores them (grid values, weights and biases in binary16)."""
+    return np.asarray(params, np.float32).astype(np.float16).astype(np.float64)
