@@ -6,12 +6,44 @@
 //   indices (dense or hashed), gathers, multilinear interpolation -> network
 //   input [features, n, (t)] -> ReLU hidden layers -> softplus output -> store.
 // Network weights live in shared memory and are read as warp-wide broadcasts;
-// the per-thread input vector sits in a [k][128] shared-memory column.
+// the per-thread input vector sits in a [k][128] shared-memory column.  The products run
+// on the packed FP32 pipe (NIV_FP32_PACKED): two FP32 FMAs per instruction, each lane an
+// ordinary FP32 FMA -- over output pairs in the first layer, over even and odd inputs
+// (two partial sums, added at the end) in the others.
 #include "niv_internal.cuh"
+
+#ifndef NIV_FP32_PACKED
+#define NIV_FP32_PACKED 1
+#endif
 
 namespace {
 
 constexpr int kThreads = 128;
+
+// a + sum_i w[i] h[i] over W inputs (w: shared-memory row, 16-byte aligned).
+template <int W>
+__device__ __forceinline__ float dot_row(const float* w, const float* h, float a) {
+    const float4* wrow = reinterpret_cast<const float4*>(w);
+    if (NIV_FP32_PACKED) {
+        float2 acc = make_float2(a, 0.0f);  // even and odd inputs
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q) {
+            const float4 w4 = wrow[q];
+            acc = __ffma2_rn(make_float2(w4.x, w4.y), make_float2(h[4 * q + 0], h[4 * q + 1]), acc);
+            acc = __ffma2_rn(make_float2(w4.z, w4.w), make_float2(h[4 * q + 2], h[4 * q + 3]), acc);
+        }
+        return acc.x + acc.y;
+    }
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+        const float4 w4 = wrow[q];
+        a = fmaf(w4.x, h[4 * q + 0], a);
+        a = fmaf(w4.y, h[4 * q + 1], a);
+        a = fmaf(w4.z, h[4 * q + 2], a);
+        a = fmaf(w4.w, h[4 * q + 3], a);
+    }
+    return a;
+}
 
 template <int DIMS, int F, int W>
 __global__ void __launch_bounds__(kThreads) query_fp32_kernel(GridArgs g, IoArgs io, const float* __restrict__ grid,
@@ -78,10 +110,20 @@ __global__ void __launch_bounds__(kThreads) query_fp32_kernel(GridArgs g, IoArgs
 #pragma unroll
             for (int o4 = 0; o4 < W / 4; ++o4) {
                 const float4 w4 = wrow[o4];
-                h[4 * o4 + 0] = fmaf(w4.x, xi, h[4 * o4 + 0]);
-                h[4 * o4 + 1] = fmaf(w4.y, xi, h[4 * o4 + 1]);
-                h[4 * o4 + 2] = fmaf(w4.z, xi, h[4 * o4 + 2]);
-                h[4 * o4 + 3] = fmaf(w4.w, xi, h[4 * o4 + 3]);
+                if (NIV_FP32_PACKED) {
+                    const float2 x2 = make_float2(xi, xi);
+                    const float2 lo = __ffma2_rn(make_float2(w4.x, w4.y), x2, make_float2(h[4 * o4 + 0], h[4 * o4 + 1]));
+                    const float2 hi = __ffma2_rn(make_float2(w4.z, w4.w), x2, make_float2(h[4 * o4 + 2], h[4 * o4 + 3]));
+                    h[4 * o4 + 0] = lo.x;
+                    h[4 * o4 + 1] = lo.y;
+                    h[4 * o4 + 2] = hi.x;
+                    h[4 * o4 + 3] = hi.y;
+                } else {
+                    h[4 * o4 + 0] = fmaf(w4.x, xi, h[4 * o4 + 0]);
+                    h[4 * o4 + 1] = fmaf(w4.y, xi, h[4 * o4 + 1]);
+                    h[4 * o4 + 2] = fmaf(w4.z, xi, h[4 * o4 + 2]);
+                    h[4 * o4 + 3] = fmaf(w4.w, xi, h[4 * o4 + 3]);
+                }
             }
         }
 #pragma unroll
@@ -92,19 +134,7 @@ __global__ void __launch_bounds__(kThreads) query_fp32_kernel(GridArgs g, IoArgs
         for (int layer = 1; layer < n_hidden - 1; ++layer) {
             const float* Wl = wp;  // [W][W] row-major
             const float* bl = wp + W * W;
-            for (int o = 0; o < W; ++o) {
-                float a = bl[o];
-                const float4* wrow = reinterpret_cast<const float4*>(Wl + o * W);
-#pragma unroll
-                for (int q = 0; q < W / 4; ++q) {
-                    const float4 w4 = wrow[q];
-                    a = fmaf(w4.x, h[4 * q + 0], a);
-                    a = fmaf(w4.y, h[4 * q + 1], a);
-                    a = fmaf(w4.z, h[4 * q + 2], a);
-                    a = fmaf(w4.w, h[4 * q + 3], a);
-                }
-                s_x[o * kThreads + k] = fmaxf(a, 0.0f);
-            }
+            for (int o = 0; o < W; ++o) s_x[o * kThreads + k] = fmaxf(dot_row<W>(Wl + o * W, h, bl[o]), 0.0f);
 #pragma unroll
             for (int q = 0; q < W; ++q) h[q] = s_x[q * kThreads + k];
             wp += W * W + W;
@@ -121,17 +151,7 @@ __global__ void __launch_bounds__(kThreads) query_fp32_kernel(GridArgs g, IoArgs
             z1 = bo[1];
             z2 = bo[2];
             for (int o = 0; o < W; ++o) {
-                float a = bl[o];
-                const float4* wrow = reinterpret_cast<const float4*>(Wl + o * W);
-#pragma unroll
-                for (int q = 0; q < W / 4; ++q) {
-                    const float4 w4 = wrow[q];
-                    a = fmaf(w4.x, h[4 * q + 0], a);
-                    a = fmaf(w4.y, h[4 * q + 1], a);
-                    a = fmaf(w4.z, h[4 * q + 2], a);
-                    a = fmaf(w4.w, h[4 * q + 3], a);
-                }
-                a = fmaxf(a, 0.0f);
+                const float a = fmaxf(dot_row<W>(Wl + o * W, h, bl[o]), 0.0f);
                 z0 = fmaf(Wo[o], a, z0);
                 z1 = fmaf(Wo[W + o], a, z1);
                 z2 = fmaf(Wo[2 * W + o], a, z2);
