@@ -50,7 +50,8 @@ typedef struct niv_model* niv_handle;
 /* network precision of a query */
 #define NIV_FP32 0 /* plain path: FP32 features, weights and arithmetic on CUDA cores */
 #define NIV_FP16 1 /* fused path: FP16 features and weights, tensor-core MLP, FP32 accumulate */
-#define NIV_FP8 2  /* fused path: E4M3 weights and activations with per-layer scales, FP32 accumulate */
+#define NIV_FP8 2  /* fused path: E4M3 weights and activations (two codes each) with per-layer
+                      scales, FP32 accumulate */
 
 /* element type of [n][4] record buffers */
 #define NIV_F32 0
@@ -278,8 +279,11 @@ NIV_API int niv_fit(niv_handle h, const float* pos, const float* nrm, const floa
  * Calibrate the E4M3 network path (NIV_FP8).  Runs the FP32 network over the n
  * device records pos/nrm ([n][4], dtype_in) and takes, for every matrix product,
  * the amax of its FP32 input; the activation scale is s_a = 2^ceil(log2(amax/448))
- * (1 if amax = 0).  Weight scales s_w = 2^ceil(log2(amax|W|/448)) per layer.  Packs
- * e4m3(W / s_w) for the tensor cores.  Must be called again after niv_set_params.
+ * (1 if amax = 0).  Weight scales s_w = 2^ceil(log2(amax|W|/448)) per layer.  Every
+ * scaled weight v = W / s_w is packed for the tensor cores as two E4M3 codes,
+ * h = e4m3(v) and l = e4m3(v - h); the query forms the layer inputs the same way from
+ * a / s_a and sums the products h_W h_a + h_W l_a + l_W h_a in FP32 (one code keeps 3
+ * mantissa bits, two about 8).  Must be called again after niv_set_params.
  * Synchronises `stream`.  NIV_ERR_UNSUPPORTED for width 16.
  */
 NIV_API int niv_fp8_calibrate(niv_handle h, const void* pos, const void* nrm, int64_t n, int32_t dtype_in,
