@@ -341,6 +341,26 @@ NIV_API int niv_mc_irradiance(const float* scene, int64_t scene_len, const float
                               uint8_t* out_keep, niv_stream stream);
 
 /*
+ * Primary-visibility G-buffer of the analytic scene: the world position, normal and
+ * albedo per pixel that the per-pixel query reads (Sec. 4.4; the deferred-shading inputs
+ * of Fig. 3).  A pinhole camera at eye (host float[3]) looks down +z with +y up; the
+ * ray of pixel (i, j), row 0 at the top, has direction
+ * ((2 (i + 0.5) / width - 1) s width / height, (1 - 2 (j + 0.5) / height) s, 1),
+ * normalised, with s = tan(vfov_deg / 2).  The first hit beyond 1e-4 follows
+ * niv_mc_irradiance's geometry in FP32 with the rotating sphere at scene parameter t:
+ * unit normals, outward for spheres and boxes, into the room for the walls; a ray leaving
+ * through the open skylight hits nothing.  pos, nrm, alb: device [width * height][4]
+ * records of dtype_out (NIV_F16 or NIV_F32; xyz and a pad of 0; all zero where nothing
+ * is hit), aligned to the record size; alb and hit (device uint8 [width * height]: 1
+ * where the ray hit) may be NULL.  scene: host description as in niv_mc_irradiance.
+ * NIV_ERR_ARG for sizes <= 0, more than 2^31 pixels or vfov_deg outside (0, 180).
+ * Asynchronous.
+ */
+NIV_API int niv_gbuffer_raycast(const float* scene, int64_t scene_len, int32_t width, int32_t height, double vfov_deg,
+                                const float* eye, float t, void* pos, void* nrm, void* alb, int32_t dtype_out,
+                                uint8_t* hit, niv_stream stream);
+
+/*
  * Keep the samples niv_mc_irradiance flagged out_keep = 1 (Sec. 4.5 culling, App. I
  * null discard), in their original order: out_x4, out_n4 (device float32 [m][4]),
  * out_t (device float32 [m], nullable; copies t, or 0 when t is NULL) and

@@ -463,6 +463,25 @@ def training_samples(scene_blob, n, surface_frac=0.2, seed=0, index_base=0, with
     return x4, n4, t, patch
 
 
+def gbuffer_raycast(scene_blob, width, height, eye, vfov_deg=60.0, t=0.0, dtype=torch.float16, want_albedo=True,
+                    want_hit=False, device="cuda", stream=None):
+    """Primary-visibility G-buffer of the analytic scene on the device (niv_gbuffer_raycast):
+    (pos [W*H][4], nrm [W*H][4], albedo [W*H][4] or None, hit [W*H] uint8 or None), records of
+    ``dtype`` (float16 or float32), row 0 at the top."""
+    blob = np.ascontiguousarray(scene_blob, np.float32)
+    eye3 = np.ascontiguousarray(eye, np.float32).reshape(3)
+    n = int(width) * int(height)
+    pos, nrm = (torch.empty((n, 4), dtype=dtype, device=device) for _ in range(2))
+    alb = torch.empty((n, 4), dtype=dtype, device=device) if want_albedo else None
+    hit = torch.empty(n, dtype=torch.uint8, device=device) if want_hit else None
+    check(lib().niv_gbuffer_raycast(ctypes.c_void_p(blob.ctypes.data), blob.size, int(width), int(height),
+                                    float(vfov_deg), ctypes.c_void_p(eye3.ctypes.data), float(t),
+                                    ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                                    ctypes.c_void_p(alb.data_ptr() if alb is not None else 0), _rec_dtype(pos),
+                                    ctypes.c_void_p(hit.data_ptr() if hit is not None else 0), _stream(stream)))
+    return pos, nrm, alb, hit
+
+
 def compact_targets(x4, n4, E, keep, t=None, stream=None):
     """Kept samples in order: (x4, n4, target4, t or None), each cut to the kept count."""
     m = x4.shape[0]

@@ -95,3 +95,29 @@ def test_model_files_are_checked_before_the_device(libniv, tmp_path):
     assert libniv.niv_load(str(short).encode(), ctypes.byref(h)) == NIV_ERR_ARG
     assert h.value == 1234
     assert libniv.niv_save(None, b"x", None) == NIV_ERR_ARG
+
+
+def test_gbuffer_raycast_arguments_fail_on_the_host(libniv):
+    import numpy as np
+    from paper_2602_12949_gb300._lib import NIV_ERR_ARG, NIV_ERR_ALIGN, NIV_F16, NIV_F32
+    from niv_inputs import room_scene
+    blob = np.ascontiguousarray(room_scene(0).blob(), np.float32)
+    eye = np.zeros(3, np.float32)
+    bp, ep = ctypes.c_void_p(blob.ctypes.data), ctypes.c_void_p(eye.ctypes.data)
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every case fails before a launch
+
+    def call(w=8, h=8, fov=60.0, pos=fake, nrm=fake, dt=NIV_F16, n=blob.size, scene=bp):
+        return libniv.niv_gbuffer_raycast(scene, n, w, h, fov, ep, 0.0, pos, nrm, None, dt, None, None)
+
+    assert call(scene=None) == NIV_ERR_ARG
+    assert call(pos=None) == NIV_ERR_ARG
+    assert call(w=0) == NIV_ERR_ARG
+    assert call(h=-1) == NIV_ERR_ARG
+    assert call(w=1 << 16, h=1 << 16) == NIV_ERR_ARG  # 2^32 pixels
+    assert call(fov=0.0) == NIV_ERR_ARG
+    assert call(fov=180.0) == NIV_ERR_ARG
+    assert call(dt=7) == NIV_ERR_ARG
+    assert call(n=blob.size - 1) == NIV_ERR_ARG
+    assert call(pos=ctypes.c_void_p((1 << 20) + 8), dt=NIV_F32) == NIV_ERR_ALIGN
+    assert call(nrm=ctypes.c_void_p((1 << 20) + 4)) == NIV_ERR_ALIGN
+    assert libniv.niv_last_error()
