@@ -398,12 +398,15 @@ def _table1_and_half(dev, flush, stream, dpos, dnrm, steps, warmup):
 
 def run_peaks(a):
     """Rates the roofline of the other paths needs, measured on this GPU: FP32 FMA (the
-    library's probe kernel, independent FMA chains on every thread), FP8 dense tensor
+    probe kernel of libniv_peaks.so, independent FMA chains on every thread), FP8 dense tensor
     (torch._scaled_mm, E4M3 8192^3) and L2 read bandwidth (torch sum over a 64 MiB tensor,
     L2-resident after the first pass).  Best of the timed repetitions, CUDA events."""
     import ctypes
     import torch
-    from paper_2602_12949_gb300._lib import check, lib
+    from paper_2602_12949_gb300.build import BENCH_LIB
+    peaks = ctypes.CDLL(BENCH_LIB)
+    peaks.niv_peak_ffma.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+    peaks.niv_peak_ffma.restype = ctypes.c_int
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
@@ -425,8 +428,10 @@ def run_peaks(a):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     blocks, iters = sms * 8 * 4, 8192
     buf = torch.zeros(blocks, device=dev)
-    ms = best(lambda: check(lib().niv_peak_ffma(ctypes.c_void_p(buf.data_ptr()), blocks, iters,
-                                                ctypes.c_void_p(stream.cuda_stream))), 10)
+    def ffma():
+        if peaks.niv_peak_ffma(ctypes.c_void_p(buf.data_ptr()), blocks, iters, ctypes.c_void_p(stream.cuda_stream)):
+            raise RuntimeError("niv_peak_ffma failed")
+    ms = best(ffma, 10)
     res["fp32_ffma_tflops"] = 2.0 * 8 * iters * 256 * blocks / (ms * 1e-3) / 1e12
     try:
         n = 8192

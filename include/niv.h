@@ -577,15 +577,6 @@ NIV_API int niv_selftest_wait_expiry(uint32_t limit_us, niv_stream stream);
  */
 NIV_API int niv_selftest_philox(const uint32_t* in6, int64_t n, uint32_t* out4, niv_stream stream);
 
-/*
- * Diagnostic, no paper counterpart: the FP32 FMA rate of this GPU for the plain path's
- * roofline.  Launches `blocks` CTAs of 256 threads, each thread running 8 independent
- * FMA chains for `iters` steps (2 * 8 * iters FLOP per thread, 4096 * blocks * iters in
- * all); out (device float32 [blocks]) is written only in a case that does not occur, so
- * that the chains are kept.  Asynchronous on `stream`; time it with events.
- */
-NIV_API int niv_peak_ffma(float* out, int32_t blocks, int32_t iters, niv_stream stream);
-
 #ifdef __cplusplus
 }
 #endif

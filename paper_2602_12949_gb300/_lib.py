@@ -68,7 +68,6 @@ _SIGNATURES = [
     ("niv_set_params", ctypes.c_int, [_VP, _VP, _I64, _VP]),
     ("niv_get_params", ctypes.c_int, [_VP, _VP, _I64, _VP]),
     ("niv_save", ctypes.c_int, [_VP, ctypes.c_char_p, _VP]),
-    ("niv_peak_ffma", ctypes.c_int, [_VP, _I32, _I32, _VP]),
     ("niv_load", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_VP)]),
     ("niv_query", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),
     ("niv_query_host", ctypes.c_int, [_VP, _VP, _VP, _I64, _I32, ctypes.POINTER(QueryParams), _VP, _I32, _I32, _VP]),

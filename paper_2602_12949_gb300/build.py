@@ -10,6 +10,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libniv.so")
+# Measurement aids that only the benchmark loads, kept out of the product library.
+BENCH_CSRC = os.path.join(PKG, "bench_csrc")
+BENCH_LIB = os.path.join(PKG, "libniv_peaks.so")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,7 +38,8 @@ def _stale(target, inputs):
 
 
 def _compile(src, extra=()):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    prefix = "bench_" if os.path.dirname(src) == BENCH_CSRC else ""
+    obj = os.path.join(BUILD, prefix + os.path.basename(src)[:-3] + ".o")
     if _stale(obj, [src] + _deps()):
         cmd = [NVCC, *ARCH, *FLAGS, *EXTRA, *extra, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -52,16 +56,18 @@ def build(force=False, verbose_ptxas=False):
             os.remove(o)
     extra = ("-Xptxas", "-v") if verbose_ptxas else ()
     srcs = _sources()
-    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if force or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-               "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
+    bench_srcs = sorted(glob.glob(os.path.join(BENCH_CSRC, "*.cu")))
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs) + len(bench_srcs), os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(lambda s: _compile(s, extra), srcs + bench_srcs))
+    for lib, lib_objs in ((LIB, objs[:len(srcs)]), (BENCH_LIB, objs[len(srcs):])):
+        if lib_objs and (force or _stale(lib, lib_objs)):
+            tmp = lib + ".tmp%d" % os.getpid()
+            cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *lib_objs,
+                   "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
+            os.replace(tmp, lib)
     return LIB
 
 
