@@ -361,6 +361,29 @@ NIV_API int niv_gbuffer_raycast(const float* scene, int64_t scene_len, int32_t w
                                 uint8_t* hit, niv_stream stream);
 
 /*
+ * Triangle meshes inserted into a G-buffer made by niv_gbuffer_raycast (the dynamic
+ * objects of Sec. 4.4 in the deferred-shading inputs), with the same camera arguments.
+ * A pixel's ray hits triangle (A, B, C) at distance t > 1e-6 (Moeller-Trumbore in FP32,
+ * barycentrics accepted to 1e-5 outside the edges so that shared edges leave no cracks); the
+ * nearest hit closer than the surface already in the pixel (|pos - eye| where hit = 1)
+ * replaces it: position eye + t d, the face normal (B - A) x (C - A) normalised and turned
+ * toward the camera, the mesh's albedo, hit = 1.  Among triangles at the same t the lowest
+ * index wins.  Triangles with a vertex less than 1e-3 in front of the camera plane
+ * (z - eye_z <= 1e-3) are skipped.  tri9: device float32 [n_tris][9] (the three vertices),
+ * tri_mesh: device int32 [n_tris] (mesh index; an index outside [0, n_meshes) gives albedo
+ * 0), mesh_albedo: host float32 [n_meshes][3], 1 <= n_meshes <= 64.  pos, nrm, alb (may be
+ * NULL): device [width * height][4] records of dtype (NIV_F16 / NIV_F32), updated in place;
+ * hit: device uint8 [width * height], read and updated; mesh_id (may be NULL): device int32
+ * [width * height], set to the winning mesh or -1; scratch: device uint64 [width * height].
+ * A triangle's work is its projected bounding box, so a triangle that covers much of the
+ * screen is slow.  Asynchronous.
+ */
+NIV_API int niv_gbuffer_meshes(const float* tri9, const int32_t* tri_mesh, int64_t n_tris, const float* mesh_albedo,
+                               int32_t n_meshes, int32_t width, int32_t height, double vfov_deg, const float* eye,
+                               void* pos, void* nrm, void* alb, int32_t dtype, uint8_t* hit, int32_t* mesh_id,
+                               uint64_t* scratch, niv_stream stream);
+
+/*
  * Keep the samples niv_mc_irradiance flagged out_keep = 1 (Sec. 4.5 culling, App. I
  * null discard), in their original order: out_x4, out_n4 (device float32 [m][4]),
  * out_t (device float32 [m], nullable; copies t, or 0 when t is NULL) and

@@ -92,6 +92,8 @@ _SIGNATURES = [
     ("niv_selftest_philox", ctypes.c_int, [_VP, _I64, _VP, _VP]),
     ("niv_training_samples", ctypes.c_int, [_VP, _I64, _I64, _F, _U64, _U64, _VP, _VP, _VP, _VP, _VP]),
     ("niv_gbuffer_raycast", ctypes.c_int, [_VP, _I64, _I32, _I32, _D, _VP, _F, _VP, _VP, _VP, _I32, _VP, _VP]),
+    ("niv_gbuffer_meshes", ctypes.c_int, [_VP, _VP, _I64, _VP, _I32, _I32, _I32, _D, _VP, _VP, _VP, _VP, _I32, _VP,
+                                          _VP, _VP, _VP]),
     ("niv_shade", ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
     ("niv_dyn_create", ctypes.c_int, [_VP, _I64, ctypes.POINTER(_VP)]),
     ("niv_dyn_destroy", ctypes.c_int, [_VP]),

@@ -482,6 +482,26 @@ def gbuffer_raycast(scene_blob, width, height, eye, vfov_deg=60.0, t=0.0, dtype=
     return pos, nrm, alb, hit
 
 
+def gbuffer_meshes(tri9, tri_mesh, mesh_albedo, pos, nrm, alb, hit, width, height, eye, vfov_deg=60.0,
+                   want_mesh_id=False, stream=None):
+    """Insert triangle meshes into a G-buffer in place (niv_gbuffer_meshes): tri9 device float32
+    [T][9], tri_mesh device int32 [T], mesh_albedo host [M][3]; pos/nrm/alb records and hit
+    (uint8) as made by gbuffer_raycast.  Returns the mesh index per pixel (int32, -1: none) or None."""
+    alb3 = np.ascontiguousarray(mesh_albedo, np.float32).reshape(-1, 3)
+    eye3 = np.ascontiguousarray(eye, np.float32).reshape(3)
+    n = int(width) * int(height)
+    if hit is None or hit.dtype != torch.uint8 or hit.numel() != n:
+        raise ValueError("hit must be a uint8 tensor of width * height flags")
+    scratch = torch.empty(n, dtype=torch.int64, device=pos.device)
+    mesh_id = torch.empty(n, dtype=torch.int32, device=pos.device) if want_mesh_id else None
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+    check(lib().niv_gbuffer_meshes(ptr(tri9), ptr(tri_mesh), int(tri9.shape[0]), ctypes.c_void_p(alb3.ctypes.data),
+                                   len(alb3), int(width), int(height), float(vfov_deg), ctypes.c_void_p(eye3.ctypes.data),
+                                   ptr(pos), ptr(nrm), ptr(alb), _rec_dtype(pos), ptr(hit), ptr(mesh_id), ptr(scratch),
+                                   _stream(stream)))
+    return mesh_id
+
+
 def compact_targets(x4, n4, E, keep, t=None, stream=None):
     """Kept samples in order: (x4, n4, target4, t or None), each cut to the kept count."""
     m = x4.shape[0]

@@ -121,3 +121,28 @@ def test_gbuffer_raycast_arguments_fail_on_the_host(libniv):
     assert call(pos=ctypes.c_void_p((1 << 20) + 8), dt=NIV_F32) == NIV_ERR_ALIGN
     assert call(nrm=ctypes.c_void_p((1 << 20) + 4)) == NIV_ERR_ALIGN
     assert libniv.niv_last_error()
+
+
+def test_gbuffer_meshes_arguments_fail_on_the_host(libniv):
+    import numpy as np
+    from paper_2602_12949_gb300._lib import NIV_ERR_ARG, NIV_ERR_ALIGN, NIV_F16
+    eye = np.zeros(3, np.float32)
+    alb = np.ones((2, 3), np.float32)
+    ep, ap = ctypes.c_void_p(eye.ctypes.data), ctypes.c_void_p(alb.ctypes.data)
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every case fails before a launch
+
+    def call(nt=4, nm=2, w=8, h=8, fov=60.0, pos=fake, scratch=fake, hit=fake, tri=fake, dt=NIV_F16):
+        return libniv.niv_gbuffer_meshes(tri, fake, nt, ap, nm, w, h, fov, ep, pos, fake, None, dt, hit, None,
+                                         scratch, None)
+
+    assert call(hit=None) == NIV_ERR_ARG
+    assert call(scratch=None) == NIV_ERR_ARG
+    assert call(nt=-1) == NIV_ERR_ARG
+    assert call(tri=None) == NIV_ERR_ARG
+    assert call(nm=0) == NIV_ERR_ARG
+    assert call(nm=65) == NIV_ERR_ARG
+    assert call(w=0) == NIV_ERR_ARG
+    assert call(fov=200.0) == NIV_ERR_ARG
+    assert call(dt=3) == NIV_ERR_ARG
+    assert call(pos=ctypes.c_void_p((1 << 20) + 4)) == NIV_ERR_ALIGN
+    assert call(scratch=ctypes.c_void_p((1 << 20) + 4)) == NIV_ERR_ALIGN

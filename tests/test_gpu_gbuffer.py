@@ -117,3 +117,66 @@ def test_gbuffer_reproduces_the_bench_records(niv):
     niv.sync_status()
     m.close()
     assert np.array_equal(e_dev[same], e_host[same])
+
+
+def _host_meshes(W, H, seed=0):
+    from niv_inputs.meshes import dynamic_objects, _raster_lib
+    pos, nrm, alb, hit = raycast_gbuffer(room_scene(seed), W, H, impl="c")
+    verts, tris, ids, albedo = dynamic_objects(seed)
+    hit8 = hit.astype(np.uint8)
+    mesh_id = np.full(W * H, -1, np.int32)
+    pos, nrm, alb = (np.ascontiguousarray(a) for a in (pos, nrm, alb))
+    verts, albedo = np.ascontiguousarray(verts), np.ascontiguousarray(albedo)
+    cam = np.asarray(CAMERA_POS, np.float64)
+    _raster_lib().niv_raster_meshes(verts.ctypes.data, tris.ctypes.data, ids.ctypes.data, len(tris), albedo.ctypes.data,
+                                    W, H, 60.0, cam.ctypes.data, pos.ctypes.data, nrm.ctypes.data, alb.ctypes.data,
+                                    hit8.ctypes.data, mesh_id.ctypes.data)
+    return pos, nrm, alb, hit8.astype(bool), mesh_id, (verts, tris, ids, albedo)
+
+
+def _device_meshes(niv, W, H, geom, dtype=torch.float32):
+    verts, tris, ids, albedo = geom
+    pos, nrm, alb, hit = niv.gbuffer_raycast(room_scene(0).blob(), W, H, CAMERA_POS, dtype=dtype, want_hit=True)
+    tri9 = torch.from_numpy(verts[tris].reshape(-1, 9).astype(np.float32)).cuda()
+    tri_mesh = torch.from_numpy(ids.astype(np.int32)).cuda()
+    mid = niv.gbuffer_meshes(tri9, tri_mesh, albedo, pos, nrm, alb, hit, W, H, CAMERA_POS, want_mesh_id=True)
+    niv.sync_status()
+    return pos, nrm, alb, hit, mid
+
+
+@pytest.mark.parametrize("W,H", [(960, 540), (1920, 1080)])
+def test_gbuffer_meshes_match_host_raster(niv, W, H):
+    hpos, hnrm, halb, hhit, hmid, geom = _host_meshes(W, H)
+    pos, nrm, alb, hit, mid = _device_meshes(niv, W, H, geom)
+    dpos, dnrm, dalb = (a.cpu().numpy() for a in (pos, nrm, alb))
+    dhit, dmid = hit.cpu().numpy().astype(bool), mid.cpu().numpy()
+    n = W * H
+    covered = hmid >= 0
+    assert covered.mean() > 0.03  # the three objects cover a few percent of the frame
+    same = dmid == hmid
+    assert (n - same.sum()) / n <= EDGE_FRACTION, (n - same.sum()) / n
+    assert np.array_equal(dhit[same], hhit[same])
+    obj = same & covered
+    assert np.all(dalb[obj, :3] == halb[obj].astype(np.float32))
+    ep = np.abs(dpos[obj, :3] - hpos[obj]).max(axis=1)
+    en = np.abs(dnrm[obj, :3] - hnrm[obj]).max(axis=1)
+    print("meshes: %d object pixels, mesh differs on %d of %d; |dpos| max %.2e, 99.9%% %.2e; |dnrm| 99%% %.2e, max %.2e"
+          % (obj.sum(), n - same.sum(), n, ep.max(), np.quantile(ep, 0.999), np.quantile(en, 0.99), en.max()))
+    assert np.quantile(ep, 0.999) <= POS_TOL and ep.max() <= POS_MAX
+    # a pixel on the edge between two triangles of one mesh may take either one's face normal
+    assert np.quantile(en, 0.99) <= NRM_TOL and en.max() <= 0.3
+    assert np.abs(np.linalg.norm(dnrm[obj, :3], axis=1) - 1).max() < 1e-5
+
+
+def test_gbuffer_meshes_repeat_bit_identically_in_fp16(niv):
+    W, H = 640, 360
+    *_, geom = _host_meshes(W, H)
+    a = _device_meshes(niv, W, H, geom, dtype=torch.float16)
+    b = _device_meshes(niv, W, H, geom, dtype=torch.float16)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    # pixels the meshes did not win keep the ray-cast records
+    pos, nrm, alb, hit = niv.gbuffer_raycast(room_scene(0).blob(), W, H, CAMERA_POS, dtype=torch.float16, want_hit=True)
+    keep = (a[4] < 0)
+    assert torch.equal(a[0][keep], pos[keep]) and torch.equal(a[1][keep], nrm[keep])
+    assert bool((a[4] >= 0).any())
