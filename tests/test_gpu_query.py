@@ -161,7 +161,7 @@ def test_query_host_matches_device_query(niv):
                                                               (0, 0, 300001, "fp32", np.float32),
                                                               (1920, 1080, 0, "fp16", np.float32)])
 def test_chunked_host_query_matches_device_query(niv, width, rows, n_extra, precision, rec):
-    # large calls are split into chunks of whole 8-row bands (or 128-record tiles) whose
+    # large calls are split into chunks of whole bands of tile rows (or 128-record tiles) whose
     # copies overlap the queries of their neighbours: the result must not change by a bit
     m, params, om = make(niv, MODEL_C1, seed=4)
     n = width * rows + n_extra
