@@ -29,11 +29,34 @@ def _rec_dtype(t):
     raise TypeError("records must be float16 or float32, got %s" % t.dtype)
 
 
-def _check_records(t, name):
+def _check_records(t, name, n=None, dtype=None):
+    """A contiguous [n][4] device tensor of FP16 or FP32 records (the kernels read and write
+    whole records, so a wrong shape or type would take them outside the buffer)."""
     if not isinstance(t, torch.Tensor) or t.dim() != 2 or t.shape[1] != 4 or not t.is_contiguous():
         raise ValueError("%s must be a contiguous [n][4] tensor" % name)
     if not t.is_cuda:
         raise ValueError("%s must live on the GPU (use query_host for host buffers)" % name)
+    if t.dtype not in (torch.float16, torch.float32) or (dtype is not None and t.dtype != dtype):
+        raise TypeError("%s must hold %s records, got %s" % (name, dtype or "float16 or float32", t.dtype))
+    if n is not None and t.shape[0] != n:
+        raise ValueError("%s must hold %d records, got %d" % (name, n, t.shape[0]))
+
+
+def _check_dev(t, name, dtype, shape):
+    """A contiguous device tensor of the given dtype and shape."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+
+
+def _cuda_device(device):
+    d = torch.device(device)
+    if d.type != "cuda":
+        raise ValueError("device must be a CUDA device, got %s" % d)
+    return d
 
 
 class NIVModel:
@@ -173,12 +196,14 @@ class NIVModel:
     def query_shade(self, pos, nrm, albedo, direct, out=None, precision="fp16", aabb_min=(0.0, 0.0, 0.0),
                     aabb_max=(1.0, 1.0, 1.0), t=0.0, image_width=0, stream=None):
         """Fused query + shading: FP16 rgba = (albedo * E / pi + direct, 1) for every record."""
-        for a, name in ((pos, "pos"), (nrm, "nrm"), (albedo, "albedo"), (direct, "direct")):
-            _check_records(a, name)
-        if albedo.dtype != torch.float16 or direct.dtype != torch.float16:
-            raise TypeError("albedo and direct must be float16 records")
+        _check_records(pos, "pos")
+        n = pos.shape[0]
+        _check_records(nrm, "nrm", n, pos.dtype)
+        _check_records(albedo, "albedo", n, torch.float16)
+        _check_records(direct, "direct", n, torch.float16)
         if out is None:
-            out = torch.empty((pos.shape[0], 4), dtype=torch.float16, device=pos.device)
+            out = torch.empty((n, 4), dtype=torch.float16, device=pos.device)
+        _check_records(out, "out", n, torch.float16)
         qp = self.query_params(aabb_min, aabb_max, t, image_width)
         check(lib().niv_query_shade(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
                                     ctypes.c_void_p(albedo.data_ptr()), ctypes.c_void_p(direct.data_ptr()),
@@ -194,12 +219,16 @@ class NIVModel:
         p, n = np.ascontiguousarray(to_np(pos)), np.ascontiguousarray(to_np(nrm))
         if p.ndim != 2 or p.shape[1] != 4 or p.shape != n.shape or p.dtype != n.dtype:
             raise ValueError("pos and nrm must be matching [n][4] arrays")
+        if p.dtype not in (np.float16, np.float32):
+            raise TypeError("pos and nrm must hold float16 or float32 records, got %s" % p.dtype)
         dt = _lib.NIV_F16 if p.dtype == np.float16 else _lib.NIV_F32
         if out is None:
             out = np.empty(p.shape, p.dtype)
         o = to_np(out) if isinstance(out, torch.Tensor) else out
-        if not (o.flags["C_CONTIGUOUS"] and o.shape == p.shape):
+        if not (isinstance(o, np.ndarray) and o.flags["C_CONTIGUOUS"] and o.shape == p.shape):
             raise ValueError("out must be a contiguous [n][4] array")
+        if o.dtype not in (np.float16, np.float32):
+            raise TypeError("out must hold float16 or float32 records, got %s" % o.dtype)
         odt = _lib.NIV_F16 if o.dtype == np.float16 else _lib.NIV_F32
         # a per-frame call: the parameter block is cached and the pointers are passed as ints
         key = (tuple(aabb_min), tuple(aabb_max), float(t), int(image_width))
@@ -215,10 +244,9 @@ class NIVModel:
         return out
 
     def _train_args(self, pos, nrm, target, t):
-        for a, name in ((pos, "pos"), (nrm, "nrm"), (target, "target")):
-            _check_records(a, name)
-            if a.dtype != torch.float32:
-                raise TypeError("%s must be float32 for training" % name)
+        _check_records(pos, "pos", None, torch.float32)
+        for a, name in ((nrm, "nrm"), (target, "target")):
+            _check_records(a, name, pos.shape[0], torch.float32)
         tp = 0
         if t is not None:
             if t.dtype != torch.float32 or not t.is_cuda or t.numel() != pos.shape[0]:
@@ -254,6 +282,8 @@ class NIVModel:
 
     def grads_into(self, out):
         """Copy the gradient buffer into a float32 tensor of param_count() values (host or device)."""
+        if not isinstance(out, torch.Tensor) or out.dtype != torch.float32 or not out.is_contiguous():
+            raise TypeError("out must be a contiguous float32 tensor")
         check(lib().niv_get_grads(self._h, ctypes.c_void_p(out.data_ptr()), out.numel(), _stream()))
         return out
 
@@ -285,7 +315,7 @@ class NIVModel:
     def fp8_calibrate(self, pos, nrm, aabb_min=(0.0, 0.0, 0.0), aabb_max=(1.0, 1.0, 1.0), t=0.0, stream=None):
         """Set the E4M3 path's activation scales from device records pos, nrm ([n][4])."""
         _check_records(pos, "pos")
-        _check_records(nrm, "nrm")
+        _check_records(nrm, "nrm", pos.shape[0], pos.dtype)
         qp = self.query_params(aabb_min, aabb_max, t, 0)
         check(lib().niv_fp8_calibrate(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
                                       pos.shape[0], _rec_dtype(pos), ctypes.byref(qp), _stream(stream)))
@@ -370,11 +400,13 @@ class DynamicGeometry:
         """AO in [0, 1] per device record (float32 [n]); E ([n][4] device records, optional) is
         scaled by it in place."""
         _check_records(pos, "pos")
-        _check_records(nrm, "nrm")
+        n = pos.shape[0]
+        _check_records(nrm, "nrm", n, pos.dtype)
         if out is None:
-            out = torch.empty(pos.shape[0], dtype=torch.float32, device=pos.device)
+            out = torch.empty(n, dtype=torch.float32, device=pos.device)
+        _check_dev(out, "out", torch.float32, (n,))
         if E is not None:
-            _check_records(E, "E")
+            _check_records(E, "E", n)
         check(lib().niv_dyn_ao(self._h, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
                                pos.shape[0], _rec_dtype(pos), int(rays), float(radius), int(seed),
                                ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(E.data_ptr() if E is not None else 0),
@@ -397,12 +429,18 @@ def upsample_shade(pos, nrm, albedo, direct, width, height, E_low, sub=2, power=
                    out=None, stream=None):
     """Full-resolution FP16 rgba from irradiance E_low queried at every sub-th pixel (joint
     bilateral upsampling guided by the G-buffer, then albedo * E / pi + direct)."""
-    for t, name in ((pos, "pos"), (nrm, "nrm"), (albedo, "albedo"), (direct, "direct"), (E_low, "E_low")):
-        _check_records(t, name)
-    if albedo.dtype != torch.float16 or direct.dtype != torch.float16:
-        raise TypeError("albedo and direct must be float16 records")
+    n = int(width) * int(height)
+    if int(sub) < 1:
+        raise ValueError("sub must be at least 1")
+    n_low = ((int(width) + int(sub) - 1) // int(sub)) * ((int(height) + int(sub) - 1) // int(sub))
+    _check_records(pos, "pos", n)
+    _check_records(nrm, "nrm", n, pos.dtype)
+    _check_records(albedo, "albedo", n, torch.float16)
+    _check_records(direct, "direct", n, torch.float16)
+    _check_records(E_low, "E_low", n_low)
     if out is None:
-        out = torch.empty((width * height, 4), dtype=torch.float16, device=pos.device)
+        out = torch.empty((n, 4), dtype=torch.float16, device=pos.device)
+    _check_records(out, "out", n, torch.float16)
     up = UpsampleParams(float(power), float(sigma), float(eps))
     check(lib().niv_upsample_shade(ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
                                    ctypes.c_void_p(albedo.data_ptr()), ctypes.c_void_p(direct.data_ptr()),
@@ -414,12 +452,12 @@ def upsample_shade(pos, nrm, albedo, direct, width, height, E_low, sub=2, power=
 
 def shade(albedo, direct, E, out=None, stream=None):
     """rgba = (albedo * E / pi + direct, 1) on FP16 [n][4] device tensors."""
-    for t, name in ((albedo, "albedo"), (direct, "direct"), (E, "E")):
-        _check_records(t, name)
-        if t.dtype != torch.float16:
-            raise TypeError("%s must be float16" % name)
+    _check_records(E, "E", None, torch.float16)
+    for t, name in ((albedo, "albedo"), (direct, "direct")):
+        _check_records(t, name, E.shape[0], torch.float16)
     if out is None:
         out = torch.empty_like(E)
+    _check_records(out, "out", E.shape[0], torch.float16)
     check(lib().niv_shade(ctypes.c_void_p(albedo.data_ptr()), ctypes.c_void_p(direct.data_ptr()),
                           ctypes.c_void_p(E.data_ptr()), E.shape[0], ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
@@ -430,14 +468,14 @@ def mc_irradiance(scene_blob, x4, n4, spp, seed=0, mode="indirect", t=None, inde
 
     Returns (E [m][3] float64 device tensor, keep [m] uint8 device tensor)."""
     blob = np.ascontiguousarray(scene_blob, np.float32)
-    _check_records(x4, "x4")
-    _check_records(n4, "n4")
+    _check_records(x4, "x4", None, torch.float32)
     m = x4.shape[0]
+    _check_records(n4, "n4", m, torch.float32)
     E = torch.empty((m, 3), dtype=torch.float64, device=x4.device)
     keep = torch.empty(m, dtype=torch.uint8, device=x4.device)
     tp = 0
     if t is not None:
-        t = t.contiguous().float()
+        _check_dev(t, "t", torch.float32, (m,))
         tp = t.data_ptr()
     md = {"total": _lib.NIV_MC_TOTAL, "indirect": _lib.NIV_MC_INDIRECT}[mode]
     check(lib().niv_mc_irradiance(ctypes.c_void_p(blob.ctypes.data), blob.size, ctypes.c_void_p(x4.data_ptr()),
@@ -452,6 +490,7 @@ def training_samples(scene_blob, n, surface_frac=0.2, seed=0, index_base=0, with
     """Training-sample candidates of Sec. 4.5 / App. I on the device (niv_training_samples):
     (x4 [n][4], n4 [n][4], t [n] or None, patch [n] int32 or None), float32 device tensors."""
     blob = np.ascontiguousarray(scene_blob, np.float32)
+    device = _cuda_device(device)
     x4 = torch.empty((n, 4), dtype=torch.float32, device=device)
     n4 = torch.empty((n, 4), dtype=torch.float32, device=device)
     t = torch.empty(n, dtype=torch.float32, device=device) if with_t else None
@@ -470,6 +509,9 @@ def gbuffer_raycast(scene_blob, width, height, eye, vfov_deg=60.0, t=0.0, dtype=
     ``dtype`` (float16 or float32), row 0 at the top."""
     blob = np.ascontiguousarray(scene_blob, np.float32)
     eye3 = np.ascontiguousarray(eye, np.float32).reshape(3)
+    device = _cuda_device(device)
+    if dtype not in (torch.float16, torch.float32):
+        raise TypeError("dtype must be torch.float16 or torch.float32")
     n = int(width) * int(height)
     pos, nrm = (torch.empty((n, 4), dtype=dtype, device=device) for _ in range(2))
     alb = torch.empty((n, 4), dtype=dtype, device=device) if want_albedo else None
@@ -490,8 +532,16 @@ def gbuffer_meshes(tri9, tri_mesh, mesh_albedo, pos, nrm, alb, hit, width, heigh
     alb3 = np.ascontiguousarray(mesh_albedo, np.float32).reshape(-1, 3)
     eye3 = np.ascontiguousarray(eye, np.float32).reshape(3)
     n = int(width) * int(height)
-    if hit is None or hit.dtype != torch.uint8 or hit.numel() != n:
-        raise ValueError("hit must be a uint8 tensor of width * height flags")
+    if not isinstance(tri9, torch.Tensor) or tri9.dim() != 2:
+        raise ValueError("tri9 must be a [T][9] tensor")
+    T = tri9.shape[0]
+    _check_dev(tri9, "tri9", torch.float32, (T, 9))
+    _check_dev(tri_mesh, "tri_mesh", torch.int32, (T,))
+    _check_records(pos, "pos", n)
+    _check_records(nrm, "nrm", n, pos.dtype)
+    if alb is not None:
+        _check_records(alb, "alb", n, pos.dtype)
+    _check_dev(hit, "hit", torch.uint8, (n,))
     scratch = torch.empty(n, dtype=torch.int64, device=pos.device)
     mesh_id = torch.empty(n, dtype=torch.int32, device=pos.device) if want_mesh_id else None
     ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)
@@ -504,7 +554,13 @@ def gbuffer_meshes(tri9, tri_mesh, mesh_albedo, pos, nrm, alb, hit, width, heigh
 
 def compact_targets(x4, n4, E, keep, t=None, stream=None):
     """Kept samples in order: (x4, n4, target4, t or None), each cut to the kept count."""
+    _check_records(x4, "x4", None, torch.float32)
     m = x4.shape[0]
+    _check_records(n4, "n4", m, torch.float32)
+    _check_dev(E, "E", torch.float64, (m, 3))
+    _check_dev(keep, "keep", torch.uint8, (m,))
+    if t is not None:
+        _check_dev(t, "t", torch.float32, (m,))
     ox, on, ot4 = (torch.empty((m, 4), dtype=torch.float32, device=x4.device) for _ in range(3))
     ot = torch.empty(m, dtype=torch.float32, device=x4.device) if t is not None else None
     cnt = ctypes.c_int64()
@@ -526,7 +582,7 @@ class ProbeGrid:
         self.lo = np.ascontiguousarray(lo, np.float32)
         self.hi = np.ascontiguousarray(hi, np.float32)
         self.count = int(np.prod(self.P))
-        self.coef16 = torch.zeros((self.count, 28), dtype=torch.float16, device=device)
+        self.coef16 = torch.zeros((self.count, 28), dtype=torch.float16, device=_cuda_device(device))
 
     @property
     def nbytes(self):
@@ -546,9 +602,10 @@ class ProbeGrid:
         """Probe irradiance at device records; with scene_blob, probes are rejected by
         ray-traced visibility ("+ RT") instead of the cosine fall-off."""
         _check_records(pos, "pos")
-        _check_records(nrm, "nrm")
+        _check_records(nrm, "nrm", pos.shape[0], pos.dtype)
         if out is None:
             out = torch.empty(pos.shape, dtype=out_dtype or pos.dtype, device=pos.device)
+        _check_records(out, "out", pos.shape[0])
         grid = (ctypes.c_void_p(self.coef16.data_ptr()), ctypes.c_void_p(self.P.ctypes.data),
                 ctypes.c_void_p(self.lo.ctypes.data), ctypes.c_void_p(self.hi.ctypes.data))
         recs = (ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(nrm.data_ptr()), pos.shape[0], _rec_dtype(pos),
