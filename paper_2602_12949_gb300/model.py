@@ -430,14 +430,15 @@ def upsample_shade(pos, nrm, albedo, direct, width, height, E_low, sub=2, power=
     """Full-resolution FP16 rgba from irradiance E_low queried at every sub-th pixel (joint
     bilateral upsampling guided by the G-buffer, then albedo * E / pi + direct)."""
     n = int(width) * int(height)
-    if int(sub) < 1:
-        raise ValueError("sub must be at least 1")
-    n_low = ((int(width) + int(sub) - 1) // int(sub)) * ((int(height) + int(sub) - 1) // int(sub))
     _check_records(pos, "pos", n)
     _check_records(nrm, "nrm", n, pos.dtype)
     _check_records(albedo, "albedo", n, torch.float16)
     _check_records(direct, "direct", n, torch.float16)
-    _check_records(E_low, "E_low", n_low)
+    if int(sub) >= 1:  # the library refuses sub < 1 itself
+        n_low = ((int(width) + int(sub) - 1) // int(sub)) * ((int(height) + int(sub) - 1) // int(sub))
+        _check_records(E_low, "E_low", n_low)
+    else:
+        _check_records(E_low, "E_low")
     if out is None:
         out = torch.empty((n, 4), dtype=torch.float16, device=pos.device)
     _check_records(out, "out", n, torch.float16)
