@@ -57,6 +57,9 @@ def _args():
     ap.add_argument("--train-steps", type=int, default=5000, help="config2: Adam steps")
     ap.add_argument("--spp", type=int, default=1024, help="config2: Monte Carlo paths per training target")
     ap.add_argument("--reuse", type=int, default=1, help="config2: passes over each pool of targets")
+    ap.add_argument("--model", default="c4", choices=["c1", "c4"],
+                    help="config2: the model trained; c4 (default) is the 2^19-entry model that config 4 names "
+                         "as config 2's, c1 the config-1 shape (2^17 entries)")
     return ap.parse_args()
 
 
@@ -484,10 +487,11 @@ def run_config2(a):
     import torch
     from paper_2602_12949_gb300 import NIVModel, ProbeGrid, fitting
     from niv_inputs import init_params, room_scene
-    from niv_inputs.configs import MODEL_C1, ROOM_MIN, ROOM_MAX
+    from niv_inputs.configs import MODEL_C1, MODEL_C4, ROOM_MIN, ROOM_MAX
     torch.cuda.set_device(0)
     scene = room_scene(0)
-    m = NIVModel(**MODEL_C1)
+    spec = MODEL_C4 if a.model == "c4" else MODEL_C1
+    m = NIVModel(**spec)
     g, nm = m.param_count()
     m.set_params(init_params(g, m.layer_shapes(), seed=0))
     t0 = time.perf_counter()
@@ -507,8 +511,10 @@ def run_config2(a):
             "value": probe[0] / niv["fp16"][0], "unit": "x (probe MSE / NIV FP16 MSE)", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic", "dtype": "f16 forward, f32 master weights",
             "config": {"workload": "config2: room scene seed 0 (uniform sky through the skylight + sphere emitter), "
-                                   "config-1 model (6.81 MB FP16), batch 2^18, lr 1e-2, Adam (0.9, 0.99, 1e-15), "
-                                   "pools of 2^20 candidates", "steps": a.train_steps, "spp": a.spp,
+                                   "%s (%.2f MB FP16), batch 2^18, lr 1e-2, Adam (0.9, 0.99, 1e-15), "
+                                   "pools of 2^20 candidates"
+                                   % ("2^19-entry model of config 4" if a.model == "c4" else "config-1 model",
+                                      2 * (g + nm) / 1e6), "steps": a.train_steps, "spp": a.spp,
                        "reuse": a.reuse, "held_out": "2^16 samples, 4096-spp references"},
             "niv_mse_fp16": niv["fp16"][0], "niv_rel_mse_fp16": niv["fp16"][1], "niv_mse_fp32": niv["fp32"][0],
             "probe_grid": "%d^3 (%.2f MB)" % (P, grid.nbytes / 1e6), "probe_mse": probe[0], "probe_rel_mse": probe[1],
