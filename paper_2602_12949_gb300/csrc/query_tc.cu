@@ -10,13 +10,14 @@
 //      tile laid out in the tensor core's canonical K-major format (the constant 1
 //      multiplies the first layer's bias, stored as an extra weight column);
 //   2. one thread issues tcgen05.mma (M = 128 records, N = width, K = 16 per
-//      instruction) against the weights resident in shared memory; the FP32
-//      accumulator lives in tensor memory (TMEM);
-//   3. each warp reads its 32 rows back with tcgen05.ld, adds the bias (FP32),
-//      rounds to FP16, applies ReLU on packed halves and writes the next layer's
-//      input tile; repeat per hidden layer;
+//      instruction) against the weights resident in shared memory, then one more
+//      K = 16 MMA that adds the layer's bias (a constant tile of ones against a
+//      tile holding the biases); the FP32 accumulator lives in tensor memory (TMEM);
+//   3. each warp reads its 32 rows back with tcgen05.ld, rounds to FP16, applies
+//      ReLU on packed halves and writes the next layer's input tile; repeat per
+//      hidden layer;
 //   4. the output layer (N = 16, three live columns) also runs on the tensor
-//      core; bias, softplus in FP32 and the store of E finish the record.
+//      core; softplus in FP32 and the store of E finish the record.
 // Parameters are FP16 (weights, biases, grid features: all parameters in half
 // precision, Table 1), accumulation FP32.  Every wait on the MMA-completion
 // barrier is bounded (2 s); on expiry the kernel records a failure in the status
@@ -27,8 +28,9 @@
 // launch-bounds residency target, NIV_TC_OUT_FMA output layer on the CUDA cores,
 // NIV_TC_FIXW kernels compiled for the 16-level models' network shapes (width 64, 48
 // input columns, 2 or 3 hidden layers), NIV_TC_ND those kernels also compiled for their
-// dense-level counts (NIV_BLEND_PAIRS in encoding.cuh: a corner's two features blended as
-// one packed FP32 pair).
+// dense-level counts, NIV_TC_BIAS_MMA biases added by the tensor core, NIV_TC_NRM_EARLY
+// normal records loaded at the start of a tile (NIV_BLEND_PAIRS in
+// encoding.cuh: a corner's two features blended as one packed FP32 pair).
 #include <cuda_fp8.h>
 #include <string.h>
 
@@ -67,6 +69,27 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 #ifndef NIV_TC_OUT_FMA
 #define NIV_TC_OUT_FMA 0
 #endif
+// Biases of the hidden layers after the first and of the output layer added by the tensor core:
+// one more K = 16 MMA per layer, of a constant tile whose column 0 is 1 against a tile whose
+// column 0 holds the layer's FP16 biases (exact products), in place of the FP32 adds of the
+// epilogue (measured 3% faster at 1080p).  Layer 1's bias always rides in a column of W1.
+#ifndef NIV_TC_BIAS_MMA
+#define NIV_TC_BIAS_MMA 1
+#endif
+constexpr bool kBiasMma = NIV_TC_BIAS_MMA != 0;
+// FP16 records: the normal loaded with the position at the start of a tile and held as its raw
+// 8 bytes through the encoding, so that its latency hides behind the encoding (measured 3%
+// faster at 1080p, 1% on the 4-D config-3 model at 4K); FP32 records read it after the encoding.
+#ifndef NIV_TC_NRM_EARLY
+#define NIV_TC_NRM_EARLY 1
+#endif
+constexpr bool kNrmEarly = NIV_TC_NRM_EARLY != 0 && kP == 1;
+
+__device__ __forceinline__ float4 rec16_to_float4(uint2 r) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
 constexpr int kHdr = 128;    // barriers + TMEM address slot at the start of dynamic shared memory
 constexpr int kNO = 16;      // rows of the output-layer tile (3 live)
 constexpr bool kOutFma = NIV_TC_OUT_FMA != 0;  // output layer on the CUDA cores instead of the tensor core
@@ -81,6 +104,7 @@ struct TcLayout {
     int32_t K1, W, n_hidden, col_extra;  // col_extra: tile column of n.x (features end before it)
     int32_t col_one;                     // tile column holding the constant 1 (first-layer bias)
     uint32_t w1, wh, wo, bias, wout, total;  // byte offsets inside the packed network
+    uint32_t ones, bt;  // NIV_TC_BIAS_MMA: the 128 x 16 ones tile, then the W x 16 bias tiles and 16 x 16 b_out tile
 };
 
 __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
@@ -109,14 +133,20 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
 
 // Issue one layer for each of the kP tiles: sum over K/16 steps of act x W^T into TMEM (tile p
 // reads act + p act_stride and accumulates at tmem + p tmem_stride), then signal `bar`.
+// ones != 0: then add the bias, ones-tile x bias-tile^T (both K = 16, column 0 live).
 __device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t act, uint32_t w, uint32_t K, uint32_t idesc,
-                                            uint32_t bar, uint32_t act_stride = 0, uint32_t tmem_stride = 0) {
+                                            uint32_t bar, uint32_t act_stride = 0, uint32_t tmem_stride = 0,
+                                            uint32_t ones = 0u, uint32_t bias = 0u) {
     const uint32_t sbo = (K >> 3) * 128u;
 #pragma unroll
-    for (int p = 0; p < kP; ++p)
+    for (int p = 0; p < kP; ++p) {
         for (uint32_t ks = 0; ks < K / 16; ++ks)
             tc::mma_f16(tmem + p * tmem_stride, tc::smem_desc(act + p * act_stride + ks * 256u, 128u, sbo),
                         tc::smem_desc(w + ks * 256u, 128u, sbo), idesc, ks > 0 ? 1u : 0u);
+        if (kBiasMma && ones != 0u)
+            tc::mma_f16(tmem + p * tmem_stride, tc::smem_desc(ones, 128u, 256u), tc::smem_desc(bias, 128u, 256u),
+                        idesc, 1u);
+    }
     tc::mma_commit(bar);
 }
 
@@ -310,10 +340,12 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
     for (; walk[0].tile < n_tiles && ok;) {
         int64_t r[kP], rr[kP];
         float u[kP][4];
+        uint2 nrm_raw = make_uint2(0u, 0u);
 #pragma unroll
         for (int p = 0; p < kP; ++p) {
             r[p] = walk[p].record(tid, io.n, io.image_width);
             rr[p] = r[p] < io.n ? walk[p].source(r[p], io) : 0;
+            if (kNrmEarly && io.in_f16) nrm_raw = __ldg(reinterpret_cast<const uint2*>(io.nrm) + rr[p]);
             const float4 pv = niv_load_rec(io.pos, rr[p], io.in_f16);
             u[p][0] = niv_unit(pv.x, g.aabb_min[0], g.inv_ext[0]);
             u[p][1] = niv_unit(pv.y, g.aabb_min[1], g.inv_ext[1]);
@@ -343,7 +375,8 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
 #pragma unroll
         for (int p = 0; p < kP; ++p) {
         uint8_t* s_row = s_act + p * tile_bytes;
-        const float4 nv = niv_load_rec(io.nrm, rr[p], io.in_f16);  // read late: not live during the encoding
+        // FP32 records: read late, not live during the encoding
+        const float4 nv = (kNrmEarly && io.in_f16) ? rec16_to_float4(nrm_raw) : niv_load_rec(io.nrm, rr[p], io.in_f16);
         int tail = 8;  // columns written from col_extra on
         if (g.t_bands == 0) {  // [n.x, n.y, n.z, (t), 1, 0, ...]: the 1 multiplies the first layer's bias column
             const bool has_t = g.n_in > (PE != 0 ? 0 : L * F) + 6 * g.pe_bands + 3;
@@ -387,7 +420,9 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         for (int layer = 0; layer < NH && ok; ++layer) {
             if (tid == 0) {
                 tc::fence_after_sync();
-                issue_layer(tmem, act_a, net_a + w_off, K, idesc_h, bar, tile_bytes, wg_cols);
+                issue_layer(tmem, act_a, net_a + w_off, K, idesc_h, bar, tile_bytes, wg_cols,
+                            kBiasMma && layer > 0 ? net_a + lay.ones : 0u,
+                            net_a + lay.bt + (uint32_t)((layer > 0 ? layer - 1 : 0) * W * 32));
             }
             if (!group_wait_mma(bar, phase, warp, wg)) {
                 if (tid == 0) atomicExch(status, 1);
@@ -409,7 +444,7 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
                 uint8_t* s_row = s_act + p * tile_bytes;
                 float v[16];
                 tc::tmem_ld16(tmem_row + (uint32_t)(p * wg_cols + c * 16), v);
-                if (layer > 0) {
+                if (layer > 0 && !kBiasMma) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {  // biases 16-byte aligned: one load per four
                         const float4 b = reinterpret_cast<const float4*>(bias + c * 16)[j];
@@ -452,7 +487,8 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
         if (!kOutFma) {
             if (tid == 0) {
                 tc::fence_after_sync();
-                issue_layer(tmem, act_a, net_a + lay.wo, (uint32_t)W, idesc_o, bar, tile_bytes, wg_cols);
+                issue_layer(tmem, act_a, net_a + lay.wo, (uint32_t)W, idesc_o, bar, tile_bytes, wg_cols,
+                            kBiasMma ? net_a + lay.ones : 0u, net_a + lay.bt + (uint32_t)((NH - 1) * W * 32));
             }
             if (!group_wait_mma(bar, phase, warp, wg)) {
                 if (tid == 0) atomicExch(status, 1);
@@ -467,10 +503,16 @@ __global__ void __launch_bounds__(kT * kWG, NIV_TC_MINB) query_tc_f16_kernel(Gri
             if (!kOutFma) {
                 float z[4];
                 tmem_ld4(tmem_row + (uint32_t)(p * wg_cols), z);
-                const float* bo = s_bias + (NH - 1) * W;
-                z0 = z[0] + bo[0];
-                z1 = z[1] + bo[1];
-                z2 = z[2] + bo[2];
+                if (kBiasMma) {
+                    z0 = z[0];
+                    z1 = z[1];
+                    z2 = z[2];
+                } else {
+                    const float* bo = s_bias + (NH - 1) * W;
+                    z0 = z[0] + bo[0];
+                    z1 = z[1] + bo[1];
+                    z2 = z[2] + bo[2];
+                }
             }
             if (out_act == 1) {
                 z0 = niv_softplus_lp(z0);
@@ -634,6 +676,11 @@ int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s) {
     lay.bias = up(lay.wo + (uint32_t)(kNO * W * 2));
     lay.wout = up(lay.bias + (uint32_t)(((nh - 1) * W + 4) * 4));
     lay.total = up(lay.wout + (uint32_t)(3 * W * 4));
+    if (kBiasMma) {
+        lay.ones = lay.total;
+        lay.bt = up(lay.ones + (uint32_t)(kT * 16 * 2));
+        lay.total = up(lay.bt + (uint32_t)(((nh - 1) * W + kNO) * 16 * 2));
+    }
     static_assert(sizeof(TcLayout) <= sizeof(((niv_model*)0)->tc_layout), "layout slot too small");
     memcpy(m->tc_layout, &lay, sizeof lay);
     std::vector<uint8_t> buf(lay.total, 0);
@@ -665,6 +712,12 @@ int niv_pack_tc(niv_model* m, const float* mlp_host, cudaStream_t s) {
         }
     p += 3 * W;
     for (int r = 0; r < 3; ++r) bias[(nh - 1) * W + r] = h16(p[r]);
+    if (kBiasMma) {  // column 0 of the ones tile is 1; column 0 of each bias tile the layer's biases
+        for (int r = 0; r < kT; ++r) put(lay.ones, r, 0, 16, 1.0f);
+        for (int h = 1; h < nh; ++h)
+            for (int r = 0; r < W; ++r) put(lay.bt + (uint32_t)((h - 1) * W * 32), r, 0, 16, bias[(h - 1) * W + r]);
+        for (int r = 0; r < 3; ++r) put(lay.bt + (uint32_t)((nh - 1) * W * 32), r, 0, 16, bias[(nh - 1) * W + r]);
+    }
     if (m->mlp_tc_bytes < lay.total) {
         cudaFree(m->mlp_tc);
         m->mlp_tc = nullptr;
