@@ -73,14 +73,14 @@ def _peaks():
 
 
 def _extra_peaks():
-    """FP32 FMA, FP8 tensor and L2 read rates measured by `bench.py --workload peaks` on this
-    GPU model and recorded in profiles/measured_peaks_gb300.md; {} when absent."""
+    """FP32 FMA, FP8 tensor, L2 read and host-link rates measured by `bench.py --workload peaks`
+    on this GPU model and recorded in profiles/measured_peaks_gb300.md; {} when absent."""
     out = {}
     try:
         with open(os.path.join(ROOT, "profiles", "measured_peaks_gb300.md")) as f:
             for line in f:
                 k, _, v = line.partition(":")
-                if k.strip() in ("fp32_ffma_tflops", "fp8_tflops", "l2_read_gbs"):
+                if k.strip() in ("fp32_ffma_tflops", "fp8_tflops", "l2_read_gbs", "host_frame_rw_gbs"):
                     out[k.strip()] = float(v.strip())
     except (OSError, ValueError):
         pass
@@ -402,8 +402,9 @@ def _table1_and_half(dev, flush, stream, dpos, dnrm, steps, warmup):
 def run_peaks(a):
     """Rates the roofline of the other paths needs, measured on this GPU: FP32 FMA (the
     probe kernel of libniv_peaks.so, independent FMA chains on every thread), FP8 dense tensor
-    (torch._scaled_mm, E4M3 8192^3) and L2 read bandwidth (torch sum over a 64 MiB tensor,
-    L2-resident after the first pass).  Best of the timed repetitions, CUDA events."""
+    (torch._scaled_mm, E4M3 8192^3), L2 read bandwidth (torch sum over a 64 MiB tensor,
+    L2-resident after the first pass) and the host link (libniv_peaks.so's kernel streaming
+    through page-locked host memory; copy engines).  Best of the timed repetitions, CUDA events."""
     import ctypes
     import torch
     from paper_2602_12949_gb300.build import BENCH_LIB
@@ -449,6 +450,35 @@ def run_peaks(a):
     x = torch.ones(16 << 20, device=dev)  # 64 MiB of FP32
     ms = best(lambda: x.sum(), 50)
     res["l2_read_gbs"] = x.numel() * 4 / (ms * 1e-3) / 1e9
+    del x
+    # the host link: a kernel streaming through page-locked host memory with coalesced 16-byte
+    # words (reads, writes, and both at the 2:1 ratio and sizes of a 1080p frame of FP16
+    # records: pos + nrm in, E out, as the host-buffer query moves them), and the copy engines
+    peaks.niv_peak_host_stream.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    peaks.niv_peak_host_stream.restype = ctypes.c_int
+    hblocks = sms * 8
+    sink = torch.zeros(hblocks, dtype=torch.int32, device=dev)
+    big = 256 << 20
+    hin = torch.empty(big, dtype=torch.uint8).pin_memory()
+    hout = torch.empty(big, dtype=torch.uint8).pin_memory()
+    hin.fill_(1)
+
+    def host(b_in, b_out):
+        rc = peaks.niv_peak_host_stream(ctypes.c_void_p(hin.data_ptr()) if b_in else None, b_in,
+                                        ctypes.c_void_p(hout.data_ptr()) if b_out else None, b_out,
+                                        ctypes.c_void_p(sink.data_ptr()), hblocks, ctypes.c_void_p(stream.cuda_stream))
+        if rc:
+            raise RuntimeError("niv_peak_host_stream failed (%d)" % rc)
+    res["host_read_gbs"] = big / (best(lambda: host(big, 0), 10) * 1e-3) / 1e9
+    res["host_write_gbs"] = big / (best(lambda: host(0, big), 10) * 1e-3) / 1e9
+    f_in, f_out = 2 * 1920 * 1080 * 8, 1920 * 1080 * 8
+    ms = best(lambda: host(f_in, f_out), 20)
+    res["host_frame_rw_gbs"] = (f_in + f_out) / (ms * 1e-3) / 1e9
+    res["host_frame_rw_ms"] = ms
+    dbuf = torch.empty(big, dtype=torch.uint8, device=dev)
+    res["h2d_copy_gbs"] = big / (best(lambda: dbuf.copy_(hin, non_blocking=True), 10) * 1e-3) / 1e9
+    res["d2h_copy_gbs"] = big / (best(lambda: hout.copy_(dbuf, non_blocking=True), 10) * 1e-3) / 1e9
     line = {"metric": "measured peaks for the rooflines beside the tensor one", "value": res["fp32_ffma_tflops"],
             "unit": "TFLOP/s (FP32 FMA)", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "peaks": res, "gpu": torch.cuda.get_device_name(dev), "sms": sms}
@@ -873,6 +903,20 @@ def main():
             errs["fp32"] = {"max_rel": float(np.max(np.abs(got32 - ref) / den)),
                             "max_abs_normalised": float(np.max(np.abs(got32 - ref)) / np.abs(ref).max())}
 
+    e2e = {"value": e2e_val, "unit": "Gqueries/s", "h2d_bytes_per_step": int(2 * hp.nbytes),
+           "d2h_bytes_per_step": int(ho.nbytes), "ms_per_frame": 1e3 * e2e_med,
+           "calls": len(e2e_t), "statistic": "median wall-clock time of the calls",
+           "path": "the niv_query_host C-ABI call (ctypes, arguments marshalled once) on page-locked "
+                   "buffers: the query kernel reads pos/nrm from host memory and writes E to it over "
+                   "NVLink-C2C; L2 flushed before each call"}
+    link = _extra_peaks().get("host_frame_rw_gbs")
+    if link:  # the records and results cross the host link inside the call: its measured rate bounds it
+        moved = 2 * hp.nbytes + ho.nbytes
+        e2e["roofline"] = {"bound": "host link", "achieved": moved / e2e_med / 1e9, "peak": link, "unit": "GB/s",
+                           "frac": moved / e2e_med / 1e9 / link,
+                           "peak_source": "measured: a kernel streaming the same bytes through page-locked host "
+                                          "memory (profiles/measured_peaks_gb300.md)"}
+
     line = {
         "metric": METRIC, "value": value, "unit": "Gqueries/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_step, "ms_per_frame": mean_ms, "ms_per_step_mean": ms_total / a.steps,
@@ -885,12 +929,7 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_val, "unit": "Gqueries/s", "h2d_bytes_per_step": int(2 * hp.nbytes),
-                "d2h_bytes_per_step": int(ho.nbytes), "ms_per_frame": 1e3 * e2e_med,
-                "calls": len(e2e_t), "statistic": "median wall-clock time of the calls",
-                "path": "the niv_query_host C-ABI call (ctypes, arguments marshalled once) on page-locked "
-                        "buffers: the query kernel reads pos/nrm from host memory and writes E to it over "
-                        "NVLink-C2C; L2 flushed before each call"},
+        "e2e": e2e,
         "clocks": clk.summary(),
         "gpu_launches": a.steps,
         "err_vs_fp64": errs,
