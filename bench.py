@@ -87,6 +87,17 @@ def _extra_peaks():
     return out
 
 
+def host_link_roofline(bytes_moved, seconds, link_gbs):
+    """Roofline of a host-buffer call: the records and results cross the host link inside the
+    call, so the link's measured rate for that traffic bounds it; None without a measurement."""
+    if not link_gbs or seconds <= 0:
+        return None
+    achieved = bytes_moved / seconds / 1e9
+    return {"bound": "host link", "achieved": achieved, "peak": link_gbs, "unit": "GB/s", "frac": achieved / link_gbs,
+            "peak_source": "measured: a kernel streaming the same bytes through page-locked host memory "
+                           "(profiles/measured_peaks_gb300.md)"}
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -909,13 +920,9 @@ def main():
            "path": "the niv_query_host C-ABI call (ctypes, arguments marshalled once) on page-locked "
                    "buffers: the query kernel reads pos/nrm from host memory and writes E to it over "
                    "NVLink-C2C; L2 flushed before each call"}
-    link = _extra_peaks().get("host_frame_rw_gbs")
-    if link:  # the records and results cross the host link inside the call: its measured rate bounds it
-        moved = 2 * hp.nbytes + ho.nbytes
-        e2e["roofline"] = {"bound": "host link", "achieved": moved / e2e_med / 1e9, "peak": link, "unit": "GB/s",
-                           "frac": moved / e2e_med / 1e9 / link,
-                           "peak_source": "measured: a kernel streaming the same bytes through page-locked host "
-                                          "memory (profiles/measured_peaks_gb300.md)"}
+    link_roofline = host_link_roofline(2 * hp.nbytes + ho.nbytes, e2e_med, _extra_peaks().get("host_frame_rw_gbs"))
+    if link_roofline:
+        e2e["roofline"] = link_roofline
 
     line = {
         "metric": METRIC, "value": value, "unit": "Gqueries/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,

@@ -47,3 +47,21 @@ def test_missing_or_garbled_summary_gives_none(tmp_path, monkeypatch):
     assert bench._profiled_record() is None
     os.remove(root / "profiles" / "niv_query_fp16_1080p.md")
     assert bench._profiled_record() is None
+
+
+def test_measured_peaks_include_the_host_link():
+    """The committed peak summary gives the host link's rate on a 1080p frame's traffic, which
+    bounds the end-to-end (host-buffer) figure."""
+    p = bench._extra_peaks()
+    assert p.get("host_frame_rw_gbs", 0) > 0
+    assert p.get("fp32_ffma_tflops", 0) > 0
+
+
+def test_host_link_roofline():
+    moved = 2 * 1920 * 1080 * 8 + 1920 * 1080 * 8  # pos + nrm in, E out (FP16 records)
+    r = bench.host_link_roofline(moved, 0.256e-3, 274.3)
+    assert r["bound"] == "host link" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - moved / 0.256e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 274.3) < 1e-12
+    assert bench.host_link_roofline(moved, 0.256e-3, None) is None
+    assert bench.host_link_roofline(moved, 0.0, 274.3) is None
